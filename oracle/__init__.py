@@ -1,0 +1,219 @@
+"""ORACLE -- test infrastructure only.
+
+Plain, slow, obviously-correct CPU reference for the ranking, H·v and Lanczos
+quantities of Wallerberger & Held, "Trie-based ranking of quantum many-body
+states".  Only the tests, ``__graft_entry__.smoke()`` and the benchmark's CPU
+baseline may import it; the product path (the CUDA library and its binding)
+never does, and shares no code with it.
+
+The C part (``oracle.c``) is compiled with plain gcc on first use.  The Python
+part adds what numpy does best: dense diagonalisation (``numpy.linalg.eigvalsh``)
+of small sectors and the non-interacting closed form.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+import subprocess
+import threading
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "oracle.c")
+_BUILD = os.path.join(_HERE, "_build")
+_LIB_PATH = os.path.join(_BUILD, "liboracle.so")
+_lock = threading.Lock()
+_lib = None
+
+NOT_FOUND = -1
+
+
+def build(force: bool = False) -> str:
+    """Compile oracle.c to a shared library with gcc (no GPU involved)."""
+    os.makedirs(_BUILD, exist_ok=True)
+    if force or not os.path.exists(_LIB_PATH) or os.path.getmtime(_LIB_PATH) < os.path.getmtime(_SRC):
+        tmp = _LIB_PATH + f".tmp{os.getpid()}"
+        subprocess.check_call(["gcc", "-O2", "-std=c11", "-fPIC", "-shared", "-o", tmp, _SRC, "-lm"])
+        os.replace(tmp, _LIB_PATH)
+    return _LIB_PATH
+
+
+def lib():
+    global _lib
+    with _lock:
+        if _lib is None:
+            L = C.CDLL(build())
+            u64, i64, i32, dbl = C.c_uint64, C.c_int64, C.c_int, C.c_double
+            vp = C.c_void_p
+            L.ora_binom.restype = u64; L.ora_binom.argtypes = [i32, i32]
+            L.ora_enumerate.restype = i64; L.ora_enumerate.argtypes = [i32, i32, vp, i64]
+            L.ora_rank_bisect.restype = i64; L.ora_rank_bisect.argtypes = [vp, i64, u64]
+            L.ora_rank_count.restype = u64; L.ora_rank_count.argtypes = [i32, u64]
+            L.ora_unrank_greedy.restype = u64; L.ora_unrank_greedy.argtypes = [i32, i32, u64]
+            L.ora_trie_build.restype = i64; L.ora_trie_build.argtypes = [vp, i64, i32, i32, vp, i64]
+            L.ora_trie_rank.restype = i64; L.ora_trie_rank.argtypes = [vp, i64, i32, i32, u64]
+            L.ora_sector_dim.restype = i64; L.ora_sector_dim.argtypes = [i32, i32, i32]
+            L.ora_sector_states.restype = i32; L.ora_sector_states.argtypes = [i32, i32, i32, vp]
+            L.ora_sector_rank_of.restype = i64; L.ora_sector_rank_of.argtypes = [i32, i32, i32, u64]
+            L.ora_hv_full.restype = i32; L.ora_hv_full.argtypes = [i32, vp, vp, i32, i32, vp, vp]
+            L.ora_hv_rows.restype = i32; L.ora_hv_rows.argtypes = [i32, vp, vp, i32, i32, vp, vp, i64, vp]
+            L.ora_count_elements.restype = i64; L.ora_count_elements.argtypes = [i32, vp, i32, i32, i64, i64]
+            L.ora_dense.restype = i32; L.ora_dense.argtypes = [i32, vp, vp, i32, i32, vp]
+            L.ora_tridiag_lowest.restype = dbl; L.ora_tridiag_lowest.argtypes = [vp, vp, i32]
+            L.ora_lanczos.restype = i32
+            L.ora_lanczos.argtypes = [i32, vp, vp, i32, i32, vp, i32, i32, vp, vp, vp, vp, vp]
+            _lib = L
+    return _lib
+
+
+def _p(a: np.ndarray):
+    return a.ctypes.data_as(C.c_void_p)
+
+
+def _f64(a) -> np.ndarray:
+    return np.ascontiguousarray(a, dtype=np.float64)
+
+
+# ------------------------------------------------------------------ ranking
+
+def binom(n: int, k: int) -> int:
+    return int(lib().ora_binom(n, k))
+
+
+def enumerate_sector(M: int, N: int) -> np.ndarray:
+    """C^M_N in lexicographic (= increasing numeric) order, by brute force."""
+    n = binom(M, N)
+    out = np.empty(n, dtype=np.uint64)
+    got = lib().ora_enumerate(M, N, _p(out), n)
+    if got != n:
+        raise RuntimeError("enumeration count differs from C(M, N)")
+    return out
+
+
+def rank_bisect(sorted_list: np.ndarray, alpha: int) -> int:
+    a = np.ascontiguousarray(sorted_list, dtype=np.uint64)
+    return int(lib().ora_rank_bisect(_p(a), a.size, int(alpha)))
+
+
+def rank_bisect_many(sorted_list: np.ndarray, alphas) -> np.ndarray:
+    a = np.ascontiguousarray(sorted_list, dtype=np.uint64)
+    f = lib().ora_rank_bisect
+    return np.array([f(_p(a), a.size, int(x)) for x in np.asarray(alphas, dtype=np.uint64)], dtype=np.int64)
+
+
+def rank_count(M: int, alpha: int) -> int:
+    return int(lib().ora_rank_count(M, int(alpha)))
+
+
+def unrank(M: int, N: int, i: int) -> int:
+    return int(lib().ora_unrank_greedy(M, N, int(i)))
+
+
+def trie_build(sorted_members: np.ndarray, M: int, R: int, with_table: bool = True):
+    """Packed trie of Sec. IV (depth-first layout).  Returns (size, t or None)."""
+    a = np.ascontiguousarray(sorted_members, dtype=np.uint64)
+    size = int(lib().ora_trie_build(_p(a), a.size, M, R, None, 0))
+    if size < 0:
+        raise ValueError("bad trie input")
+    if not with_table:
+        return size, None
+    t = np.empty(size, dtype=np.int64)
+    lib().ora_trie_build(_p(a), a.size, M, R, _p(t), size)
+    return size, t
+
+
+def trie_rank(t: np.ndarray, M: int, R: int, alpha: int) -> int:
+    return int(lib().ora_trie_rank(_p(t), t.size, M, R, int(alpha)))
+
+
+# ----------------------------------------------------------------- sectors
+
+def sector_dim(L: int, Nup: int, Ndn: int) -> int:
+    return int(lib().ora_sector_dim(L, Nup, Ndn))
+
+
+def sector_states(L: int, Nup: int, Ndn: int) -> np.ndarray:
+    out = np.empty(sector_dim(L, Nup, Ndn), dtype=np.uint64)
+    if lib().ora_sector_states(L, Nup, Ndn, _p(out)):
+        raise ValueError("bad sector")
+    return out
+
+
+def sector_rank(L: int, Nup: int, Ndn: int, alpha: int) -> int:
+    return int(lib().ora_sector_rank_of(L, Nup, Ndn, int(alpha)))
+
+
+# -------------------------------------------------------------------- H·v
+
+def _hU(L, h, U):
+    h = _f64(h).reshape(L, L)
+    U = _f64(np.zeros(L) if U is None else U).reshape(L)
+    return h, U
+
+
+def hv(L, h, U, Nup, Ndn, x) -> np.ndarray:
+    """y = H x over the whole sector (scatter form, Eq. mvblock)."""
+    h, U = _hU(L, h, U)
+    x = _f64(x)
+    y = np.empty_like(x)
+    rc = lib().ora_hv_full(L, _p(h), _p(U), Nup, Ndn, _p(x), _p(y))
+    if rc:
+        raise RuntimeError(f"ora_hv_full failed: {rc}")
+    return y
+
+
+def hv_rows(L, h, U, Nup, Ndn, x, rows) -> np.ndarray:
+    """Rows ``rows`` of H x (gather form)."""
+    h, U = _hU(L, h, U)
+    x = _f64(x)
+    r = np.ascontiguousarray(rows, dtype=np.int64)
+    y = np.empty(r.size, dtype=np.float64)
+    rc = lib().ora_hv_rows(L, _p(h), _p(U), Nup, Ndn, _p(x), _p(r), r.size, _p(y))
+    if rc:
+        raise RuntimeError(f"ora_hv_rows failed: {rc}")
+    return y
+
+
+def count_elements(L, h, Nup, Ndn, row0: int = 0, row1: int = 0) -> int:
+    h, _ = _hU(L, h, None)
+    return int(lib().ora_count_elements(L, _p(h), Nup, Ndn, row0, row1))
+
+
+def dense(L, h, U, Nup, Ndn) -> np.ndarray:
+    h, U = _hU(L, h, U)
+    D = sector_dim(L, Nup, Ndn)
+    Hm = np.empty((D, D), dtype=np.float64)
+    if lib().ora_dense(L, _p(h), _p(U), Nup, Ndn, _p(Hm)):
+        raise RuntimeError("ora_dense failed")
+    return Hm
+
+
+def dense_E0(L, h, U, Nup, Ndn) -> float:
+    """Lowest eigenvalue of the dense sector matrix (numpy eigvalsh)."""
+    return float(np.linalg.eigvalsh(dense(L, h, U, Nup, Ndn))[0])
+
+
+def free_E0(h, Nup: int, Ndn: int) -> float:
+    """U = 0 closed form: sum of the lowest N_up plus lowest N_dn one-body levels."""
+    e = np.linalg.eigvalsh(_f64(h))
+    return float(e[:Nup].sum() + e[:Ndn].sum())
+
+
+def tridiag_lowest(a, b) -> float:
+    a = _f64(a); b = _f64(b if len(b) else [0.0])
+    return float(lib().ora_tridiag_lowest(_p(a), _p(b), a.size))
+
+
+def lanczos(L, h, U, Nup, Ndn, s0, iters: int, reorth: bool):
+    """FP64 Lanczos; returns dict(E0, alpha, beta, k, ritz)."""
+    h, U = _hU(L, h, U)
+    s0 = _f64(s0)
+    a = np.zeros(iters); b = np.zeros(max(iters, 1)); e = np.zeros(iters)
+    k = C.c_int(0); E0 = C.c_double(0.0)
+    rc = lib().ora_lanczos(L, _p(h), _p(U), Nup, Ndn, _p(s0), iters, int(bool(reorth)), _p(a), _p(b),
+                           C.byref(k), C.byref(E0), _p(e))
+    if rc:
+        raise RuntimeError(f"ora_lanczos failed: {rc}")
+    kk = k.value
+    return dict(E0=E0.value, alpha=a[:kk].copy(), beta=b[:max(kk - 1, 0)].copy(), k=kk, ritz=e[:kk].copy())
