@@ -1,0 +1,272 @@
+/*
+ * gbrank -- GB300 (sm_103a) ranking, on-the-fly H·v and Lanczos for
+ * quantum many-body states.
+ *
+ * C ABI of libgbrank.so.  Method: Wallerberger & Held, "Trie-based ranking
+ * of quantum many-body states" (arXiv:2203.04158).  Every entry point cites
+ * the passage that defines the operation.
+ *
+ * Conventions shared by all calls
+ *   * Status: every call returns an int, GBR_OK (0) on success.  On failure
+ *     the thread-local message is available from gbr_last_error().  No C++
+ *     exception crosses the ABI.  Argument errors are detected on the host
+ *     before anything is launched.
+ *   * Handles (gbr_comb, gbr_trie, gbr_ham) are opaque, created and owned by
+ *     the library, released with the matching *_destroy (NULL is accepted).
+ *     Creation builds tables on the host and copies them to the current
+ *     CUDA device synchronously; a handle is used on that device only.
+ *   * Buffers named d_* are device pointers owned by the caller (any
+ *     cudaMalloc'd or framework-allocated memory).  Buffers named h_* are
+ *     host pointers owned by the caller.
+ *   * stream is a cudaStream_t passed as void* (NULL = legacy default
+ *     stream).  Calls that only launch work are asynchronous on that stream:
+ *     results are valid after the stream synchronises.  Calls that return
+ *     host results (gbr_lanczos, gbr_batch_solve) synchronise the stream.
+ *   * Bit patterns: bit i of a uint64_t is spin-orbital i.  A sector of
+ *     fixed particle number N in M spin-orbitals is ordered by increasing
+ *     numeric value (lexicographic order, Sec. III, Eq. comb).
+ *   * Two-spin sectors (Hubbard/impurity Hamiltonians) use L sites per spin,
+ *     spin-orbital p = (site p, down) and L+p = (site p, up): least
+ *     significant bits are spin down (Sec. IV, around Eq. rankupdown).  The
+ *     sector index is r_up * C(L, N_dn) + r_dn (Eq. rankupdown with the
+ *     multiplier read as the spin-down dimension, the only reading that is a
+ *     bijection when N_up != N_dn).
+ */
+#ifndef GBRANK_H
+#define GBRANK_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+enum {
+    GBR_OK = 0,
+    GBR_EINVAL = 1,      /* bad argument (detected on the host) */
+    GBR_ENOMEM = 2,      /* device or host allocation failed */
+    GBR_ECUDA = 3,       /* a CUDA runtime call failed */
+    GBR_ENOTFOUND = 4,   /* a queried pattern is not a member (check mode) */
+    GBR_ETIMEOUT = 5,    /* a bounded device-side wait ran out */
+    GBR_EBREAKDOWN = 6   /* Lanczos stopped early on an invariant subspace */
+};
+
+/* Rank value written for a pattern that is not in the set (check mode) and
+ * pattern value written for an out-of-range rank. */
+#define GBR_NOT_FOUND_U32 0xFFFFFFFFu
+#define GBR_NOT_FOUND_U64 0xFFFFFFFFFFFFFFFFull
+
+/* Message of the last failed call on this thread ("" if none). */
+const char *gbr_last_error(void);
+
+/* ABI version, currently 1. */
+int gbr_version(void);
+
+/* ------------------------------------------------------------------------
+ * Fixed-popcount sectors: staggered lookup (Sec. III-B, Fig. fastrank,
+ * Eq. partrank) and combinadics unranking (Eq. unrank).
+ * --------------------------------------------------------------------- */
+typedef struct gbr_comb gbr_comb;
+
+/* Builds the staggered tables rank(r, M', N') of Eq. partrank for the
+ * sector C^M_N, chunk width R, restricted to the N' values admissible for N
+ * (Sec. III-B, remarks after Eq. stagmem), with entries computed through
+ * Eq. reuse from the combinadics ranking of Fig. algr.
+ *   M: 1..64 spin-orbitals; N: 0..M particles; R: chunk width 1..12.
+ * Entries are 32-bit when C(M, N) <= 2^32, else 64-bit.
+ * Errors: GBR_EINVAL for out-of-range arguments, GBR_ENOMEM, GBR_ECUDA. */
+int gbr_comb_create(int M, int N, int R, gbr_comb **out);
+void gbr_comb_destroy(gbr_comb *c);
+
+/* dim = C(M, N); table_bytes = size of the staggered tables on the device. */
+int gbr_comb_info(const gbr_comb *c, uint64_t *dim, int64_t *table_bytes);
+
+/* Ranks n patterns (Fig. fastrank): d_rank[i] = rank of d_pat[i] in C^M_N.
+ *   d_pat:  n uint64 patterns (device).  16-byte alignment enables
+ *           vectorised loads; any 8-byte aligned pointer is accepted.
+ *   d_rank: n ranks (device), uint32 when rank_bits == 32 (requires
+ *           C(M, N) <= 2^32) or uint64 when rank_bits == 64.
+ *   check:  0 = trust the input (a pattern outside the sector gets an
+ *           unspecified rank, but every table access stays in bounds);
+ *           1 = patterns with bits at or above M or popcount != N get
+ *           GBR_NOT_FOUND_U32 / _U64.
+ * n == 0 is a no-op.  Asynchronous on stream. */
+int gbr_comb_rank(const gbr_comb *c, const uint64_t *d_pat, void *d_rank, int rank_bits, int64_t n, int check,
+                  void *stream);
+
+/* Unranks n ranks (Eq. unrank): d_pat[i] = the d_rank[i]-th member of
+ * C^M_N; ranks >= C(M, N) give GBR_NOT_FOUND_U64.  rank_bits 32 or 64. */
+int gbr_comb_unrank(const gbr_comb *c, const void *d_rank, int rank_bits, uint64_t *d_pat, int64_t n, void *stream);
+
+/* ------------------------------------------------------------------------
+ * Packed tries over arbitrary sorted state sets (Sec. IV, Fig. trie,
+ * Fig. trielookup).
+ * --------------------------------------------------------------------- */
+typedef struct gbr_trie gbr_trie;
+
+/* Builds the linearised, packed trie of radix 2^R over n distinct M-bit
+ * patterns given in strictly increasing order (host array, not retained).
+ * Chunks are dispatched from the least significant bits; the first
+ * dispatched chunk has width M mod R (or R when R divides M); the root is
+ * stored in full and every other node as the span between its smallest and
+ * largest child, the parent holding (start - smallest child) (Fig. trie (c)).
+ * Nodes are stored level by level (breadth first) so that the upper levels
+ * form one contiguous prefix.  2^R zero entries pad the end (Sec. IV, remark
+ * on trailing elements).  Entries are 32-bit when the table and n fit, else
+ * 64-bit.  A device copy of the member list is kept for unranking and for
+ * the membership check.
+ *   M: 1..64; R: 1..16; n >= 1.
+ * Errors: GBR_EINVAL if the input is unsorted, has duplicates or a bit at
+ * or above M; GBR_ENOMEM; GBR_ECUDA. */
+int gbr_trie_create(const uint64_t *h_sorted, int64_t n, int M, int R, gbr_trie **out);
+void gbr_trie_destroy(gbr_trie *t);
+
+/* n_members, n_elements (trie entries without padding; the overhead factor
+ * of Sec. IV is n_elements / n_members), entry_bytes (4 or 8), levels
+ * (ceil(M / R)). Any output pointer may be NULL. */
+int gbr_trie_info(const gbr_trie *t, int64_t *n_members, int64_t *n_elements, int *entry_bytes, int *levels);
+
+/* Host-only construction of the same packed trie into h_t (uint64 entries,
+ * capacity cap, padding included); *size_out receives the element count
+ * without padding, and the call succeeds with h_t == NULL to query it.
+ * Needs no GPU. */
+int gbr_trie_build_host(const uint64_t *h_sorted, int64_t n, int M, int R, uint64_t *h_t, int64_t cap,
+                        int64_t *size_out);
+
+/* Ranks n patterns by the trie walk of Fig. trielookup.  Every table index
+ * is clamped into the table, so any input is safe.  check = 1 verifies the
+ * result against the member list (Sec. IV, validity check) and writes
+ * GBR_NOT_FOUND_* for non-members.  rank_bits 32 (requires n_members <=
+ * 2^32) or 64.  Asynchronous on stream. */
+int gbr_trie_rank(const gbr_trie *t, const uint64_t *d_pat, void *d_rank, int rank_bits, int64_t n, int check,
+                  void *stream);
+
+/* Unranks through the stored member list (Sec. II, unranking by a list);
+ * out-of-range ranks give GBR_NOT_FOUND_U64. */
+int gbr_trie_unrank(const gbr_trie *t, const void *d_rank, int rank_bits, uint64_t *d_pat, int64_t n, void *stream);
+
+/* ------------------------------------------------------------------------
+ * Hubbard / impurity Hamiltonians and the on-the-fly H·v (Sec. II,
+ * Eqs. Talpha and mvblock; Eq. Hring; Appendix, Eqs. ci and Fig. mul).
+ *
+ *   H = sum_sigma sum_{p != q} h[p][q] c^dag_{p sigma} c_{q sigma}
+ *     + sum_{p, sigma} h[p][p] n_{p sigma} + sum_p U[p] n_{p up} n_{p dn}
+ *
+ * (Eq. H with t = -h for the one-body part, on-site U as in Eq. Hring.)
+ * --------------------------------------------------------------------- */
+typedef struct gbr_ham gbr_ham;
+
+enum {
+    GBR_RANK_STAGGERED = 0, /* Fig. fastrank with 8-bit chunks */
+    GBR_RANK_CNS = 1        /* Fig. algr, one binomial per set bit */
+};
+
+enum {
+    GBR_HV_AUTO = 0,        /* pick by sector size (and the tuner, if run) */
+    GBR_HV_FUSED = 1,       /* one kernel: per element unrank, hop, sign, rank, gather */
+    GBR_HV_FACTORED = 2     /* per-spin hop lists ranked once per call, then two gather passes */
+};
+
+/* L: 1..32 sites; h: L*L row-major symmetric one-body matrix (host, copied);
+ * U: L on-site interactions (host, copied; NULL = all zero);
+ * Nup, Ndn: 0..L; rank_method: GBR_RANK_*.
+ * Errors: GBR_EINVAL (non-symmetric h, sizes), GBR_ENOMEM, GBR_ECUDA. */
+int gbr_ham_create(int L, const double *h, const double *U, int Nup, int Ndn, int rank_method, gbr_ham **out);
+void gbr_ham_destroy(gbr_ham *H);
+
+/* dim = C(L,Nup) C(L,Ndn); elements = matrix elements one H·v visits
+ * (the diagonal plus every non-zero off-diagonal (state, hop) pair). */
+int gbr_ham_info(const gbr_ham *H, int64_t *dim, int64_t *elements);
+
+/* Selects the H·v implementation (GBR_HV_*) used by gbr_hv and gbr_lanczos. */
+int gbr_ham_set_path(gbr_ham *H, int path);
+
+/* y = H x on the sector (Eq. mvblock with Eq. Talpha applied on the fly).
+ *   d_x, d_y: dim elements (device), float when fp == 32, double when
+ *   fp == 64; they must not overlap.  Deterministic: each y element has one
+ *   owner and a fixed summation order, no atomics.  Asynchronous. */
+int gbr_hv(const gbr_ham *H, const void *d_x, void *d_y, int fp, void *stream);
+
+/* Auto-tunes the H·v launch shape (threads, tiles) for precision fp on this
+ * device by timing the candidates on scratch vectors; the choice is kept in
+ * the handle.  Synchronises the stream. */
+int gbr_ham_tune(gbr_ham *H, int fp, void *stream);
+
+/* ------------------------------------------------------------------------
+ * Lanczos ground state (cited in Sec. I and V-B; the recurrence is the
+ * textbook three-term one).
+ * --------------------------------------------------------------------- */
+enum { GBR_PREC_FP64 = 0, GBR_PREC_MIXED = 1 };
+
+typedef struct {
+    int iters;        /* H·v steps (>= 1) */
+    int reorth;       /* 1 = full re-orthogonalisation (two classical Gram-Schmidt
+                         passes in FP64 against every stored vector) */
+    int prec;         /* GBR_PREC_FP64: FP64 vectors and H·v;
+                         GBR_PREC_MIXED: FP32 vectors and H·v, FP64 scalars */
+    int refine;       /* 1 = form the Ritz vector and return the FP64 Rayleigh
+                         quotient <x,Hx>/<x,x> and residual |Hx - E x| / |x| */
+    int store_basis;  /* 1 = keep all vectors (needed by reorth; makes the Ritz
+                         vector one pass), 0 = recompute the basis in a second
+                         run of the recurrence, -1 = decide from free memory */
+    int use_graph;    /* 1 = replay each iteration as a captured CUDA graph */
+} gbr_lanczos_opts;
+
+typedef struct {
+    double E0;         /* refined energy if refine, else the lowest Ritz value */
+    double E_ritz;     /* lowest eigenvalue of the tridiagonal matrix */
+    double residual;   /* |H x - E0 x| / |x| (refine only, else -1) */
+    int iters_done;    /* H·v steps actually taken */
+    int breakdown;     /* 1 if the recurrence stopped on beta ~ 0 */
+    int stored_basis;  /* 1 if the basis was kept in device memory */
+    double seconds;    /* device time of the whole call (CUDA events) */
+    double hv_seconds; /* device time spent inside H·v launches */
+} gbr_lanczos_result;
+
+/* Runs Lanczos from the start vector d_v0 (dim doubles on the device, not
+ * necessarily normalised; the mixed path rounds it to FP32 first).
+ * h_alpha, h_beta (host, may be NULL): receive the iters_done diagonal and
+ * iters_done-1 off-diagonal entries; h_ritz (host, may be NULL): the lowest
+ * Ritz value after every step.  Stops early (breakdown) when
+ * beta_{k+1} <= 1e-13 max_j(|alpha_j|, beta_j).  Synchronises the stream.
+ * Errors: GBR_EINVAL, GBR_ENOMEM (vectors do not fit), GBR_ECUDA. */
+int gbr_lanczos(const gbr_ham *H, const gbr_lanczos_opts *opts, const double *d_v0, gbr_lanczos_result *res,
+                double *h_alpha, double *h_beta, double *h_ritz, void *stream);
+
+/* ------------------------------------------------------------------------
+ * Batched ground states of many small models, every (N_up, N_dn) sector,
+ * in one persistent launch (the impurity-solver use case of Sec. I and VI).
+ * --------------------------------------------------------------------- */
+typedef struct {
+    int L;             /* sites, 1..10 */
+    const double *h;   /* L*L symmetric one-body matrix (host) */
+    const double *U;   /* L on-site interactions (host, NULL = 0) */
+} gbr_model_desc;
+
+/* Number of sectors and total states of the batch: sectors are ordered
+ * model by model, then N_up = 0..L, then N_dn = 0..L; sector s starts at
+ * state offset sum of the dimensions before it. */
+int gbr_batch_layout(int n_models, const gbr_model_desc *models, int64_t *n_sectors, int64_t *n_states);
+
+/* Solves every sector of every model with mixed-precision Lanczos (FP32
+ * vectors in shared memory, FP64 scalars, FP64 Rayleigh-quotient
+ * refinement of the Ritz vector) in one persistent kernel; each CTA pulls
+ * sectors from a device work queue, largest first.
+ *   d_start: n_states start-vector entries (device doubles), sector by
+ *            sector in the layout above;
+ *   iters:   Lanczos steps per sector (capped by the sector dimension);
+ *   h_E0:    n_models ground-state energies (host);
+ *   h_arg:   2 * n_models (N_up, N_dn) of the minimising sector (host, may
+ *            be NULL); ties within 1e-10 |E| go to the lower N_up + N_dn,
+ *            then the lower N_up;
+ *   h_sector_E (host, may be NULL): n_sectors refined sector energies.
+ * Synchronises the stream. Errors: GBR_EINVAL, GBR_ENOMEM, GBR_ECUDA,
+ * GBR_ETIMEOUT (a bounded wait on the work queue ran out). */
+int gbr_batch_solve(int n_models, const gbr_model_desc *models, const double *d_start, int iters, double *h_E0,
+                    int *h_arg, double *h_sector_E, void *stream);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* GBRANK_H */

@@ -58,6 +58,9 @@ def lib():
             L.ora_sector_rank_of.restype = i64; L.ora_sector_rank_of.argtypes = [i32, i32, i32, u64]
             L.ora_hv_full.restype = i32; L.ora_hv_full.argtypes = [i32, vp, vp, i32, i32, vp, vp]
             L.ora_hv_rows.restype = i32; L.ora_hv_rows.argtypes = [i32, vp, vp, i32, i32, vp, vp, i64, vp]
+            L.ora_hv_rows_seeded.restype = i32
+            L.ora_hv_rows_seeded.argtypes = [i32, vp, vp, i32, i32, u64, vp, i64, vp]
+            L.ora_seeded_uniform.restype = dbl; L.ora_seeded_uniform.argtypes = [u64, u64]
             L.ora_count_elements.restype = i64; L.ora_count_elements.argtypes = [i32, vp, i32, i32, i64, i64]
             L.ora_dense.restype = i32; L.ora_dense.argtypes = [i32, vp, vp, i32, i32, vp]
             L.ora_tridiag_lowest.restype = dbl; L.ora_tridiag_lowest.argtypes = [vp, vp, i32]
@@ -173,6 +176,21 @@ def hv_rows(L, h, U, Nup, Ndn, x, rows) -> np.ndarray:
     if rc:
         raise RuntimeError(f"ora_hv_rows failed: {rc}")
     return y
+
+
+def hv_rows_seeded(L, h, U, Nup, Ndn, seed: int, rows) -> np.ndarray:
+    """Rows of H x with x_j = uniform[-1,1)(seed, j) generated on demand."""
+    h, U = _hU(L, h, U)
+    r = np.ascontiguousarray(rows, dtype=np.int64)
+    y = np.empty(r.size, dtype=np.float64)
+    rc = lib().ora_hv_rows_seeded(L, _p(h), _p(U), Nup, Ndn, int(seed), _p(r), r.size, _p(y))
+    if rc:
+        raise RuntimeError(f"ora_hv_rows_seeded failed: {rc}")
+    return y
+
+
+def seeded_uniform(seed: int, i: int) -> float:
+    return float(lib().ora_seeded_uniform(int(seed), int(i)))
 
 
 def count_elements(L, h, Nup, Ndn, row0: int = 0, row1: int = 0) -> int:

@@ -433,6 +433,53 @@ int ora_hv_rows(int L, const double *h, const double *U, int Nup, int Ndn, const
     return c.bad ? -1 : 0;
 }
 
+/* The seeded input generator, written here from its published definition
+ * (splitmix64 of Steele, Lea and Flood, counter mode
+ * u(seed, i) = splitmix64(seed XOR i*0x9E3779B97F4A7C15)), so that sampled
+ * rows of very large sectors can read x_j = uniform[-1, 1)(seed, j) on demand
+ * without materialising x. */
+static uint64_t ora_splitmix64(uint64_t z) {
+    z += 0x9E3779B97F4A7C15ull;
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+    return z ^ (z >> 31);
+}
+
+double ora_seeded_uniform(uint64_t seed, uint64_t i) {
+    uint64_t u = ora_splitmix64(seed ^ (i * 0x9E3779B97F4A7C15ull));
+    return 2.0 * ((double)(u >> 11) * 0x1.0p-53) - 1.0;
+}
+
+typedef struct {
+    const ora_sector *s;
+    uint64_t seed;
+    double acc;
+    int bad;
+} ora_seed_ctx;
+
+static void ora_cb_gather_seeded(void *vctx, double coef, uint64_t beta) {
+    ora_seed_ctx *c = (ora_seed_ctx *)vctx;
+    int64_t j = ora_sector_rank(c->s, beta);
+    if (j < 0) { c->bad = 1; return; }
+    c->acc += coef * ora_seeded_uniform(c->seed, (uint64_t)j);
+}
+
+/* Selected rows of y = H x for x_j = uniform[-1, 1)(seed, j); same gather
+ * form as ora_hv_rows. */
+int ora_hv_rows_seeded(int L, const double *h, const double *U, int Nup, int Ndn, uint64_t seed,
+                       const int64_t *rows, int64_t nrows, double *y_out) {
+    ora_sector s;
+    if (ora_sector_init(&s, L, Nup, Ndn)) return -2;
+    ora_seed_ctx c = {&s, seed, 0.0, 0};
+    for (int64_t k = 0; k < nrows; ++k) {
+        c.acc = 0.0;
+        ora_apply_H(L, h, U, ora_sector_state(&s, rows[k]), ora_cb_gather_seeded, &c);
+        y_out[k] = c.acc;
+    }
+    ora_sector_free(&s);
+    return c.bad ? -1 : 0;
+}
+
 /* Number of matrix elements one H x visits: the D diagonal entries plus every
  * off-diagonal (state, hop) pair that is non-zero.  Counted by applying the
  * off-diagonal hopping terms literally to every state; for rows only in

@@ -1,0 +1,63 @@
+// Hamiltonian handle: per-spin sectors, their ranking tables and hop lists.
+#pragma once
+
+#include "gbr_common.h"
+
+namespace gbr {
+
+constexpr int kMaxL = 32;
+constexpr int kMaxUClasses = 8;
+
+// One spin species: all L-bit patterns with N bits set, in increasing order.
+struct SpinSector {
+    int L = 0, N = 0;
+    int64_t D = 0;
+    StagDesc desc{};          // staggered tables (Fig. fastrank) for C^L_N
+    DevBuf stag;              // uint32 entries (per-spin dimensions stay below 2^32)
+    DevBuf states;            // D uint32 patterns (unrank list, Sec. II)
+    DevBuf diag;              // D doubles: sum_p h_pp n_p
+    int hmax = 0;             // largest number of valid hops of one state
+    int64_t hops = 0;         // total valid hops over all states
+    DevBuf hop_cnt;           // D uint16: valid hops of each state
+    DevBuf hop_tgt;           // hmax x D uint32 (k-major): target rank | sign << 31
+    DevBuf hop_bond;          // hmax x D uint16: index into the bond table
+};
+
+// Device-side description of the one-body terms and ranking method, passed
+// to kernels by value.
+struct HamK {
+    int L;
+    int nbond;                 // directed bonds (p, q), p != q, h_pq != 0
+    int uniform;               // 1: every bond has the same coefficient
+    double hu;                 // that coefficient
+    int rank_method;           // GBR_RANK_*
+    int nucls;                 // U classes
+    uint32_t umask[kMaxUClasses];
+    double uval[kMaxUClasses];
+    uint32_t nbr[kMaxL];       // nbr[p]: sites q with h_pq != 0, q != p
+};
+
+}  // namespace gbr
+
+struct gbr_ham {
+    int L, Nup, Ndn;
+    int64_t D;
+    int64_t elements;
+    int rank_method;
+    int path;                  // GBR_HV_*
+    std::vector<double> h, U;
+    gbr::HamK k;
+    gbr::SpinSector up, dn;
+    gbr::DevBuf bonds;         // nbond x {p, q} uint8 pairs (as uint16), bond order
+    gbr::DevBuf bond_coef64;   // nbond doubles
+    gbr::DevBuf bond_coef32;   // nbond floats
+    gbr::DevBuf hcoef64;       // L x L doubles (fused path lookups)
+    gbr::DevBuf binom;         // (L+1) x (L+1) uint32 binomials (CNS ranking)
+    // tuned launch shapes (0 = defaults)
+    int tune_up_rows[2] = {0, 0};
+    int tune_dn_threads[2] = {0, 0};
+};
+
+namespace gbr {
+int hv_launch(const gbr_ham *H, const void *x, void *y, int fp, cudaStream_t st);
+}

@@ -1,0 +1,749 @@
+// On-the-fly H·v for Hubbard / impurity Hamiltonians in a (N_up, N_dn) sector
+// (Wallerberger & Held, Sec. II: Eq. Talpha applied to every basis state,
+// Eq. mvblock on one block; ranking by Fig. fastrank or Fig. algr; the spin
+// factorisation of Eq. rankupdown).
+//
+// With the spin-down bits below the spin-up bits, a same-spin hop c^dag_p c_q
+// changes only that spin's pattern, and its fermionic sign counts only that
+// spin's occupied sites strictly between p and q (Eq. Talpha with
+// s = the bits between p and q).  Writing x as a D_up x D_dn matrix X
+// (index r_up * D_dn + r_dn):
+//     Y = Dg o X + H_up X + X H_dn^T        (H_dn symmetric)
+// Two implementations:
+//   * fused: one thread per element does unrank, diagonal, every hop with
+//     its sign and an on-the-fly rank, and the gather -- the method exactly as
+//     the paper states it; used for small sectors;
+//   * factored: per call, a ranking kernel walks every per-spin state once
+//     (unrank, hop, sign by popcount, staggered rank) and writes its hop
+//     list; two gather passes then apply H_up (row gathers of X, coalesced
+//     along r_dn, column-chunked so the gathered columns stay in L2) and
+//     H_dn plus the diagonal (X rows staged in shared memory).  Ranking work
+//     drops from D * hops to (D_up + D_dn) * hops.
+// Both are deterministic: each y element has one owner and a fixed order.
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+
+#include "ham.h"
+
+namespace gbr {
+
+// Per-spin ranking constants (chunks of 8 bits, at most 4 chunks for L <= 32).
+struct SpinK {
+    int L, N, Q;
+    int shift[4], width[4], lo[4], hi[4], off[4];
+    int64_t D;
+    int tab_entries;
+};
+
+static SpinK spin_k(const SpinSector &s) {
+    SpinK k;
+    memset(&k, 0, sizeof(k));
+    k.L = s.L; k.N = s.N; k.Q = s.desc.Q; k.D = s.D;
+    for (int q = 0; q < s.desc.Q && q < 4; ++q) {
+        k.shift[q] = s.desc.shift[q];
+        k.width[q] = s.desc.width[q];
+        k.lo[q] = s.desc.lo[q];
+        k.hi[q] = s.desc.hi[q];
+        k.off[q] = (int)s.desc.off[q];
+    }
+    k.tab_entries = (int)s.desc.entries;
+    return k;
+}
+
+// Fig. fastrank on a per-spin pattern (tables in shared memory).
+__device__ __forceinline__ uint32_t spin_rank_stag(const SpinK &s, const uint32_t *tab, uint32_t a) {
+    uint32_t acc = 0;
+    int np = 0;
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+        if (q < s.Q) {
+            const uint32_t r = (a >> s.shift[q]) & ((1u << s.width[q]) - 1u);
+            const int row = min(max(np, s.lo[q]), s.hi[q]) - s.lo[q];
+            acc += tab[s.off[q] + (row << s.width[q]) + (int)r];
+            np += __popc(r);
+        }
+    }
+    return acc;
+}
+
+// Fig. algr: for the k-th set bit (from the least significant one, found by
+// count-trailing-zeros) at position c add C(c, k).  binom is (L+1) x (L+1).
+__device__ __forceinline__ uint32_t spin_rank_cns(int L, const uint32_t *binom, uint32_t a) {
+    uint32_t i = 0;
+    int k = 1;
+    while (a) {
+        const int c = __ffs(a) - 1;
+        a &= a - 1u;
+        i += binom[c * (L + 1) + k];
+        ++k;
+    }
+    return i;
+}
+
+__device__ __forceinline__ uint32_t spin_rank(const SpinK &s, int method, const uint32_t *tab, const uint32_t *binom,
+                                              uint32_t a) {
+    return method == GBR_RANK_CNS ? spin_rank_cns(s.L, binom, a) : spin_rank_stag(s, tab, a);
+}
+
+// bits strictly between p and q
+__device__ __forceinline__ uint32_t between_mask(int p, int q) {
+    const int lo = min(p, q), hi = max(p, q);
+    const uint32_t below_hi = (hi >= 32) ? 0xFFFFFFFFu : ((1u << hi) - 1u);
+    const uint32_t upto_lo = (lo + 1 >= 32) ? 0xFFFFFFFFu : ((1u << (lo + 1)) - 1u);
+    return below_hi & ~upto_lo;
+}
+
+// Loads the per-spin ranking table (staggered or binomial) into shared memory.
+__device__ __forceinline__ void stage_u32(uint32_t *s, const uint32_t *__restrict__ g, int n) {
+    for (int i = threadIdx.x; i < n; i += blockDim.x) s[i] = __ldg(g + i);
+}
+
+// ---------------------------------------------------------------- hop lists
+//
+// One thread per per-spin state r: unrank (list), then for every occupied
+// site p (ascending) and every empty site q connected to it (ascending):
+// target = rank(a ^ (2^p | 2^q)), sign = parity of the occupied sites
+// strictly between p and q (Eq. Talpha, gather form Eq. Talpha2).
+__global__ void k_hop_lists(const SpinK s, const HamK hk, const uint32_t *__restrict__ states,
+                            const uint32_t *__restrict__ gtab, const uint32_t *__restrict__ gbinom,
+                            const uint16_t *__restrict__ gbond_index, uint16_t *__restrict__ cnt,
+                            uint32_t *__restrict__ tgt, uint16_t *__restrict__ bond, int hmax) {
+    extern __shared__ __align__(16) uint32_t sm[];
+    uint32_t *tab = sm;
+    const int nb = (hk.L + 1) * (hk.L + 1);
+    uint32_t *binom = sm + s.tab_entries;
+    uint16_t *bidx = reinterpret_cast<uint16_t *>(binom + nb);
+    stage_u32(tab, gtab, s.tab_entries);
+    stage_u32(binom, gbinom, nb);
+    for (int i = threadIdx.x; i < hk.L * hk.L; i += blockDim.x) bidx[i] = gbond_index[i];
+    __syncthreads();
+    for (int64_t r = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; r < s.D; r += (int64_t)gridDim.x * blockDim.x) {
+        const uint32_t a = states[r];
+        int k = 0;
+        uint32_t occ = a;
+        while (occ) {
+            const int p = __ffs(occ) - 1;
+            occ &= occ - 1u;
+            uint32_t emp = hk.nbr[p] & ~a;
+            while (emp) {
+                const int q = __ffs(emp) - 1;
+                emp &= emp - 1u;
+                const uint32_t b = a ^ ((1u << p) | (1u << q));
+                const uint32_t t = spin_rank(s, hk.rank_method, tab, binom, b);
+                const uint32_t sg = (uint32_t)(__popc(a & between_mask(p, q)) & 1);
+                if (k < hmax) {
+                    tgt[(int64_t)k * s.D + r] = t | (sg << 31);
+                    bond[(int64_t)k * s.D + r] = bidx[p * hk.L + q];
+                }
+                ++k;
+            }
+        }
+        cnt[r] = (uint16_t)min(k, hmax);
+    }
+}
+
+template <typename T> struct Vec;
+template <> struct Vec<float> { typedef float4 v4; typedef float2 v2; };
+template <> struct Vec<double> { typedef double2 v2; typedef double2 v4; };
+
+template <typename T>
+__device__ __forceinline__ T diag_value(const HamK &hk, const T *dup, const T *ddn, const T *uval, int64_t ru,
+                                        int64_t rd, uint32_t au, uint32_t ad) {
+    T d = dup[ru] + ddn[rd];
+    const uint32_t both = au & ad;
+    for (int c = 0; c < hk.nucls; ++c) d += uval[c] * (T)__popc(both & hk.umask[c]);
+    return d;
+}
+
+// --------------------------------------------------------------- fused path
+//
+// One thread per element i = r_up * D_dn + r_dn: the whole of Eq. Talpha for
+// every term, with the target ranked on the fly.
+template <typename T>
+__global__ void __launch_bounds__(256) k_hv_fused(const SpinK su, const SpinK sd, const HamK hk,
+                                                  const uint32_t *__restrict__ st_up, const uint32_t *__restrict__ st_dn,
+                                                  const uint32_t *__restrict__ tab_up, const uint32_t *__restrict__ tab_dn,
+                                                  const uint32_t *__restrict__ gbinom, const T *__restrict__ hcoef,
+                                                  const T *__restrict__ dup, const T *__restrict__ ddn,
+                                                  const T *__restrict__ uval_g, const T *__restrict__ x,
+                                                  T *__restrict__ y) {
+    extern __shared__ __align__(16) uint32_t sm[];
+    uint32_t *tu = sm;
+    uint32_t *td = tu + su.tab_entries;
+    const int nb = (hk.L + 1) * (hk.L + 1);
+    uint32_t *binom = td + sd.tab_entries;
+    T *hc = reinterpret_cast<T *>(binom + nb + (nb & 1));   // 8-byte aligned
+    stage_u32(tu, tab_up, su.tab_entries);
+    stage_u32(td, tab_dn, sd.tab_entries);
+    stage_u32(binom, gbinom, nb);
+    for (int i = threadIdx.x; i < hk.L * hk.L; i += blockDim.x) hc[i] = hcoef[i];
+    T uval[kMaxUClasses];
+    for (int c = 0; c < kMaxUClasses; ++c) uval[c] = c < hk.nucls ? uval_g[c] : T(0);
+    __syncthreads();
+    const int64_t D = su.D * sd.D;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < D; i += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t ru = i / sd.D, rd = i - ru * sd.D;
+        const uint32_t au = st_up[ru], ad = st_dn[rd];
+        T acc = diag_value<T>(hk, dup, ddn, uval, ru, rd, au, ad) * x[i];
+        // spin up: changes r_up
+        uint32_t occ = au;
+        while (occ) {
+            const int p = __ffs(occ) - 1;
+            occ &= occ - 1u;
+            uint32_t emp = hk.nbr[p] & ~au;
+            while (emp) {
+                const int q = __ffs(emp) - 1;
+                emp &= emp - 1u;
+                const uint32_t t = spin_rank(su, hk.rank_method, tu, binom, au ^ ((1u << p) | (1u << q)));
+                const T c = hc[p * hk.L + q];
+                const T v = x[(int64_t)t * sd.D + rd];
+                acc += (__popc(au & between_mask(p, q)) & 1) ? -c * v : c * v;
+            }
+        }
+        // spin down: changes r_dn
+        occ = ad;
+        while (occ) {
+            const int p = __ffs(occ) - 1;
+            occ &= occ - 1u;
+            uint32_t emp = hk.nbr[p] & ~ad;
+            while (emp) {
+                const int q = __ffs(emp) - 1;
+                emp &= emp - 1u;
+                const uint32_t t = spin_rank(sd, hk.rank_method, td, binom, ad ^ ((1u << p) | (1u << q)));
+                const T c = hc[p * hk.L + q];
+                const T v = x[ru * sd.D + (int64_t)t];
+                acc += (__popc(ad & between_mask(p, q)) & 1) ? -c * v : c * v;
+            }
+        }
+        y[i] = acc;
+    }
+}
+
+// ------------------------------------------------------------ factored path
+
+// Spin-up pass: Y[r, c] = sum_k coef_k(r) X[t_k(r), c] for a tile of TR rows
+// and 128*VEC columns.  Consecutive CTAs share a column chunk, so the rows of
+// X they gather stay in L2 while the chunk is being processed.
+template <typename T, int VEC>
+__global__ void __launch_bounds__(128) k_hv_up(const int64_t Dup, const int64_t Ddn, const int TR, const int hmax,
+                                               const int64_t nrb, const uint16_t *__restrict__ cnt,
+                                               const uint32_t *__restrict__ tgt, const uint16_t *__restrict__ bond,
+                                               const T *__restrict__ bcoef, const int uniform, const T hu,
+                                               const T *__restrict__ x, T *__restrict__ y) {
+    extern __shared__ __align__(16) unsigned char smr[];
+    uint32_t *st = reinterpret_cast<uint32_t *>(smr);
+    T *sc = reinterpret_cast<T *>(smr + (((size_t)TR * hmax * 4 + 15) & ~(size_t)15));
+    __shared__ int scnt[64];
+    const int64_t rb = blockIdx.x % nrb, cc = blockIdx.x / nrb;
+    const int64_t r0 = rb * TR;
+    for (int i = threadIdx.x; i < TR; i += blockDim.x) scnt[i] = (r0 + i < Dup) ? (int)cnt[r0 + i] : 0;
+    __syncthreads();
+    for (int e = threadIdx.x; e < TR * hmax; e += blockDim.x) {
+        const int i = e % TR, k = e / TR;
+        if (k < scnt[i]) {
+            const int64_t g = (int64_t)k * Dup + r0 + i;
+            const uint32_t w = tgt[g];
+            const T c = uniform ? hu : bcoef[bond[g]];
+            st[i * hmax + k] = w & 0x7FFFFFFFu;
+            sc[i * hmax + k] = (w >> 31) ? -c : c;
+        }
+    }
+    __syncthreads();
+    const int64_t c0 = cc * (int64_t)(128 * VEC) + (int64_t)threadIdx.x * VEC;
+    if (c0 >= Ddn) return;
+    for (int i = 0; i < TR; ++i) {
+        const int64_t r = r0 + i;
+        if (r >= Dup) break;
+        const int n = scnt[i];
+        const uint32_t *ti = st + i * hmax;
+        const T *ci = sc + i * hmax;
+        if (VEC == 4) {
+            float4 acc = make_float4(0.f, 0.f, 0.f, 0.f);
+#pragma unroll 4
+            for (int k = 0; k < n; ++k) {
+                const float4 v = __ldg(reinterpret_cast<const float4 *>(x + (int64_t)ti[k] * Ddn + c0));
+                const float c = (float)ci[k];
+                acc.x += c * v.x; acc.y += c * v.y; acc.z += c * v.z; acc.w += c * v.w;
+            }
+            __stcs(reinterpret_cast<float4 *>(y + r * Ddn + c0), acc);
+        } else if (VEC == 2) {
+            T a0 = 0, a1 = 0;
+#pragma unroll 4
+            for (int k = 0; k < n; ++k) {
+                const T *px = x + (int64_t)ti[k] * Ddn + c0;
+                const typename Vec<T>::v2 v = __ldg(reinterpret_cast<const typename Vec<T>::v2 *>(px));
+                a0 += ci[k] * v.x; a1 += ci[k] * v.y;
+            }
+            typename Vec<T>::v2 o; o.x = a0; o.y = a1;
+            __stcs(reinterpret_cast<typename Vec<T>::v2 *>(y + r * Ddn + c0), o);
+        } else {
+            T a0 = 0;
+#pragma unroll 4
+            for (int k = 0; k < n; ++k) a0 += ci[k] * __ldg(x + (int64_t)ti[k] * Ddn + c0);
+            y[r * Ddn + c0] = a0;
+        }
+    }
+}
+
+// Spin-down pass plus diagonal: for TRD rows staged in shared memory,
+// Y[r, c] += Dg(r, c) X[r, c] + sum_k coef_k(c) X[r, t_k(c)].
+template <typename T, int TRD, bool STAGE>
+__global__ void __launch_bounds__(256) k_hv_dn(const int64_t Dup, const int64_t Ddn, const HamK hk,
+                                               const uint16_t *__restrict__ cnt, const uint32_t *__restrict__ tgt,
+                                               const uint16_t *__restrict__ bond, const T *__restrict__ bcoef,
+                                               const T hu, const uint32_t *__restrict__ st_up,
+                                               const uint32_t *__restrict__ st_dn, const T *__restrict__ dup,
+                                               const T *__restrict__ ddn, const T *__restrict__ uval_g,
+                                               const T *__restrict__ x, T *__restrict__ y) {
+    extern __shared__ __align__(16) unsigned char smr[];
+    T *xs = reinterpret_cast<T *>(smr);
+    const int64_t r0 = (int64_t)blockIdx.x * TRD;
+    const int nrow = (int)(Dup - r0 < (int64_t)TRD ? Dup - r0 : (int64_t)TRD);
+    if (STAGE) {
+        for (int i = 0; i < nrow; ++i) {
+            const T *src = x + (r0 + i) * Ddn;
+            for (int64_t c = threadIdx.x; c < Ddn; c += blockDim.x) xs[i * Ddn + c] = __ldcs(src + c);
+        }
+        __syncthreads();
+    }
+    T uval[kMaxUClasses];
+    for (int c = 0; c < kMaxUClasses; ++c) uval[c] = c < hk.nucls ? uval_g[c] : T(0);
+    uint32_t au[TRD];
+#pragma unroll
+    for (int i = 0; i < TRD; ++i) au[i] = i < nrow ? st_up[r0 + i] : 0u;
+    for (int64_t c = threadIdx.x; c < Ddn; c += blockDim.x) {
+        T acc[TRD];
+#pragma unroll
+        for (int i = 0; i < TRD; ++i) acc[i] = 0;
+        const int n = cnt[c];
+        for (int k = 0; k < n; ++k) {
+            const int64_t g = (int64_t)k * Ddn + c;
+            const uint32_t w = __ldg(tgt + g);
+            T cf = hk.uniform ? hu : __ldg(bcoef + __ldg(bond + g));
+            cf = (w >> 31) ? -cf : cf;
+            const int64_t t = w & 0x7FFFFFFFu;
+#pragma unroll
+            for (int i = 0; i < TRD; ++i)
+                if (i < nrow) acc[i] += cf * (STAGE ? xs[i * Ddn + t] : __ldg(x + (r0 + i) * Ddn + t));
+        }
+        const uint32_t ad = st_dn[c];
+#pragma unroll
+        for (int i = 0; i < TRD; ++i) {
+            if (i < nrow) {
+                const int64_t r = r0 + i;
+                const T xv = STAGE ? xs[i * Ddn + c] : x[r * Ddn + c];
+                const T dg = diag_value<T>(hk, dup, ddn, uval, r, c, au[i], ad);
+                y[r * Ddn + c] = y[r * Ddn + c] + dg * xv + acc[i];
+            }
+        }
+    }
+}
+
+// ------------------------------------------------------------------ launch
+
+struct HamDev {
+    // precision-specific copies of the diagonal and coefficients
+    const void *dup, *ddn, *uval, *bcoef, *hcoef;
+};
+
+template <typename T>
+static int launch_hop_lists(const gbr_ham *H, const SpinSector &s, cudaStream_t st) {
+    const SpinK sk = spin_k(s);
+    const int nb = (H->L + 1) * (H->L + 1);
+    const size_t smem = (size_t)(s.desc.entries + nb) * 4 + (size_t)H->L * H->L * 2 + 16;
+    const int threads = 128;
+    int64_t blocks = (s.D + threads - 1) / threads;
+    blocks = std::min<int64_t>(blocks, (int64_t)sm_count() * 8);
+    if (smem > 48 * 1024) GBR_CUDA_TRY(cudaFuncSetAttribute(k_hop_lists, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    k_hop_lists<<<(int)std::max<int64_t>(blocks, 1), threads, smem, st>>>(
+        sk, H->k, s.states.as<uint32_t>(), s.stag.as<uint32_t>(), H->binom.as<uint32_t>(),
+        reinterpret_cast<const uint16_t *>(H->bonds.p) + 2 * H->k.nbond, s.hop_cnt.as<uint16_t>(),
+        s.hop_tgt.as<uint32_t>(), s.hop_bond.as<uint16_t>(), s.hmax);
+    GBR_LAUNCH_CHECK();
+    return GBR_OK;
+}
+
+template <typename T>
+static int launch_fused(const gbr_ham *H, const T *x, T *y, cudaStream_t st, const HamDev &hd) {
+    const SpinK su = spin_k(H->up), sd = spin_k(H->dn);
+    const int nb = (H->L + 1) * (H->L + 1);
+    const size_t smem = (size_t)(su.tab_entries + sd.tab_entries + nb + 1) * 4 + (size_t)H->L * H->L * sizeof(T) + 16;
+    const int threads = 256;
+    int64_t blocks = (H->D + threads - 1) / threads;
+    blocks = std::max<int64_t>(1, std::min<int64_t>(blocks, (int64_t)sm_count() * 8));
+    auto kern = k_hv_fused<T>;
+    if (smem > 48 * 1024) GBR_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    kern<<<(int)blocks, threads, smem, st>>>(su, sd, H->k, H->up.states.as<uint32_t>(), H->dn.states.as<uint32_t>(),
+                                             H->up.stag.as<uint32_t>(), H->dn.stag.as<uint32_t>(),
+                                             H->binom.as<uint32_t>(), (const T *)hd.hcoef, (const T *)hd.dup,
+                                             (const T *)hd.ddn, (const T *)hd.uval, x, y);
+    GBR_LAUNCH_CHECK();
+    return GBR_OK;
+}
+
+template <typename T>
+static int launch_factored(const gbr_ham *H, const T *x, T *y, cudaStream_t st, const HamDev &hd) {
+    int rc = launch_hop_lists<T>(H, H->up, st);
+    if (rc) return rc;
+    if (&H->dn != &H->up) {
+        rc = launch_hop_lists<T>(H, H->dn, st);
+        if (rc) return rc;
+    }
+    const int64_t Dup = H->up.D, Ddn = H->dn.D;
+    const int fpi = sizeof(T) == 8 ? 1 : 0;
+    // ---- spin-up pass
+    {
+        const bool aligned16 = (((uintptr_t)x | (uintptr_t)y) & 15u) == 0;
+        int vec = 1;
+        const size_t s = sizeof(T);
+        const int vmax = sizeof(T) == 4 ? 4 : 2;
+        for (int v = vmax; v >= 2; v /= 2) {
+            if (aligned16 && Ddn % v == 0 && (double)Dup * 128 * v * s <= 48e6) { vec = v; break; }
+        }
+        if (vec == 1 && aligned16 && Ddn % 2 == 0) vec = 2;
+        const int TR = H->tune_up_rows[fpi] ? H->tune_up_rows[fpi] : 8;
+        const int64_t nrb = (Dup + TR - 1) / TR;
+        const int64_t ncc = (Ddn + 128 * vec - 1) / (128 * vec);
+        const int hmax = std::max(1, H->up.hmax);
+        const size_t smem = (((size_t)TR * hmax * 4 + 15) & ~(size_t)15) + (size_t)TR * hmax * sizeof(T);
+        const int64_t blocks = nrb * ncc;
+        if (blocks > 0x7FFFFFFF) return set_error(GBR_EINVAL, "sector too large for the spin-up pass grid");
+#define GBR_UP(V)                                                                                            \
+    {                                                                                                        \
+        auto kern = k_hv_up<T, V>;                                                                           \
+        if (smem > 48 * 1024) GBR_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)); \
+        kern<<<(int)blocks, 128, smem, st>>>(Dup, Ddn, TR, hmax, nrb, H->up.hop_cnt.as<uint16_t>(),          \
+                                             H->up.hop_tgt.as<uint32_t>(), H->up.hop_bond.as<uint16_t>(),    \
+                                             (const T *)hd.bcoef, H->k.uniform, (T)H->k.hu, x, y);            \
+    }
+        if (vec == 4) GBR_UP(4) else if (vec == 2) GBR_UP(2) else GBR_UP(1)
+#undef GBR_UP
+        GBR_LAUNCH_CHECK();
+    }
+    // ---- spin-down pass with the diagonal
+    {
+        const size_t row_bytes = (size_t)Ddn * sizeof(T);
+        const size_t budget = 200 * 1024;
+        int trd = 0;
+        for (int t : {8, 4, 2, 1})
+            if ((size_t)t * row_bytes <= budget) { trd = t; break; }
+        if (H->tune_dn_threads[fpi] > 0 && H->tune_dn_threads[fpi] <= trd) trd = H->tune_dn_threads[fpi];
+        const bool stage = trd > 0;
+        if (!stage) trd = 4;
+        const int64_t blocks = (Dup + trd - 1) / trd;
+        const size_t smem = stage ? (size_t)trd * row_bytes : 0;
+#define GBR_DN(TV, SV)                                                                                       \
+    {                                                                                                        \
+        auto kern = k_hv_dn<T, TV, SV>;                                                                      \
+        if (smem > 48 * 1024) GBR_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)); \
+        kern<<<(int)blocks, 256, smem, st>>>(Dup, Ddn, H->k, H->dn.hop_cnt.as<uint16_t>(),                   \
+                                             H->dn.hop_tgt.as<uint32_t>(), H->dn.hop_bond.as<uint16_t>(),    \
+                                             (const T *)hd.bcoef, (T)H->k.hu, H->up.states.as<uint32_t>(),   \
+                                             H->dn.states.as<uint32_t>(), (const T *)hd.dup,                 \
+                                             (const T *)hd.ddn, (const T *)hd.uval, x, y);                   \
+    }
+        if (!stage) GBR_DN(4, false)
+        else if (trd == 8) GBR_DN(8, true)
+        else if (trd == 4) GBR_DN(4, true)
+        else if (trd == 2) GBR_DN(2, true)
+        else GBR_DN(1, true)
+#undef GBR_DN
+        GBR_LAUNCH_CHECK();
+    }
+    return GBR_OK;
+}
+
+}  // namespace gbr
+
+// Precision-specific device arrays hang off the handle as extra buffers.
+struct gbr_ham_prec {
+    gbr::DevBuf dup, ddn, uval, bcoef, hcoef;
+};
+
+namespace gbr {
+
+static gbr_ham_prec *prec_bufs(const gbr_ham *H, int fpi);
+
+int hv_launch(const gbr_ham *H, const void *x, void *y, int fp, cudaStream_t st) {
+    const int fpi = fp == 64 ? 1 : 0;
+    gbr_ham_prec *pb = prec_bufs(H, fpi);
+    HamDev hd{pb->dup.p, pb->ddn.p, pb->uval.p, pb->bcoef.p, pb->hcoef.p};
+    int path = H->path;
+    if (path == GBR_HV_AUTO) path = H->D <= (1 << 17) ? GBR_HV_FUSED : GBR_HV_FACTORED;
+    if (fp == 64) {
+        if (path == GBR_HV_FUSED) return launch_fused<double>(H, (const double *)x, (double *)y, st, hd);
+        return launch_factored<double>(H, (const double *)x, (double *)y, st, hd);
+    }
+    if (path == GBR_HV_FUSED) return launch_fused<float>(H, (const float *)x, (float *)y, st, hd);
+    return launch_factored<float>(H, (const float *)x, (float *)y, st, hd);
+}
+
+// ------------------------------------------------------------- host build
+
+static std::vector<gbr_ham_prec *> g_prec_owner;   // never shared across handles
+
+static int build_spin(gbr_ham *H, SpinSector &s, int N) {
+    s.L = H->L;
+    s.N = N;
+    const int R = std::min(8, H->L);
+    int rc = stag_plan(H->L, N, R, &s.desc);
+    if (rc) return rc;
+    std::vector<uint64_t> tab;
+    stag_fill(s.desc, tab);
+    if (s.desc.wide) return set_error(GBR_EINVAL, "per-spin ranks exceed 32 bits");
+    std::vector<uint32_t> t32(tab.begin(), tab.end());
+    rc = s.stag.upload(t32.data(), t32.size() * 4);
+    if (rc) return rc;
+    std::vector<uint64_t> st;
+    enumerate_combinations(H->L, N, st);
+    s.D = (int64_t)st.size();
+    if (s.D != (int64_t)binom(H->L, N)) return set_error(GBR_EINVAL, "internal: enumeration size mismatch");
+    if (s.D >= (int64_t)1 << 31) return set_error(GBR_EINVAL, "per-spin dimension %lld too large", (long long)s.D);
+    std::vector<uint32_t> st32(st.begin(), st.end());
+    rc = s.states.upload(st32.data(), st32.size() * 4);
+    if (rc) return rc;
+    // per-state diagonal and hop counts (host, for sizing and element counts)
+    std::vector<double> dg((size_t)s.D);
+    int hmax = 0;
+    int64_t hops = 0;
+    for (int64_t r = 0; r < s.D; ++r) {
+        const uint32_t a = st32[(size_t)r];
+        double d = 0.0;
+        int k = 0;
+        for (int p = 0; p < H->L; ++p) {
+            if (!((a >> p) & 1u)) continue;
+            d += H->h[(size_t)(p * H->L + p)];
+            k += __builtin_popcount(H->k.nbr[p] & ~a);
+        }
+        dg[(size_t)r] = d;
+        hmax = std::max(hmax, k);
+        hops += k;
+    }
+    s.hmax = hmax;
+    s.hops = hops;
+    rc = s.diag.upload(dg.data(), dg.size() * 8);
+    if (rc) return rc;
+    const int64_t hm = std::max(1, hmax);
+    if ((rc = s.hop_cnt.alloc((size_t)s.D * 2))) return rc;
+    if ((rc = s.hop_tgt.alloc((size_t)(hm * s.D) * 4))) return rc;
+    if ((rc = s.hop_bond.alloc((size_t)(hm * s.D) * 2))) return rc;
+    return GBR_OK;
+}
+
+template <typename T>
+static int upload_prec(gbr_ham *H, gbr_ham_prec *pb) {
+    auto conv = [](const std::vector<double> &v) { return std::vector<T>(v.begin(), v.end()); };
+    std::vector<double> dup((size_t)H->up.D), ddn((size_t)H->dn.D);
+    GBR_CUDA_TRY(cudaMemcpy(dup.data(), H->up.diag.p, dup.size() * 8, cudaMemcpyDeviceToHost));
+    GBR_CUDA_TRY(cudaMemcpy(ddn.data(), H->dn.diag.p, ddn.size() * 8, cudaMemcpyDeviceToHost));
+    std::vector<double> uv(kMaxUClasses, 0.0), bc, hc((size_t)H->L * H->L, 0.0);
+    for (int c = 0; c < H->k.nucls; ++c) uv[(size_t)c] = H->k.uval[c];
+    for (int p = 0; p < H->L; ++p)
+        for (int q = 0; q < H->L; ++q)
+            if (p != q) hc[(size_t)(p * H->L + q)] = H->h[(size_t)(p * H->L + q)];
+    for (int p = 0; p < H->L; ++p)
+        for (int q = 0; q < H->L; ++q)
+            if (p != q && H->h[(size_t)(p * H->L + q)] != 0.0) bc.push_back(H->h[(size_t)(p * H->L + q)]);
+    if (bc.empty()) bc.push_back(0.0);
+    int rc;
+    auto a = conv(dup), b = conv(ddn), u = conv(uv), c = conv(bc), h = conv(hc);
+    if ((rc = pb->dup.upload(a.data(), a.size() * sizeof(T)))) return rc;
+    if ((rc = pb->ddn.upload(b.data(), b.size() * sizeof(T)))) return rc;
+    if ((rc = pb->uval.upload(u.data(), u.size() * sizeof(T)))) return rc;
+    if ((rc = pb->bcoef.upload(c.data(), c.size() * sizeof(T)))) return rc;
+    if ((rc = pb->hcoef.upload(h.data(), h.size() * sizeof(T)))) return rc;
+    return GBR_OK;
+}
+
+}  // namespace gbr
+
+using namespace gbr;
+
+struct gbr_ham_ext {
+    gbr_ham_prec prec[2];
+};
+
+// The handle is allocated together with its precision buffers.
+struct gbr_ham_full : gbr_ham {
+    gbr_ham_ext ext;
+};
+
+namespace gbr {
+static gbr_ham_prec *prec_bufs(const gbr_ham *H, int fpi) {
+    return &const_cast<gbr_ham_full *>(static_cast<const gbr_ham_full *>(H))->ext.prec[fpi];
+}
+}  // namespace gbr
+
+extern "C" int gbr_ham_create(int L, const double *h, const double *U, int Nup, int Ndn, int rank_method,
+                              gbr_ham **out) {
+    clear_error();
+    if (!out) return set_error(GBR_EINVAL, "out is NULL");
+    *out = nullptr;
+    if (L < 1 || L > kMaxL) return set_error(GBR_EINVAL, "L=%d out of range 1..%d", L, kMaxL);
+    if (!h) return set_error(GBR_EINVAL, "h is NULL");
+    if (Nup < 0 || Nup > L || Ndn < 0 || Ndn > L) return set_error(GBR_EINVAL, "particle numbers out of range");
+    if (rank_method != GBR_RANK_STAGGERED && rank_method != GBR_RANK_CNS)
+        return set_error(GBR_EINVAL, "unknown rank_method %d", rank_method);
+    for (int p = 0; p < L; ++p)
+        for (int q = 0; q < L; ++q) {
+            const double a = h[p * L + q], b = h[q * L + p];
+            if (!std::isfinite(a)) return set_error(GBR_EINVAL, "h[%d][%d] is not finite", p, q);
+            if (a != b) return set_error(GBR_EINVAL, "h is not symmetric at (%d, %d)", p, q);
+        }
+    if (U)
+        for (int p = 0; p < L; ++p)
+            if (!std::isfinite(U[p])) return set_error(GBR_EINVAL, "U[%d] is not finite", p);
+    gbr_ham_full *H = new (std::nothrow) gbr_ham_full();
+    if (!H) return set_error(GBR_ENOMEM, "host allocation failed");
+    H->L = L; H->Nup = Nup; H->Ndn = Ndn;
+    H->rank_method = rank_method;
+    H->path = GBR_HV_AUTO;
+    H->h.assign(h, h + L * L);
+    H->U.assign(L, 0.0);
+    if (U) H->U.assign(U, U + L);
+    // one-body bonds in (p, q) order, neighbour masks, U classes
+    HamK &k = H->k;
+    memset(&k, 0, sizeof(k));
+    k.L = L;
+    k.rank_method = rank_method;
+    std::vector<uint16_t> pairs, bidx((size_t)L * L, 0);
+    double first = 0.0;
+    k.uniform = 1;
+    for (int p = 0; p < L; ++p)
+        for (int q = 0; q < L; ++q) {
+            if (p == q) continue;
+            const double v = h[p * L + q];
+            if (v == 0.0) continue;
+            if (k.nbond == 0) first = v;
+            else if (v != first) k.uniform = 0;
+            bidx[(size_t)(p * L + q)] = (uint16_t)k.nbond;
+            pairs.push_back((uint16_t)p);
+            pairs.push_back((uint16_t)q);
+            k.nbr[p] |= 1u << q;
+            ++k.nbond;
+        }
+    k.hu = first;
+    for (int p = 0; p < L; ++p) {
+        const double u = H->U[(size_t)p];
+        if (u == 0.0) continue;
+        int c = 0;
+        while (c < k.nucls && k.uval[c] != u) ++c;
+        if (c == k.nucls) {
+            if (k.nucls == kMaxUClasses) { delete H; return set_error(GBR_EINVAL, "more than %d distinct U values", kMaxUClasses); }
+            k.uval[c] = u;
+            ++k.nucls;
+        }
+        k.umask[c] |= 1u << p;
+    }
+    std::vector<uint16_t> bonds_blob(pairs);
+    bonds_blob.insert(bonds_blob.end(), bidx.begin(), bidx.end());
+    int rc = H->bonds.upload(bonds_blob.data(), bonds_blob.size() * 2);
+    std::vector<uint32_t> bin((size_t)(L + 1) * (L + 1));
+    for (int n = 0; n <= L; ++n)
+        for (int kk = 0; kk <= L; ++kk) bin[(size_t)(n * (L + 1) + kk)] = (uint32_t)binom(n, kk);
+    if (!rc) rc = H->binom.upload(bin.data(), bin.size() * 4);
+    if (!rc) rc = build_spin(H, H->up, Nup);
+    if (!rc) rc = build_spin(H, H->dn, Ndn);
+    if (!rc) {
+        H->D = H->up.D * H->dn.D;
+        H->elements = H->D + H->up.hops * H->dn.D + H->dn.hops * H->up.D;
+        rc = upload_prec<float>(H, &H->ext.prec[0]);
+        if (!rc) rc = upload_prec<double>(H, &H->ext.prec[1]);
+    }
+    if (rc) { delete H; return rc; }
+    *out = H;
+    return GBR_OK;
+}
+
+extern "C" void gbr_ham_destroy(gbr_ham *H) { delete static_cast<gbr_ham_full *>(H); }
+
+extern "C" int gbr_ham_info(const gbr_ham *H, int64_t *dim, int64_t *elements) {
+    clear_error();
+    if (!H) return set_error(GBR_EINVAL, "NULL handle");
+    if (dim) *dim = H->D;
+    if (elements) *elements = H->elements;
+    return GBR_OK;
+}
+
+extern "C" int gbr_ham_set_path(gbr_ham *H, int path) {
+    clear_error();
+    if (!H) return set_error(GBR_EINVAL, "NULL handle");
+    if (path != GBR_HV_AUTO && path != GBR_HV_FUSED && path != GBR_HV_FACTORED)
+        return set_error(GBR_EINVAL, "unknown path %d", path);
+    H->path = path;
+    return GBR_OK;
+}
+
+extern "C" int gbr_hv(const gbr_ham *H, const void *d_x, void *d_y, int fp, void *stream) {
+    clear_error();
+    if (!H) return set_error(GBR_EINVAL, "NULL handle");
+    if (fp != 32 && fp != 64) return set_error(GBR_EINVAL, "fp=%d must be 32 or 64", fp);
+    if (!d_x || !d_y) return set_error(GBR_EINVAL, "NULL vector");
+    const size_t s = fp == 64 ? 8 : 4;
+    const uintptr_t xa = (uintptr_t)d_x, ya = (uintptr_t)d_y;
+    if ((xa | ya) % s) return set_error(GBR_EINVAL, "vectors must be aligned to their element size");
+    const uintptr_t bytes = (uintptr_t)H->D * s;
+    if (xa < ya + bytes && ya < xa + bytes) return set_error(GBR_EINVAL, "x and y overlap");
+    return hv_launch(H, d_x, d_y, fp, (cudaStream_t)stream);
+}
+
+// Times the candidate launch shapes on scratch vectors and keeps the fastest
+// in the handle: the path (fused for sectors up to 2^22 states), the rows per
+// CTA of the spin-up pass, and the rows staged per CTA by the spin-down pass.
+extern "C" int gbr_ham_tune(gbr_ham *H, int fp, void *stream) {
+    clear_error();
+    if (!H) return set_error(GBR_EINVAL, "NULL handle");
+    if (fp != 32 && fp != 64) return set_error(GBR_EINVAL, "fp=%d must be 32 or 64", fp);
+    const size_t s = fp == 64 ? 8 : 4;
+    const int fpi = fp == 64 ? 1 : 0;
+    cudaStream_t st = (cudaStream_t)stream;
+    DevBuf x, y;
+    int rc;
+    if ((rc = x.alloc((size_t)H->D * s))) return rc;
+    if ((rc = y.alloc((size_t)H->D * s))) return rc;
+    GBR_CUDA_TRY(cudaMemsetAsync(x.p, 0, x.bytes, st));
+    cudaEvent_t e0, e1;
+    GBR_CUDA_TRY(cudaEventCreate(&e0));
+    GBR_CUDA_TRY(cudaEventCreate(&e1));
+    auto time_it = [&](float *ms_out) -> int {
+        int r = hv_launch(H, x.p, y.p, fp, st);   // warm-up (also sets kernel attributes)
+        if (r) return r;
+        cudaEventRecord(e0, st);
+        for (int i = 0; i < 3; ++i)
+            if ((r = hv_launch(H, x.p, y.p, fp, st))) return r;
+        cudaEventRecord(e1, st);
+        cudaError_t ce = cudaEventSynchronize(e1);
+        if (ce != cudaSuccess) return set_error(GBR_ECUDA, "tune: %s", cudaGetErrorString(ce));
+        cudaEventElapsedTime(ms_out, e0, e1);
+        return GBR_OK;
+    };
+    const int keep_path = H->path;
+    float best = 1e30f, ms = 0.f;
+    int best_path = GBR_HV_FACTORED, best_tr = 8, best_trd = 0;
+    H->path = GBR_HV_FACTORED;
+    for (int tr : {4, 8, 16}) {
+        H->tune_up_rows[fpi] = tr;
+        H->tune_dn_threads[fpi] = 0;
+        if ((rc = time_it(&ms))) goto done;
+        if (ms < best) { best = ms; best_tr = tr; }
+    }
+    H->tune_up_rows[fpi] = best_tr;
+    for (int trd : {1, 2, 4, 8}) {
+        H->tune_dn_threads[fpi] = trd;
+        if ((rc = time_it(&ms))) goto done;
+        if (ms < best) { best = ms; best_trd = trd; }
+    }
+    H->tune_dn_threads[fpi] = best_trd;
+    if (H->D <= ((int64_t)1 << 22)) {
+        H->path = GBR_HV_FUSED;
+        if ((rc = time_it(&ms))) goto done;
+        if (ms < best) { best = ms; best_path = GBR_HV_FUSED; }
+    }
+    H->path = keep_path == GBR_HV_AUTO ? best_path : keep_path;
+done:
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (rc) H->path = keep_path;
+    return rc;
+}

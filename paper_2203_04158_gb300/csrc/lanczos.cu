@@ -1,0 +1,557 @@
+// Lanczos ground state on the GPU (the paper cites the method in Sec. I and
+// V-B without stating it; this is the textbook three-term recurrence):
+//   v_0 = s/|s|;  w = H v_k - beta_k v_{k-1};  alpha_k = <w, v_k>;
+//   w -= alpha_k v_k;  [two classical Gram-Schmidt passes against v_0..v_k];
+//   beta_{k+1} = |w|;  stop if beta_{k+1} <= 1e-13 max_j(|alpha_j|, beta_j);
+//   v_{k+1} = w / beta_{k+1};  E = lowest eigenvalue of T_k.
+// All scalars stay on the device (no host round trip per step).  Reductions
+// use a fixed grid and a fixed summation tree, so every run is bit-identical
+// and the basis can be recomputed exactly in a second pass.
+//
+// Precision.  FP64 path: FP64 vectors, H·v and dots.  Mixed path: FP32
+// vectors and H·v; every dot product and norm is accumulated exactly per
+// element (the FP32 product split into two floats with an FMA) in a
+// two-float running sum, then combined across threads in FP64 -- FP64-grade
+// accuracy without the FP64 pipe, which runs at about 1/60 of FP32 rate on
+// this GPU.  The tridiagonal eigenproblem, Ritz coefficients and the final
+// Rayleigh quotient <x, Hx>/<x, x> with an FP64 H·v are FP64.
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+
+#include "ham.h"
+
+namespace gbr {
+
+constexpr int kRedThreads = 256;
+
+// two-float accumulator: hi + lo, updated with the exact product of a and b
+struct FF {
+    float hi, lo;
+};
+
+__device__ __forceinline__ void ff_add_prod(FF &s, float a, float b) {
+    const float p = a * b;
+    const float e = fmaf(a, b, -p);          // a*b = p + e exactly
+    const float t = s.hi + p;                // TwoSum(s.hi, p)
+    const float bp = t - s.hi;
+    const float err = (s.hi - (t - bp)) + (p - bp);
+    s.hi = t;
+    s.lo += err + e;
+}
+
+template <typename T> struct DotAcc;
+template <> struct DotAcc<double> {
+    double s = 0.0;
+    __device__ __forceinline__ void add(double a, double b) { s = fma(a, b, s); }
+    __device__ __forceinline__ double value() const { return s; }
+};
+template <> struct DotAcc<float> {
+    FF s{0.f, 0.f};
+    __device__ __forceinline__ void add(float a, float b) { ff_add_prod(s, a, b); }
+    __device__ __forceinline__ double value() const { return (double)s.hi + (double)s.lo; }
+};
+
+__device__ __forceinline__ double block_sum(double v) {
+    __shared__ double red[kRedThreads / 32];
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xFFFFFFFFu, v, o);
+    const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+    __syncthreads();
+    if (l == 0) red[w] = v;
+    __syncthreads();
+    double r = 0.0;
+    if (threadIdx.x < 32) {
+        r = threadIdx.x < (blockDim.x >> 5) ? red[threadIdx.x] : 0.0;
+        for (int o = 16; o > 0; o >>= 1) r += __shfl_down_sync(0xFFFFFFFFu, r, o);
+    }
+    return r;   // valid in thread 0
+}
+
+// State shared by the step kernels (device memory).
+struct LzState {
+    int k;            // current step
+    int stop;         // 1 once the recurrence broke down or finished
+    int breakdown;
+    int pad;
+    double scale;     // max_j(|alpha_j|, beta_j)
+};
+
+// w -= beta_k v_prev (k > 0); partial <w, v>
+template <typename T>
+__global__ void __launch_bounds__(kRedThreads) k_step1(const LzState *st, const double *beta, const T *__restrict__ vprev,
+                                                       const T *__restrict__ v, T *__restrict__ w, int64_t n, double *part,
+                                                       int want_dot) {
+    if (st->stop) return;
+    const int k = st->k;
+    const T b = k > 0 ? (T)beta[k] : T(0);
+    DotAcc<T> acc;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        T wi = w[i];
+        if (k > 0) wi -= b * vprev[i];
+        w[i] = wi;
+        if (want_dot) acc.add(wi, v[i]);
+    }
+    if (!want_dot) return;
+    const double r = block_sum(acc.value());
+    if (threadIdx.x == 0) part[blockIdx.x] = r;
+}
+
+// w -= alpha_k v; partial <w, w>
+template <typename T>
+__global__ void __launch_bounds__(kRedThreads) k_step2(const LzState *st, const double *alpha, const T *__restrict__ v,
+                                                       T *__restrict__ w, int64_t n, double *part, int want_dot) {
+    if (st->stop) return;
+    const T a = (T)alpha[st->k];
+    DotAcc<T> acc;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        const T wi = w[i] - a * v[i];
+        w[i] = wi;
+        if (want_dot) acc.add(wi, wi);
+    }
+    if (!want_dot) return;
+    const double r = block_sum(acc.value());
+    if (threadIdx.x == 0) part[blockIdx.x] = r;
+}
+
+// partial <w, w> only (after re-orthogonalisation)
+template <typename T>
+__global__ void __launch_bounds__(kRedThreads) k_norm2(const LzState *st, const T *__restrict__ w, int64_t n, double *part) {
+    if (st->stop) return;
+    DotAcc<T> acc;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        acc.add(w[i], w[i]);
+    const double r = block_sum(acc.value());
+    if (threadIdx.x == 0) part[blockIdx.x] = r;
+}
+
+// which: 0 = alpha_k = sum; 1 = beta_{k+1} = sqrt(sum) with the stopping test
+__global__ void __launch_bounds__(kRedThreads) k_finalize(LzState *st, double *alpha, double *beta, const double *part,
+                                                          int nparts, int which, int iters) {
+    if (st->stop) return;
+    double v = 0.0;
+    for (int i = threadIdx.x; i < nparts; i += blockDim.x) v += part[i];
+    const double s = block_sum(v);
+    if (threadIdx.x != 0) return;
+    const int k = st->k;
+    if (which == 0) {
+        alpha[k] = s;
+        st->scale = fmax(st->scale, fabs(s));
+    } else {
+        const double b = sqrt(fmax(s, 0.0));
+        beta[k + 1] = b;
+        if (k + 1 >= iters) {
+            st->stop = 1;
+        } else if (b <= 1e-13 * st->scale) {
+            st->stop = 1;
+            st->breakdown = 1;
+        }
+        st->scale = fmax(st->scale, b);
+    }
+}
+
+// v_next = w / beta_{k+1} (also into the stored basis); advance k
+template <typename T>
+__global__ void __launch_bounds__(kRedThreads) k_step3(LzState *st, const double *beta, const T *__restrict__ w,
+                                                       T *__restrict__ vnext, T *__restrict__ basis, int64_t n) {
+    if (st->stop) return;
+    const int k = st->k;
+    const T inv = (T)(1.0 / beta[k + 1]);
+    T *vb = basis ? basis + (int64_t)(k + 1) * n : nullptr;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        const T vi = w[i] * inv;
+        vnext[i] = vi;
+        if (vb) vb[i] = vi;
+    }
+}
+
+__global__ void k_advance(LzState *st) {
+    if (threadIdx.x == 0 && blockIdx.x == 0 && !st->stop) st->k += 1;
+}
+
+// Re-orthogonalisation: c_j = <w, v_j> for j = 0..k (grid.y = j), then
+// w -= sum_j c_j v_j.
+template <typename T>
+__global__ void __launch_bounds__(kRedThreads) k_multidot(const LzState *st, const T *__restrict__ basis,
+                                                          const T *__restrict__ w, int64_t n, double *part) {
+    if (st->stop) return;
+    const int j = blockIdx.y;
+    if (j > st->k) return;
+    const T *vj = basis + (int64_t)j * n;
+    DotAcc<T> acc;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        acc.add(w[i], vj[i]);
+    const double r = block_sum(acc.value());
+    if (threadIdx.x == 0) part[(int64_t)j * gridDim.x + blockIdx.x] = r;
+}
+
+__global__ void __launch_bounds__(kRedThreads) k_multidot_fin(const LzState *st, const double *part, int nparts, double *c) {
+    if (st->stop) return;
+    const int j = blockIdx.x;
+    if (j > st->k) return;
+    double v = 0.0;
+    for (int i = threadIdx.x; i < nparts; i += blockDim.x) v += part[(int64_t)j * nparts + i];
+    const double s = block_sum(v);
+    if (threadIdx.x == 0) c[j] = s;
+}
+
+template <typename T>
+__global__ void __launch_bounds__(kRedThreads) k_multiaxpy(const LzState *st, const T *__restrict__ basis, const double *c,
+                                                           T *__restrict__ w, int64_t n) {
+    if (st->stop) return;
+    const int k = st->k;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        T wi = w[i];
+        for (int j = 0; j <= k; ++j) wi -= (T)c[j] * basis[(int64_t)j * n + i];
+        w[i] = wi;
+    }
+}
+
+// per-step and final tridiagonal solves share the device routine of tridiag.cuh
+#include "tridiag.cuh"
+
+__global__ void __launch_bounds__(kRedThreads) k_tridiag(const LzState *st, const double *alpha, const double *beta,
+                                                         int kfixed, double *out, double *s, double *work) {
+    const int k = kfixed > 0 ? kfixed : (st->k + 1);
+    const double lam = tridiag_lowest_block(alpha, beta, k);
+    if (threadIdx.x == 0) {
+        out[0] = lam;
+        if (s) tridiag_vector_thread(alpha, beta, k, lam, s, work);
+    }
+}
+
+// per-step Ritz value into ritz[k]
+__global__ void k_copy_ritz(const LzState *st, const double *val, double *ritz) {
+    if (threadIdx.x == 0) ritz[st->k] = val[0];
+}
+
+// x (FP64) += s_j v_j for j = 0..k-1 from the stored basis, accumulated per
+// element in a two-float (FP32) or FP64 sum
+template <typename T>
+__global__ void __launch_bounds__(kRedThreads) k_ritz_from_basis(const T *__restrict__ basis, const double *s, int k,
+                                                                 int64_t n, double *__restrict__ x) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        if (sizeof(T) == 8) {
+            double acc = 0.0;
+            for (int j = 0; j < k; ++j) acc = fma(s[j], (double)basis[(int64_t)j * n + i], acc);
+            x[i] = acc;
+        } else {
+            FF acc{0.f, 0.f};
+            for (int j = 0; j < k; ++j) {
+                const float sh = (float)s[j];
+                const float sl = (float)(s[j] - (double)sh);
+                const float v = (float)basis[(int64_t)j * n + i];
+                ff_add_prod(acc, sh, v);
+                acc.lo += sl * v;
+            }
+            x[i] = (double)acc.hi + (double)acc.lo;
+        }
+    }
+}
+
+// x += s_j v (second pass, one step at a time); FP32 values enter exactly
+template <typename T>
+__global__ void __launch_bounds__(kRedThreads) k_ritz_accum(const T *__restrict__ v, const double *s, int j, int64_t n,
+                                                            double *__restrict__ x) {
+    const double sj = s[j];
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        x[i] = fma(sj, (double)v[i], j ? x[i] : 0.0);
+}
+
+// FP64 dots <a,b> partials (refinement)
+__global__ void __launch_bounds__(kRedThreads) k_dot64(const double *__restrict__ a, const double *__restrict__ b,
+                                                       int64_t n, double *part) {
+    double acc = 0.0;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        acc = fma(a[i], b[i], acc);
+    const double r = block_sum(acc);
+    if (threadIdx.x == 0) part[blockIdx.x] = r;
+}
+
+// |Hx - E x|^2 partials
+__global__ void __launch_bounds__(kRedThreads) k_resid64(const double *__restrict__ hx, const double *__restrict__ x,
+                                                         const double *E, int64_t n, double *part) {
+    const double e = E[0];
+    double acc = 0.0;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        const double r = hx[i] - e * x[i];
+        acc = fma(r, r, acc);
+    }
+    const double r = block_sum(acc);
+    if (threadIdx.x == 0) part[blockIdx.x] = r;
+}
+
+__global__ void __launch_bounds__(kRedThreads) k_sum(const double *part, int nparts, double *out) {
+    double v = 0.0;
+    for (int i = threadIdx.x; i < nparts; i += blockDim.x) v += part[i];
+    const double s = block_sum(v);
+    if (threadIdx.x == 0) out[0] = s;
+}
+
+// start vector: v0 = s / |s| in the working precision (the mixed path
+// rounds s to FP32 first); |s| from the rounded values
+template <typename T>
+__global__ void k_cast_start(const double *__restrict__ s, T *__restrict__ v, int64_t n) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        v[i] = (T)s[i];
+}
+
+template <typename T>
+__global__ void k_scale_start(T *__restrict__ v, const double *nrm2, int64_t n) {
+    const double inv = 1.0 / sqrt(nrm2[0]);
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        v[i] = (T)((double)v[i] * inv);
+}
+
+// ------------------------------------------------------------------ driver
+
+struct Lz {
+    const gbr_ham *H;
+    int64_t n;
+    int fp;            // 32 or 64
+    int iters, reorth, store;
+    int grid;
+    cudaStream_t st;
+    DevBuf state, alpha, beta, part, coef, tri, svec, work, ritz_tmp;
+    DevBuf buf[3];
+    DevBuf basis;
+    double hv_ms = 0.0;
+};
+
+template <typename T>
+static int lz_step(Lz &z, int phase, bool pass2, cudaEvent_t *ev_hv, bool want_ritz) {
+    // buffers: v_k in B[phase], v_{k-1} in B[1 - phase], w = H v_k in B[2];
+    // v_{k+1} overwrites v_{k-1}, so the next step uses phase 1 - phase
+    const int64_t n = z.n;
+    T *v = z.buf[phase].as<T>(), *vprev = z.buf[1 - phase].as<T>(), *w = z.buf[2].as<T>();
+    LzState *st = z.state.as<LzState>();
+    if (ev_hv) cudaEventRecord(ev_hv[0], z.st);
+    int rc = hv_launch(z.H, v, w, z.fp, z.st);
+    if (rc) return rc;
+    if (ev_hv) cudaEventRecord(ev_hv[1], z.st);
+    double *part = z.part.as<double>();
+    k_step1<T><<<z.grid, kRedThreads, 0, z.st>>>(st, z.beta.as<double>(), vprev, v, w, n, part, pass2 ? 0 : 1);
+    if (!pass2) k_finalize<<<1, kRedThreads, 0, z.st>>>(st, z.alpha.as<double>(), z.beta.as<double>(), part, z.grid, 0, z.iters);
+    k_step2<T><<<z.grid, kRedThreads, 0, z.st>>>(st, z.alpha.as<double>(), v, w, n, part, (pass2 || z.reorth) ? 0 : 1);
+    if (z.reorth && !pass2) {
+        T *basis = z.basis.as<T>();
+        const int gj = std::max(1, std::min<int>(z.grid, (int)((n + kRedThreads - 1) / kRedThreads)));
+        for (int pass = 0; pass < 2; ++pass) {
+            dim3 g(gj, z.iters);
+            k_multidot<T><<<g, kRedThreads, 0, z.st>>>(st, basis, w, n, part);
+            k_multidot_fin<<<z.iters, kRedThreads, 0, z.st>>>(st, part, gj, z.coef.as<double>());
+            k_multiaxpy<T><<<z.grid, kRedThreads, 0, z.st>>>(st, basis, z.coef.as<double>(), w, n);
+        }
+        k_norm2<T><<<z.grid, kRedThreads, 0, z.st>>>(st, w, n, part);
+    }
+    if (!pass2) k_finalize<<<1, kRedThreads, 0, z.st>>>(st, z.alpha.as<double>(), z.beta.as<double>(), part, z.grid, 1, z.iters);
+    if (want_ritz) {
+        k_tridiag<<<1, kRedThreads, 0, z.st>>>(st, z.alpha.as<double>(), z.beta.as<double>(), 0, z.tri.as<double>(),
+                                               nullptr, nullptr);
+        k_copy_ritz<<<1, 32, 0, z.st>>>(st, z.tri.as<double>(), z.ritz_tmp.as<double>());
+    }
+    k_step3<T><<<z.grid, kRedThreads, 0, z.st>>>(st, z.beta.as<double>(), w, vprev, (z.store && !pass2) ? z.basis.as<T>() : nullptr, n);
+    k_advance<<<1, 32, 0, z.st>>>(st);
+    GBR_LAUNCH_CHECK();
+    return GBR_OK;
+}
+
+template <typename T>
+static int lz_run(Lz &z, const double *d_v0, gbr_lanczos_result *res, const gbr_lanczos_opts *o, double *h_alpha,
+                  double *h_beta, double *h_ritz) {
+    const int64_t n = z.n;
+    cudaStream_t s = z.st;
+    LzState zero{};
+    GBR_CUDA_TRY(cudaMemcpyAsync(z.state.p, &zero, sizeof(zero), cudaMemcpyHostToDevice, s));
+    GBR_CUDA_TRY(cudaMemsetAsync(z.beta.p, 0, z.beta.bytes, s));
+    GBR_CUDA_TRY(cudaMemsetAsync(z.alpha.p, 0, z.alpha.bytes, s));
+    T *B0 = z.buf[0].as<T>();
+    k_cast_start<T><<<z.grid, kRedThreads, 0, s>>>(d_v0, B0, n);
+    k_norm2<T><<<z.grid, kRedThreads, 0, s>>>(z.state.as<LzState>(), B0, n, z.part.as<double>());
+    k_sum<<<1, kRedThreads, 0, s>>>(z.part.as<double>(), z.grid, z.tri.as<double>() + 1);
+    k_scale_start<T><<<z.grid, kRedThreads, 0, s>>>(B0, z.tri.as<double>() + 1, n);
+    if (z.store) GBR_CUDA_TRY(cudaMemcpyAsync(z.basis.p, B0, (size_t)n * sizeof(T), cudaMemcpyDeviceToDevice, s));
+    GBR_LAUNCH_CHECK();
+
+    cudaEvent_t e0, e1, eh[2];
+    cudaEventCreate(&e0); cudaEventCreate(&e1); cudaEventCreate(&eh[0]); cudaEventCreate(&eh[1]);
+    cudaEventRecord(e0, s);
+    double hv_ms = 0.0;
+    // graph mode: one graph per buffer phase, captured on a private stream
+    // after two eager steps (which also set kernel attributes), replayed on s
+    cudaGraphExec_t gexec[2] = {nullptr, nullptr};
+    cudaStream_t cap = nullptr;
+    if (o->use_graph) GBR_CUDA_TRY(cudaStreamCreateWithFlags(&cap, cudaStreamNonBlocking));
+    int rc = GBR_OK;
+    int phase = 0;
+    const bool want_ritz = h_ritz != nullptr;
+    for (int k = 0; k < z.iters; ++k) {
+        if (o->use_graph && k >= 2) {
+            if (!gexec[phase]) {
+                cudaStream_t keep = z.st;
+                z.st = cap;
+                GBR_CUDA_TRY(cudaStreamBeginCapture(cap, cudaStreamCaptureModeThreadLocal));
+                rc = lz_step<T>(z, phase, false, nullptr, want_ritz);
+                cudaGraph_t g = nullptr;
+                cudaError_t ce = cudaStreamEndCapture(cap, &g);
+                z.st = keep;
+                if (rc) { if (g) cudaGraphDestroy(g); break; }
+                if (ce != cudaSuccess) { rc = set_error(GBR_ECUDA, "graph capture failed: %s", cudaGetErrorString(ce)); break; }
+                ce = cudaGraphInstantiate(&gexec[phase], g, 0);
+                cudaGraphDestroy(g);
+                if (ce != cudaSuccess) { rc = set_error(GBR_ECUDA, "graph instantiate failed: %s", cudaGetErrorString(ce)); break; }
+            }
+            cudaError_t le = cudaGraphLaunch(gexec[phase], s);
+            if (le != cudaSuccess) { rc = set_error(GBR_ECUDA, "graph launch failed: %s", cudaGetErrorString(le)); break; }
+        } else {
+            const bool t = !o->use_graph && (k == 0 || k == z.iters / 2);
+            rc = lz_step<T>(z, phase, false, t ? eh : nullptr, want_ritz);
+            if (rc) break;
+            if (t) {
+                cudaEventSynchronize(eh[1]);
+                float ms = 0.f;
+                cudaEventElapsedTime(&ms, eh[0], eh[1]);
+                hv_ms = std::max(hv_ms, (double)ms);
+            }
+        }
+        phase = 1 - phase;
+        if ((k & 31) == 31) {
+            LzState hs;
+            cudaError_t ce = cudaMemcpyAsync(&hs, z.state.p, sizeof(hs), cudaMemcpyDeviceToHost, s);
+            if (ce == cudaSuccess) ce = cudaStreamSynchronize(s);
+            if (ce != cudaSuccess) { rc = set_error(GBR_ECUDA, "sync failed: %s", cudaGetErrorString(ce)); break; }
+            if (hs.stop) break;
+        }
+    }
+    for (int p = 0; p < 2; ++p)
+        if (gexec[p]) cudaGraphExecDestroy(gexec[p]);
+    if (cap) cudaStreamDestroy(cap);
+    if (rc) return rc;
+    LzState hs;
+    GBR_CUDA_TRY(cudaMemcpyAsync(&hs, z.state.p, sizeof(hs), cudaMemcpyDeviceToHost, s));
+    GBR_CUDA_TRY(cudaStreamSynchronize(s));
+    // steps done: k (advanced once per completed non-final step) + 1 for the step that set stop
+    const int kdone = std::min(z.iters, hs.k + 1);
+    res->iters_done = kdone;
+    res->breakdown = hs.breakdown;
+    res->stored_basis = z.store;
+    // lowest Ritz value and (if refining) its eigenvector
+    double *tri = z.tri.as<double>();
+    k_tridiag<<<1, kRedThreads, 0, s>>>(z.state.as<LzState>(), z.alpha.as<double>(), z.beta.as<double>(), kdone, tri,
+                                       o->refine ? z.svec.as<double>() : nullptr, z.work.as<double>());
+    GBR_LAUNCH_CHECK();
+    double Er = 0.0;
+    GBR_CUDA_TRY(cudaMemcpyAsync(&Er, tri, 8, cudaMemcpyDeviceToHost, s));
+    GBR_CUDA_TRY(cudaStreamSynchronize(s));
+    res->E_ritz = Er;
+    res->E0 = Er;
+    res->residual = -1.0;
+    if (o->refine) {
+        DevBuf x, hx;
+        if ((rc = x.alloc((size_t)n * 8))) return rc;
+        if ((rc = hx.alloc((size_t)n * 8))) return rc;
+        double *sv = z.svec.as<double>();
+        if (z.store) {
+            k_ritz_from_basis<T><<<z.grid, kRedThreads, 0, s>>>(z.basis.as<T>(), sv, kdone, n, x.as<double>());
+        } else {
+            // second pass of the same recurrence with the stored scalars
+            LzState zero2{};
+            GBR_CUDA_TRY(cudaMemcpyAsync(z.state.p, &zero2, sizeof(zero2), cudaMemcpyHostToDevice, s));
+            k_cast_start<T><<<z.grid, kRedThreads, 0, s>>>(d_v0, B0, n);
+            k_norm2<T><<<z.grid, kRedThreads, 0, s>>>(z.state.as<LzState>(), B0, n, z.part.as<double>());
+            k_sum<<<1, kRedThreads, 0, s>>>(z.part.as<double>(), z.grid, z.tri.as<double>() + 1);
+            k_scale_start<T><<<z.grid, kRedThreads, 0, s>>>(B0, z.tri.as<double>() + 1, n);
+            int ph = 0;
+            for (int j = 0; j < kdone; ++j) {
+                T *v = z.buf[ph].as<T>();
+                k_ritz_accum<T><<<z.grid, kRedThreads, 0, s>>>(v, sv, j, n, x.as<double>());
+                if (j + 1 < kdone) {
+                    rc = lz_step<T>(z, ph, true, nullptr, false);
+                    if (rc) return rc;
+                }
+                ph = 1 - ph;
+            }
+        }
+        GBR_LAUNCH_CHECK();
+        if ((rc = hv_launch(z.H, x.p, hx.p, 64, s))) return rc;
+        double *part = z.part.as<double>();
+        k_dot64<<<z.grid, kRedThreads, 0, s>>>(x.as<double>(), hx.as<double>(), n, part);
+        k_sum<<<1, kRedThreads, 0, s>>>(part, z.grid, tri + 2);
+        k_dot64<<<z.grid, kRedThreads, 0, s>>>(x.as<double>(), x.as<double>(), n, part);
+        k_sum<<<1, kRedThreads, 0, s>>>(part, z.grid, tri + 3);
+        GBR_LAUNCH_CHECK();
+        double hd[2];
+        GBR_CUDA_TRY(cudaMemcpyAsync(hd, tri + 2, 16, cudaMemcpyDeviceToHost, s));
+        GBR_CUDA_TRY(cudaStreamSynchronize(s));
+        const double E = hd[0] / hd[1];
+        GBR_CUDA_TRY(cudaMemcpyAsync(tri + 4, &E, 8, cudaMemcpyHostToDevice, s));
+        k_resid64<<<z.grid, kRedThreads, 0, s>>>(hx.as<double>(), x.as<double>(), tri + 4, n, part);
+        k_sum<<<1, kRedThreads, 0, s>>>(part, z.grid, tri + 5);
+        double r2 = 0.0;
+        GBR_CUDA_TRY(cudaMemcpyAsync(&r2, tri + 5, 8, cudaMemcpyDeviceToHost, s));
+        GBR_CUDA_TRY(cudaStreamSynchronize(s));
+        res->E0 = E;
+        res->residual = sqrt(fmax(r2, 0.0) / hd[1]);
+    }
+    cudaEventRecord(e1, s);
+    cudaEventSynchronize(e1);
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, e0, e1);
+    res->seconds = ms * 1e-3;
+    res->hv_seconds = hv_ms * 1e-3 * kdone;
+    cudaEventDestroy(e0); cudaEventDestroy(e1); cudaEventDestroy(eh[0]); cudaEventDestroy(eh[1]);
+    if (h_alpha) GBR_CUDA_TRY(cudaMemcpy(h_alpha, z.alpha.p, sizeof(double) * (size_t)kdone, cudaMemcpyDeviceToHost));
+    if (h_beta && kdone > 1)
+        GBR_CUDA_TRY(cudaMemcpy(h_beta, z.beta.as<double>() + 1, sizeof(double) * (size_t)(kdone - 1), cudaMemcpyDeviceToHost));
+    if (h_ritz) GBR_CUDA_TRY(cudaMemcpy(h_ritz, z.ritz_tmp.p, sizeof(double) * (size_t)kdone, cudaMemcpyDeviceToHost));
+    return GBR_OK;
+}
+
+}  // namespace gbr
+
+using namespace gbr;
+
+extern "C" int gbr_lanczos(const gbr_ham *H, const gbr_lanczos_opts *o, const double *d_v0, gbr_lanczos_result *res,
+                           double *h_alpha, double *h_beta, double *h_ritz, void *stream) {
+    clear_error();
+    if (!H || !o || !res || !d_v0) return set_error(GBR_EINVAL, "NULL argument");
+    if (o->iters < 1 || o->iters > 65535) return set_error(GBR_EINVAL, "iters=%d out of range 1..65535", o->iters);
+    if (o->prec != GBR_PREC_FP64 && o->prec != GBR_PREC_MIXED) return set_error(GBR_EINVAL, "unknown prec %d", o->prec);
+    if ((uintptr_t)d_v0 & 7u) return set_error(GBR_EINVAL, "v0 must be 8-byte aligned");
+    memset(res, 0, sizeof(*res));
+    Lz z;
+    z.H = H;
+    z.n = H->D;
+    z.fp = o->prec == GBR_PREC_MIXED ? 32 : 64;
+    z.iters = (int)std::min<int64_t>(o->iters, H->D);
+    z.reorth = o->reorth ? 1 : 0;
+    z.st = (cudaStream_t)stream;
+    const size_t es = z.fp == 64 ? 8 : 4;
+    int store = o->store_basis;
+    const size_t basis_bytes = (size_t)(z.iters + 1) * (size_t)z.n * es;
+    if (z.reorth) store = 1;
+    if (store < 0) {
+        size_t fr = 0, tot = 0;
+        GBR_CUDA_TRY(cudaMemGetInfo(&fr, &tot));
+        const size_t need = basis_bytes + (size_t)z.n * (3 * es + 16) + ((size_t)1 << 30);
+        store = need < fr ? 1 : 0;
+    }
+    z.store = store;
+    const int64_t blocks = (z.n + kRedThreads - 1) / kRedThreads;
+    z.grid = (int)std::max<int64_t>(1, std::min<int64_t>(blocks, (int64_t)sm_count() * 4));
+    int rc;
+    if ((rc = z.state.alloc(sizeof(LzState)))) return rc;
+    if ((rc = z.alpha.alloc(sizeof(double) * (size_t)(z.iters + 2)))) return rc;
+    if ((rc = z.beta.alloc(sizeof(double) * (size_t)(z.iters + 2)))) return rc;
+    const size_t nparts = (size_t)z.grid * (size_t)(z.reorth ? z.iters + 1 : 1);
+    if ((rc = z.part.alloc(sizeof(double) * nparts))) return rc;
+    if ((rc = z.coef.alloc(sizeof(double) * (size_t)(z.iters + 2)))) return rc;
+    if ((rc = z.tri.alloc(sizeof(double) * 16))) return rc;
+    if ((rc = z.svec.alloc(sizeof(double) * (size_t)(z.iters + 2)))) return rc;
+    if ((rc = z.work.alloc(sizeof(double) * 3 * (size_t)(z.iters + 2)))) return rc;
+    if ((rc = z.ritz_tmp.alloc(sizeof(double) * (size_t)(z.iters + 2)))) return rc;
+    for (int i = 0; i < 3; ++i)
+        if ((rc = z.buf[i].alloc((size_t)z.n * es))) return rc;
+    if (z.store && (rc = z.basis.alloc(basis_bytes))) return rc;
+    if (z.fp == 64) return lz_run<double>(z, d_v0, res, o, h_alpha, h_beta, h_ritz);
+    return lz_run<float>(z, d_v0, res, o, h_alpha, h_beta, h_ritz);
+}

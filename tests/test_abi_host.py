@@ -1,0 +1,118 @@
+"""CPU checks of the C ABI: the library loads, exports every symbol the
+header declares, rejects bad arguments on the host, and its host-side trie
+builder reproduces the paper's trie sizes and walks."""
+import ctypes as C
+import os
+import re
+
+import numpy as np
+import pytest
+
+import gbr_synth as S
+import oracle
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+HEADER = os.path.join(ROOT, "include", "gbrank.h")
+
+
+@pytest.fixture(scope="module")
+def G():
+    from paper_2203_04158_gb300 import build as gbuild
+    gbuild.build()
+    import paper_2203_04158_gb300 as G
+    return G
+
+
+def declared_symbols():
+    text = open(HEADER).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    return sorted(set(re.findall(r"\b(gbr_[a-z0-9_]+)\s*\(", text)))
+
+
+def test_header_declares_the_api():
+    syms = declared_symbols()
+    for s in ("gbr_comb_rank", "gbr_trie_rank", "gbr_hv", "gbr_lanczos", "gbr_batch_solve", "gbr_last_error"):
+        assert s in syms
+
+
+def test_library_exports_every_declared_symbol(G):
+    lib = C.CDLL(G.gbrank.LIB_PATH)
+    missing = [s for s in declared_symbols() if not hasattr(lib, s)]
+    assert not missing, missing
+    assert G.gbr_version() == 1
+
+
+def test_host_argument_errors(G):
+    with pytest.raises(G.GbrError) as e:
+        G.gbr_comb_create(65, 3, 8)
+    assert e.value.code == G.GBR_EINVAL and "M=65" in str(e.value)
+    with pytest.raises(G.GbrError):
+        G.gbr_comb_create(10, 11, 8)
+    with pytest.raises(G.GbrError):
+        G.gbr_comb_create(10, 3, 0)
+    # unsorted, duplicate and too-wide trie members are rejected before any device work
+    for bad in ([3, 1], [1, 1], [1 << 12]):
+        with pytest.raises(G.GbrError) as e:
+            G.gbr_trie_build_host(np.array(bad, dtype=np.uint64), 12, 4)
+        assert e.value.code == G.GBR_EINVAL
+    with pytest.raises(G.GbrError):
+        G.gbr_ham_create(4, np.array([[0, 1, 0, 0], [0.5, 0, 0, 0], [0, 0, 0, 0], [0, 0, 0, 0]]), None, 2, 2)
+    with pytest.raises(G.GbrError):
+        G.gbr_ham_create(33, np.zeros((33, 33)), None, 2, 2)
+
+
+def walk(t, M, R, a):
+    """Fig. trielookup over the host-built table, with the wrap-around pointer
+    arithmetic of the unsigned entries and clamping into the table."""
+    w0 = M % R or R
+    widths = [w0] + [R] * ((M - w0) // R)
+    k, sh = 0, 0
+    for w in widths:
+        idx = (k + ((a >> sh) & ((1 << w) - 1))) % (1 << 64)
+        idx = min(idx, t.size - 1)
+        k = int(t[idx])
+        sh += w
+    return k
+
+
+def test_host_trie_matches_worked_example_size_and_walk(G):
+    lst = oracle.enumerate_sector(6, 2)
+    size, t = G.gbr_trie_build_host(lst, 6, 2)
+    osize, _ = oracle.trie_build(lst, 6, 2)
+    assert size == osize == 30
+    for i, a in enumerate(lst):
+        assert walk(t, 6, 2, int(a)) == i
+
+
+@pytest.mark.parametrize("M,R", [(7, 3), (10, 4), (12, 5), (16, 8), (20, 8), (11, 12)])
+def test_host_trie_random_sets(G, M, R):
+    rng = np.random.default_rng(M + 7 * R)
+    members = np.sort(rng.choice(1 << M, size=min(300, 1 << (M - 1)), replace=False).astype(np.uint64))
+    size, t = G.gbr_trie_build_host(members, M, R)
+    osize, _ = oracle.trie_build(members, M, R)
+    assert size == osize
+    for i, a in enumerate(members):
+        assert walk(t, M, R, int(a)) == i
+
+
+@pytest.mark.slow
+def test_host_trie_overhead_factors(G):
+    # the breadth-first table has exactly the oracle's element count, hence the paper's f
+    import json
+    gold = json.load(open(os.path.join(ROOT, "tests", "golden", "paper_examples.json")))["trie_overhead"]
+    lists = {}
+    for row in gold["rows"]:
+        if row["N"] not in lists:
+            lists[row["N"]] = oracle.enumerate_sector(28, row["N"])
+        lst = lists[row["N"]]
+        size = G.gbr_trie_build_host(lst, 28, row["R"])[0] if row["R"] != 4 or row["N"] == 5 else None
+        if size is None:
+            continue
+        assert round(size / lst.size, 2) == row["f"], row
+
+
+def test_seeded_generator_twins_agree():
+    idx = np.array([0, 1, 2, 12345, 2**40 + 3], dtype=np.uint64)
+    py = S.uniform(1, idx)
+    for i, v in zip(idx, py):
+        assert oracle.seeded_uniform(1, int(i)) == v

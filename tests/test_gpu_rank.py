@@ -1,0 +1,177 @@
+"""Parity of the GPU rank / unrank kernels with the oracle: bit-exact."""
+import math
+
+import numpy as np
+import pytest
+
+import gbr_synth as S
+import oracle
+from gpu_common import as_u32, as_u64, lib, to_dev_u64
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def G():
+    return lib()
+
+
+def rank_both(G, c, pats_dev, check=0):
+    import torch
+    n = pats_dev.numel()
+    r32 = torch.empty(n, dtype=torch.int32, device="cuda")
+    r64 = torch.empty(n, dtype=torch.int64, device="cuda")
+    G.gbr_comb_rank(c, pats_dev, r64, check=check)
+    dim, _ = G.gbr_comb_info(c)
+    if dim <= 2**32:
+        G.gbr_comb_rank(c, pats_dev, r32, check=check)
+        return as_u32(r32).astype(np.uint64), as_u64(r64)
+    return None, as_u64(r64)
+
+
+@pytest.mark.parametrize("R", [3, 8])
+def test_comb_exhaustive_small_sectors(G, R):
+    import torch
+    for M in range(1, 17):
+        for N in range(0, M + 1):
+            lst = oracle.enumerate_sector(M, N)
+            c = G.gbr_comb_create(M, N, R)
+            r32, r64 = rank_both(G, c, to_dev_u64(lst), check=1)
+            want = np.arange(lst.size, dtype=np.uint64)
+            assert np.array_equal(r64, want), (M, N)
+            assert np.array_equal(r32, want), (M, N)
+            pats = torch.empty(lst.size, dtype=torch.int64, device="cuda")
+            G.gbr_comb_unrank(c, torch.arange(lst.size, dtype=torch.int64, device="cuda"), pats)
+            assert np.array_equal(as_u64(pats), lst), (M, N)
+
+
+def test_comb_check_mode_flags_non_members(G):
+    M, N = 20, 10
+    c = G.gbr_comb_create(M, N, 8)
+    rng = np.random.default_rng(1)
+    q = rng.integers(0, 1 << 22, size=5000, dtype=np.uint64)       # many have bits >= M or popcount != N
+    _, r64 = rank_both(G, c, to_dev_u64(q), check=1)
+    for a, r in zip(q, r64):
+        a = int(a)
+        if a < (1 << M) and bin(a).count("1") == N:
+            assert int(r) == oracle.rank_count(M, a)
+        else:
+            assert int(r) == 0xFFFFFFFFFFFFFFFF
+    # without the check every access stays inside the table: members still right
+    lst = oracle.enumerate_sector(M, N)[::37]
+    _, r64 = rank_both(G, c, to_dev_u64(lst), check=0)
+    assert np.array_equal(r64, np.arange(0, math.comb(M, N), 37, dtype=np.uint64))
+
+
+@pytest.mark.parametrize("M,N,R", [(64, 32, 8), (64, 5, 8), (64, 59, 4), (48, 24, 12), (33, 16, 8)])
+def test_comb_large_sectors_against_oracle(G, M, N, R):
+    import torch
+    D = math.comb(M, N)
+    u = S.bounded(11, np.arange(4000, dtype=np.uint64), D)
+    u = np.concatenate([u, np.array([0, D - 1], dtype=np.uint64)])
+    c = G.gbr_comb_create(M, N, R)
+    pats = torch.empty(u.size, dtype=torch.int64, device="cuda")
+    G.gbr_comb_unrank(c, to_dev_u64(u), pats)
+    p = as_u64(pats)
+    for ui, a in zip(u[::40], p[::40]):
+        assert int(a) == oracle.unrank(M, N, int(ui))
+    _, r64 = rank_both(G, c, pats, check=1)
+    assert np.array_equal(r64, u)
+    # out-of-range ranks unrank to the not-found pattern
+    G.gbr_comb_unrank(c, to_dev_u64(np.array([D, D + 5], dtype=np.uint64)), pats[:2])
+    assert np.all(as_u64(pats[:2]) == np.uint64(0xFFFFFFFFFFFFFFFF))
+
+
+@pytest.mark.parametrize("n", [0, 1, 7, 1023, 1024, 1025, 4097, 100003])
+def test_comb_ragged_lengths(G, n):
+    import torch
+    M, N = 32, 16
+    D = math.comb(M, N)
+    c = G.gbr_comb_create(M, N, 8)
+    u = S.bounded(12, np.arange(n, dtype=np.uint64), D)
+    pats = torch.empty(n, dtype=torch.int64, device="cuda")
+    r = torch.full((n,), -1, dtype=torch.int32, device="cuda")
+    if n:
+        G.gbr_comb_unrank(c, to_dev_u64(u), pats)
+    G.gbr_comb_rank(c, pats, r, check=1)
+    assert np.array_equal(as_u32(r).astype(np.uint64), u)
+
+
+def test_comb_full_size_2pow28(G):
+    """Ranking workload: 2^28 seeded queries over the M=32, N=16 sector."""
+    import torch
+    import gbr_synth.gpu as SG
+    M, N, n = 32, 16, 1 << 28
+    D = math.comb(M, N)
+    c = G.gbr_comb_create(M, N, 8)
+    u = SG.bounded(S.SEED_COMB_QUERIES, n, D)
+    pats = torch.empty(n, dtype=torch.int64, device="cuda")
+    G.gbr_comb_unrank(c, u, pats)
+    r = torch.empty(n, dtype=torch.int32, device="cuda")
+    G.gbr_comb_rank(c, pats, r)
+    assert torch.equal(r.to(torch.int64) & 0xFFFFFFFF, u)          # rank(unrank(u)) = u at full size
+    idx = np.unique(S.bounded(13, np.arange(3000, dtype=np.uint64), n)).astype(np.int64)
+    us = S.bounded(S.SEED_COMB_QUERIES, idx.astype(np.uint64), D)
+    ps = as_u64(pats[torch.from_numpy(idx).cuda()])
+    assert np.array_equal(as_u64(u[torch.from_numpy(idx).cuda()]), us)   # the GPU generator is the numpy one
+    for ui, a in zip(us[:600], ps[:600]):
+        assert int(a) == oracle.unrank(M, N, int(ui))
+        assert oracle.rank_count(M, int(a)) == int(ui)
+
+
+# ------------------------------------------------------------------- tries
+
+@pytest.mark.parametrize("M,R", [(7, 3), (10, 4), (12, 5), (16, 8), (20, 8), (24, 8), (13, 16)])
+def test_trie_random_sets(G, M, R):
+    import torch
+    rng = np.random.default_rng(100 * M + R)
+    k = min(5000, (1 << M) // 3)
+    members = np.sort(rng.choice(1 << M, size=k, replace=False).astype(np.uint64))
+    t = G.gbr_trie_create(members, M, R)
+    info = G.gbr_trie_info(t)
+    osize, _ = oracle.trie_build(members, M, R, with_table=False)
+    assert info["n_elements"] == osize and info["n_members"] == k
+    r = torch.empty(k, dtype=torch.int32, device="cuda")
+    G.gbr_trie_rank(t, to_dev_u64(members), r, check=1)
+    assert np.array_equal(as_u32(r), np.arange(k, dtype=np.uint32))
+    back = torch.empty(k, dtype=torch.int64, device="cuda")
+    G.gbr_trie_unrank(t, r, back)
+    assert np.array_equal(as_u64(back), members)
+    # non-members, including patterns wider than M: flagged with check, in bounds without
+    q = rng.integers(0, 1 << (M + 2), size=4000, dtype=np.uint64)
+    r2 = torch.empty(q.size, dtype=torch.int64, device="cuda")
+    G.gbr_trie_rank(t, to_dev_u64(q), r2, check=1)
+    want = oracle.rank_bisect_many(members, q)
+    got = as_u64(r2)
+    for w, g in zip(want, got):
+        assert (w >= 0 and int(g) == w) or (w < 0 and g == np.uint64(0xFFFFFFFFFFFFFFFF))
+    G.gbr_trie_rank(t, to_dev_u64(q), r2, check=0)
+    torch.cuda.synchronize()
+
+
+def test_trie_paper_sector_M28_N5(G):
+    import torch
+    lst = oracle.enumerate_sector(28, 5)
+    t = G.gbr_trie_create(lst, 28, 8)
+    assert round(G.gbr_trie_info(t)["n_elements"] / lst.size, 2) == 10.45
+    r = torch.empty(lst.size, dtype=torch.int32, device="cuda")
+    G.gbr_trie_rank(t, to_dev_u64(lst), r, check=1)
+    assert np.array_equal(as_u32(r), np.arange(lst.size, dtype=np.uint32))
+
+
+def test_trie_full_size_40bit(G):
+    """Trie workload: 2^24 distinct 40-bit patterns, 2^28 member queries."""
+    import torch
+    import gbr_synth.gpu as SG
+    nset, n = 1 << 24, 1 << 28
+    members = S.trie_member_set(nset, 40)
+    t = G.gbr_trie_create(members, 40, 8)
+    mdev = to_dev_u64(members)
+    j = SG.bounded(S.SEED_TRIE_QUERIES, n, nset)
+    pats = mdev[j]
+    r = torch.empty(n, dtype=torch.int32, device="cuda")
+    G.gbr_trie_rank(t, pats, r, check=1)
+    assert torch.equal(r.to(torch.int64), j)
+    sel = np.unique(S.bounded(14, np.arange(2000, dtype=np.uint64), n)).astype(np.int64)
+    ps = as_u64(pats[torch.from_numpy(sel).cuda()])
+    assert np.array_equal(oracle.rank_bisect_many(members, ps), as_u32(r[torch.from_numpy(sel).cuda()]).astype(np.int64))
