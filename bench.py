@@ -1,0 +1,379 @@
+#!/usr/bin/env python
+"""Benchmark of the on-the-fly H·v / Lanczos hot path on one GB300 per rank.
+
+Workload (default): the 4x4 Hubbard torus with diagonal hopping, t = 1,
+t' = -0.3, U = 8, N_up = N_dn = 7 (1.31e8 states, 8.93e9 matrix elements per
+H·v).  One step is one complete mixed-precision ground-state solve through
+the public API: 200 Lanczos steps with FP32 vectors and FP32 on-the-fly H·v
+(unrank, hop, sign, staggered rank, gather), FP64-grade scalars, the FP64
+tridiagonal eigenpair, the Ritz vector and its FP64 H·v Rayleigh quotient.
+The metric is H·v matrix elements per second over the whole step.
+
+Also reported (outside the timed steps): the all-FP64 GPU solve of the same
+sector for the mixed-vs-FP64 comparison, and ranks/s of the staggered and
+trie ranking kernels on their full-size workloads.
+
+``--impl reference`` times the CPU oracle on a bounded sample of the same
+workload (rank 0 only).  With torchrun (N > 1) every rank solves its own
+replica: the path has no exchange step on one node, so scaling is weak.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "H·v matrix elements/s"
+UNIT = "elements/s"
+WORKLOAD = "hubbard_4x4_tp_mixed_lanczos"
+L, NUP, NDN, UVAL, TP, ITERS = 16, 7, 7, 8.0, -0.3, 200
+
+
+def peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        d = json.load(open(p))
+        return float(d["hbm_gbs"]), "measured"
+    return 6800.0, "fallback"
+
+
+class Clocks:
+    """Samples SM clocks and throttle reasons with nvidia-smi while running."""
+
+    def __init__(self, index: int):
+        self.index = index
+        self.samples = []
+        self._stop = threading.Event()
+        self._t = None
+
+    def _run(self):
+        q = ("clocks.sm,clocks.max.sm,clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+        while not self._stop.is_set():
+            try:
+                out = subprocess.run(["nvidia-smi", "-i", str(self.index), f"--query-gpu={q}",
+                                      "--format=csv,noheader,nounits"], capture_output=True, text=True, timeout=5)
+                f = [x.strip() for x in out.stdout.strip().split(",")]
+                if len(f) == 6:
+                    self.samples.append(f)
+            except Exception:
+                pass
+            self._stop.wait(0.2)
+
+    def __enter__(self):
+        self._t = threading.Thread(target=self._run, daemon=True)
+        self._t.start()
+        return self
+
+    def __exit__(self, *a):
+        self._stop.set()
+        self._t.join(timeout=10)
+
+    def summary(self):
+        if not self.samples:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+        sm = [float(s[0]) for s in self.samples if s[0].replace(".", "").isdigit()]
+        mx = [float(s[1]) for s in self.samples if s[1].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for s in self.samples for i in range(4) if s[2 + i].lower() == "active"})
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": reasons, "samples": len(self.samples)}
+
+
+def model():
+    import gbr_synth as S
+    return S.square(4, 4, 1.0, TP), S.uniform_U(L, UVAL)
+
+
+def src_hash():
+    h = hashlib.sha256()
+    for f in ("hv.cu", "ham.h"):
+        h.update(open(os.path.join(ROOT, "paper_2203_04158_gb300", "csrc", f), "rb").read())
+    return h.hexdigest()[:16]
+
+
+def ncu_traffic(kernel: str):
+    """DRAM bytes per launch of the kernel from the committed ncu summary, or
+    None if there is none or the kernel source changed since it was taken."""
+    p = os.path.join(ROOT, "profiles", "ncu_counters.json")
+    if not os.path.exists(p):
+        return None
+    d = json.load(open(p))
+    e = d.get(WORKLOAD, {}).get(kernel)
+    if not e or e.get("src_hash") != src_hash():
+        return None
+    return e.get("dram_bytes_per_launch_full_size")
+
+
+# --------------------------------------------------------------------- oracle
+
+def oracle_sample(seconds: float):
+    """Times the CPU oracle's H·v on a contiguous block of rows of the sector,
+    sized to take about ``seconds``.  Returns (elements/s, description)."""
+    import numpy as np
+    import gbr_synth as S
+    import oracle
+    h, U = model()
+    D = oracle.sector_dim(L, NUP, NDN)
+    r0 = D // 3
+    n = 2000
+    while True:
+        rows = np.arange(r0, r0 + n, dtype=np.int64)
+        t0 = time.perf_counter()
+        oracle.hv_rows_seeded(L, h, U, NUP, NDN, S.SEED_START, rows)
+        dt = time.perf_counter() - t0
+        if dt >= 0.5 * seconds or n >= D - r0:
+            break
+        n = min(D - r0, int(n * max(2.0, 1.2 * seconds / max(dt, 1e-3))))
+    elems = oracle.count_elements(L, h, NUP, NDN, r0, r0 + n)
+    desc = (f"rows [{r0}, {r0 + n}) of the 4x4 sector: {elems} matrix elements by literal operator "
+            f"application (Eq. cee) with bisection ranking, single thread, {dt:.1f} s")
+    return elems / dt, desc, dt
+
+
+def run_reference(args, rank: int):
+    if rank != 0:
+        return
+    vals, descs = [], []
+    for _ in range(args.warmup):
+        oracle_sample(2.0)
+    for _ in range(args.steps):
+        v, d, dt = oracle_sample(args.cpu_seconds / max(1, args.steps))
+        vals.append(v)
+        descs.append(d)
+    v = statistics.median(vals)
+    line = {"metric": METRIC, "value": v, "unit": UNIT, "impl": "reference", "n_gpus": 0, "steps": args.steps,
+            "warmup": args.warmup, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "f64", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "dim": math.comb(16, 7) ** 2},
+            "cpu_baseline": {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": descs[-1]},
+            "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+# ------------------------------------------------------------------------ GPU
+
+def ranking_extras(G, torch):
+    """Full-size ranking workloads, timed with CUDA events (outside the steps)."""
+    import numpy as np
+    import gbr_synth as S
+    import gbr_synth.gpu as SG
+    out = {}
+    hbm, _ = peaks()
+    n = 1 << 28
+    D = math.comb(32, 16)
+    c = G.gbr_comb_create(32, 16, 8)
+    u = SG.bounded(S.SEED_COMB_QUERIES, n, D)
+    pats = torch.empty(n, dtype=torch.int64, device="cuda")
+    G.gbr_comb_unrank(c, u, pats)
+    del u
+    r = torch.empty(n, dtype=torch.int32, device="cuda")
+    for _ in range(3):
+        G.gbr_comb_rank(c, pats, r)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    reps = 10
+    e0.record()
+    for _ in range(reps):
+        G.gbr_comb_rank(c, pats, r)
+    e1.record()
+    torch.cuda.synchronize()
+    t = e0.elapsed_time(e1) / 1e3 / reps
+    out["staggered_M32_N16"] = {"queries": n, "ranks_per_s": n / t, "ms": t * 1e3,
+                                "GBs": 12 * n / t / 1e9, "frac_of_hbm": 12 * n / t / 1e9 / hbm}
+    ps, _ = torch.sort(pats)
+    G.gbr_comb_rank(c, ps, r)
+    e0.record()
+    for _ in range(reps):
+        G.gbr_comb_rank(c, ps, r)
+    e1.record()
+    torch.cuda.synchronize()
+    t = e0.elapsed_time(e1) / 1e3 / reps
+    out["staggered_M32_N16_sorted"] = {"ranks_per_s": n / t, "ms": t * 1e3}
+    del pats, ps, r
+    members = S.trie_member_set(1 << 24, 40)
+    tr = G.gbr_trie_create(members, 40, 8)
+    info = G.gbr_trie_info(tr)
+    mdev = torch.from_numpy(members.view(np.int64)).cuda()
+    j = SG.bounded(S.SEED_TRIE_QUERIES, n, 1 << 24)
+    q = mdev[j]
+    del j
+    r = torch.empty(n, dtype=torch.int32, device="cuda")
+    G.gbr_trie_rank(tr, q, r)
+    reps = 5
+    e0.record()
+    for _ in range(reps):
+        G.gbr_trie_rank(tr, q, r)
+    e1.record()
+    torch.cuda.synchronize()
+    t = e0.elapsed_time(e1) / 1e3 / reps
+    out["trie_40bit_2p24"] = {"queries": n, "ranks_per_s": n / t, "ms": t * 1e3,
+                              "overhead_f": info["n_elements"] / info["n_members"], "levels": info["levels"]}
+    qs, _ = torch.sort(q)
+    G.gbr_trie_rank(tr, qs, r)
+    e0.record()
+    for _ in range(reps):
+        G.gbr_trie_rank(tr, qs, r)
+    e1.record()
+    torch.cuda.synchronize()
+    t = e0.elapsed_time(e1) / 1e3 / reps
+    out["trie_40bit_2p24_sorted"] = {"ranks_per_s": n / t, "ms": t * 1e3}
+    del q, qs, r, mdev, tr
+    torch.cuda.empty_cache()
+    return out
+
+
+def run_ours(args, rank: int, world: int):
+    import numpy as np
+    import torch
+    import __graft_entry__
+    if rank == 0 or world == 1:
+        __graft_entry__.build()
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+    import gbr_synth as S
+    import gbr_synth.gpu as SG
+    import paper_2203_04158_gb300 as G
+
+    dev = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(dev)
+    h, U = model()
+    H = G.gbr_ham_create(L, h, U, NUP, NDN)
+    D, elems = G.gbr_ham_info(H)
+    s = SG.uniform(S.SEED_START, D)
+
+    def solve(prec=G.GBR_PREC_MIXED, profile=True, refine=True):
+        return G.gbr_lanczos(H, s, ITERS, prec=prec, refine=refine, store_basis=-1, profile=profile)
+
+    def barrier():
+        if world > 1:
+            import torch.distributed as dist
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    for _ in range(args.warmup):
+        solve()
+    barrier()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    n0 = G.gbr_launch_count()
+    results = []
+    with Clocks(dev) as clk:
+        barrier()
+        e0.record()
+        for _ in range(args.steps):
+            results.append(solve())
+        e1.record()
+        barrier()
+    launches = G.gbr_launch_count() - n0
+    t = e0.elapsed_time(e1) / 1e3
+    if world > 1:
+        import torch.distributed as dist
+        tt = torch.tensor([t], dtype=torch.float64, device="cuda")
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        t = tt.item()
+    iters_done = results[-1]["iters"]
+    elems_step = elems * (iters_done + 1)        # FP32 H·v per step plus the FP64 refinement H·v
+    value = elems_step * args.steps * world / t
+
+    # dominant kernel from the live per-stage event timings
+    st = np.sum([r["stage_seconds"] for r in results], axis=0)
+    nl = np.sum([r["stage_launches"] for r in results], axis=0)
+    names = ["k_hop_lists", "k_transpose", "k_gather_dn", "k_gather_up_combine"]
+    # algorithmic bytes of each kernel's own function: transpose reads and
+    # writes a vector; the spin-down gather reads X^T once and writes Z^T;
+    # the spin-up gather reads X once, reads Z^T and writes y
+    bytes_per = [0, 2 * D * 4, 2 * D * 4, 3 * D * 4]
+    k = int(np.argmax(st))
+    avg = st[k] / max(nl[k], 1)
+    hbm, src = peaks()
+    achieved = bytes_per[k] / avg / 1e9
+    roofline = {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s", "frac": achieved / hbm,
+                "traffic": ncu_traffic(names[k]), "kernel": names[k], "peak_source": src,
+                "avg_launch_ms": avg * 1e3,
+                "algorithmic_bytes_per_launch": bytes_per[k],
+                "stage_share": {names[i]: float(st[i] / st.sum()) for i in range(4)}}
+
+    # end to end through the public API with host buffers
+    s_host = s.cpu().pin_memory()
+    e2e_t = []
+    for i in range(max(2, min(args.steps, 3))):
+        barrier()
+        t0 = time.perf_counter()
+        H2 = G.gbr_ham_create(L, h, U, NUP, NDN)
+        s_dev = s_host.to("cuda", non_blocking=True)
+        r2 = G.gbr_lanczos(H2, s_dev, ITERS, prec=G.GBR_PREC_MIXED, refine=True, store_basis=-1)
+        _ = r2["E0"]
+        H2.close()
+        del s_dev
+        torch.cuda.synchronize()
+        e2e_t.append(time.perf_counter() - t0)
+    e2e_v = elems * (r2["iters"] + 1) / statistics.median(e2e_t)
+
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": t / args.steps * 1e3, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32+f64", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "lattice": "4x4 torus", "t": 1.0, "tp": TP, "U": UVAL,
+                       "N_up": NUP, "N_dn": NDN, "dim": D, "elements_per_hv": elems, "lanczos_iters": ITERS,
+                       "precision": "FP32 vectors and H·v, FP64-grade dots, FP64 tridiagonal and Rayleigh quotient",
+                       "basis": "stored" if results[-1]["stored_basis"] else "recomputed",
+                       "l2": "inputs larger than L2 (0.52 GB FP32 vectors)", "parallelism": f"replicas{world}"},
+            "clocks": clk.summary(), "gpu_launches": int(launches), "roofline": roofline,
+            "e2e": {"value": e2e_v, "unit": UNIT, "h2d_bytes_per_step": D * 8,
+                    "d2h_bytes_per_step": 8 * (2 * ITERS + 8)},
+            "E0": results[-1]["E0"], "residual": results[-1]["residual"]}
+
+    if rank == 0 and not args.no_extras:
+        r64 = solve(prec=G.GBR_PREC_FP64, profile=False, refine=False)
+        rm = results[-1]
+        line["lanczos"] = {"mixed_E0": rm["E0"], "mixed_s": rm["seconds"], "fp64_E0": r64["E0"],
+                           "fp64_s": r64["seconds"], "rel_diff": abs(rm["E0"] - r64["E0"]) / abs(r64["E0"]),
+                           "speedup_mixed_over_fp64": r64["seconds"] / rm["seconds"]}
+        try:
+            line["ranking"] = ranking_extras(G, torch)
+        except Exception as ex:  # report rather than hide
+            line["ranking"] = {"error": repr(ex)}
+    if rank == 0 and world == 1 and not args.no_cpu:
+        v, desc, dt = oracle_sample(args.cpu_seconds)
+        line["cpu_baseline"] = {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": desc}
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--cpu-seconds", type=float, default=15.0)
+    ap.add_argument("--no-extras", action="store_true")
+    ap.add_argument("--no-cpu", action="store_true")
+    args = ap.parse_args()
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    if args.impl == "reference":
+        run_reference(args, rank)
+        return
+    if world > 1:
+        import torch
+        import torch.distributed as dist
+        torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
+        dist.init_process_group("nccl")
+    run_ours(args, rank, world)
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

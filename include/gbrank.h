@@ -184,8 +184,26 @@ int gbr_ham_set_path(gbr_ham *H, int path);
 /* y = H x on the sector (Eq. mvblock with Eq. Talpha applied on the fly).
  *   d_x, d_y: dim elements (device), float when fp == 32, double when
  *   fp == 64; they must not overlap.  Deterministic: each y element has one
- *   owner and a fixed summation order, no atomics.  Asynchronous. */
+ *   owner and a fixed summation order, no atomics.  Asynchronous.  The
+ *   factored path uses two scratch vectors owned by the handle (allocated on
+ *   first use): calls on one handle must not overlap. */
 int gbr_hv(const gbr_ham *H, const void *d_x, void *d_y, int fp, void *stream);
+
+/* One stage of the factored H·v, for timing and inspection.  With x viewed
+ * as the D_up x D_dn matrix X:
+ *   stage 1: rank the per-spin hop lists (unrank, hop, sign, staggered or
+ *            combinadics rank) into the handle's tables (x, y unused);
+ *   stage 2: X^T into the handle's scratch (y unused);
+ *   stage 3: Z^T = H_dn X^T into the handle's scratch (x, y unused);
+ *   stage 4: y = H_up X + Dg o X + Z (row gathers, diagonal, combine).
+ * Calling 1..4 in order on one stream equals gbr_hv with the factored path.
+ * Arguments as for gbr_hv; the handle's scratch (two vectors of dim
+ * elements) is allocated on first use, so one H·v at a time per handle. */
+int gbr_hv_stage(const gbr_ham *H, const void *d_x, void *d_y, int fp, int stage, void *stream);
+
+/* Kernels this library has launched in the process so far (eager launches
+ * plus, for replayed CUDA graphs, the kernels each replay runs). */
+int64_t gbr_launch_count(void);
 
 /* Auto-tunes the H·v launch shape (threads, tiles) for precision fp on this
  * device by timing the candidates on scratch vectors; the choice is kept in
@@ -210,6 +228,7 @@ typedef struct {
                          vector one pass), 0 = recompute the basis in a second
                          run of the recurrence, -1 = decide from free memory */
     int use_graph;    /* 1 = replay each iteration as a captured CUDA graph */
+    int profile;      /* 1 = time every H·v stage with CUDA events (no graphs) */
 } gbr_lanczos_opts;
 
 typedef struct {
@@ -220,7 +239,12 @@ typedef struct {
     int breakdown;     /* 1 if the recurrence stopped on beta ~ 0 */
     int stored_basis;  /* 1 if the basis was kept in device memory */
     double seconds;    /* device time of the whole call (CUDA events) */
-    double hv_seconds; /* device time spent inside H·v launches */
+    double hv_seconds; /* device time spent inside H·v launches (profile only) */
+    double stage_seconds[4]; /* profile: total device time of the H·v stages
+                                (hop lists, transpose, spin-down gather,
+                                spin-up gather with diagonal; the fused path
+                                is counted in the last slot) */
+    int stage_launches[4];   /* profile: launches of each stage */
 } gbr_lanczos_result;
 
 /* Runs Lanczos from the start vector d_v0 (dim doubles on the device, not

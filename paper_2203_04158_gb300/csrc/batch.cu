@@ -219,78 +219,88 @@ __global__ void __launch_bounds__(kBatchThreads) k_batch(const SectorDesc *__res
         build_spin(L, sd.Ndn, sd.Ddn, hmax, hs, bidx, bin, dn);
         const int D = sd.Dup * sd.Ddn;
         const int K = min(iters, D);
-        // v0 = fp32(s) / |fp32(s)|
-        float fh = 0.f, fl = 0.f;
-        for (int i = threadIdx.x; i < D; i += blockDim.x) {
-            const float s = (float)start[sd.off + i];
-            v[i] = s;
-            ffp(fh, fl, s, s);
-        }
-        __syncthreads();
-        const double n0 = sqrt(bsum((double)fh + (double)fl, red));
+        // Two cycles: the second restarts from the (FP32-rounded) Ritz vector of
+        // the first, which removes what the FP32 recurrence lost.  Each cycle
+        // runs the recurrence twice: once for the scalars, once more (bit
+        // identical) to accumulate the Ritz vector x in FP64.
         int kdone = 0;
-        double scale = 0.0;
-        for (int pass = 0; pass < 2; ++pass) {
-            if (pass == 1) {
-                for (int i = threadIdx.x; i < D; i += blockDim.x) v[i] = (float)start[sd.off + i];
+        for (int cyc = 0; cyc < 2; ++cyc) {
+            if (cyc == 1) {
+                for (int i = threadIdx.x; i < D; i += blockDim.x) hx[i] = x[i];
                 __syncthreads();
             }
-            for (int i = threadIdx.x; i < D; i += blockDim.x) { v[i] = (float)((double)v[i] / n0); vp[i] = 0.f; }
-            __syncthreads();
-            const int ksteps = pass == 0 ? K : kdone;
-            for (int k = 0; k < ksteps; ++k) {
-                if (pass == 1) {
-                    for (int i = threadIdx.x; i < D; i += blockDim.x) x[i] = fma(svec[k], (double)v[i], k ? x[i] : 0.0);
-                    if (k + 1 == ksteps) break;
-                }
-                hv_small<float>(sd, hmax, up, dn, bc32, U32, v, w);
-                __syncthreads();
-                const float bk = k ? (float)beta[k] : 0.f;
-                float ah = 0.f, al = 0.f;
+            const int Kc = cyc == 0 ? K : min(K, max(24, K / 2));
+            float fh = 0.f, fl = 0.f;
+            for (int i = threadIdx.x; i < D; i += blockDim.x) {
+                const float s = (float)(cyc == 0 ? start[sd.off + i] : hx[i]);
+                ffp(fh, fl, s, s);
+            }
+            const double n0 = sqrt(bsum((double)fh + (double)fl, red));
+            double scale = 0.0;
+            kdone = 0;
+            for (int pass = 0; pass < 2; ++pass) {
                 for (int i = threadIdx.x; i < D; i += blockDim.x) {
-                    float wi = w[i];
-                    if (k) wi -= bk * vp[i];
-                    w[i] = wi;
-                    ffp(ah, al, wi, v[i]);
+                    const float s = (float)(cyc == 0 ? start[sd.off + i] : hx[i]);
+                    v[i] = (float)((double)s / n0);
+                    vp[i] = 0.f;
                 }
                 __syncthreads();
-                if (pass == 0) {
-                    const double a = bsum((double)ah + (double)al, red);
-                    if (threadIdx.x == 0) alpha[k] = a;
-                    scale = fmax(scale, fabs(a));
-                }
-                __syncthreads();
-                const float ak = (float)alpha[k];
-                float bh = 0.f, bl = 0.f;
-                for (int i = threadIdx.x; i < D; i += blockDim.x) {
-                    const float wi = w[i] - ak * v[i];
-                    w[i] = wi;
-                    ffp(bh, bl, wi, wi);
-                }
-                __syncthreads();
-                if (pass == 0) {
-                    const double b = sqrt(fmax(bsum((double)bh + (double)bl, red), 0.0));
-                    if (threadIdx.x == 0) beta[k + 1] = b;
-                    kdone = k + 1;
-                    const bool stop = (k + 1 >= K) || (b <= 1e-13 * fmax(scale, b));
-                    scale = fmax(scale, b);
+                const int ksteps = pass == 0 ? Kc : kdone;
+                for (int k = 0; k < ksteps; ++k) {
+                    if (pass == 1) {
+                        for (int i = threadIdx.x; i < D; i += blockDim.x) x[i] = fma(svec[k], (double)v[i], k ? x[i] : 0.0);
+                        if (k + 1 == ksteps) break;
+                    }
+                    hv_small<float>(sd, hmax, up, dn, bc32, U32, v, w);
                     __syncthreads();
-                    if (stop) break;
+                    const float bk = k ? (float)beta[k] : 0.f;
+                    float ah = 0.f, al = 0.f;
+                    for (int i = threadIdx.x; i < D; i += blockDim.x) {
+                        float wi = w[i];
+                        if (k) wi -= bk * vp[i];
+                        w[i] = wi;
+                        ffp(ah, al, wi, v[i]);
+                    }
+                    __syncthreads();
+                    if (pass == 0) {
+                        const double a = bsum((double)ah + (double)al, red);
+                        if (threadIdx.x == 0) alpha[k] = a;
+                        scale = fmax(scale, fabs(a));
+                    }
+                    __syncthreads();
+                    const float ak = (float)alpha[k];
+                    float bh = 0.f, bl = 0.f;
+                    for (int i = threadIdx.x; i < D; i += blockDim.x) {
+                        const float wi = w[i] - ak * v[i];
+                        w[i] = wi;
+                        ffp(bh, bl, wi, wi);
+                    }
+                    __syncthreads();
+                    if (pass == 0) {
+                        const double b = sqrt(fmax(bsum((double)bh + (double)bl, red), 0.0));
+                        if (threadIdx.x == 0) beta[k + 1] = b;
+                        kdone = k + 1;
+                        const bool stop = (k + 1 >= Kc) || (b <= 1e-13 * fmax(scale, b));
+                        scale = fmax(scale, b);
+                        __syncthreads();
+                        if (stop) break;
+                    }
+                    __syncthreads();
+                    const float inv = (float)(1.0 / beta[k + 1]);
+                    for (int i = threadIdx.x; i < D; i += blockDim.x) {
+                        const float vn = w[i] * inv;
+                        vp[i] = v[i];
+                        v[i] = vn;
+                    }
+                    __syncthreads();
                 }
-                __syncthreads();
-                const float inv = (float)(1.0 / beta[k + 1]);
-                for (int i = threadIdx.x; i < D; i += blockDim.x) {
-                    const float vn = w[i] * inv;
-                    vp[i] = v[i];
-                    v[i] = vn;
+                if (pass == 0) {
+                    const double lam = tridiag_lowest_block(alpha, beta, kdone);
+                    if (threadIdx.x == 0) tridiag_vector_thread(alpha, beta, kdone, lam, svec, work);
+                    __syncthreads();
                 }
-                __syncthreads();
             }
-            if (pass == 0) {
-                const double lam = tridiag_lowest_block(alpha, beta, kdone);
-                if (threadIdx.x == 0) tridiag_vector_thread(alpha, beta, kdone, lam, svec, work);
-                __syncthreads();
-            }
+            __syncthreads();
         }
         __syncthreads();
         // FP64 Rayleigh quotient of the Ritz vector
@@ -416,6 +426,7 @@ extern "C" int gbr_batch_solve(int n_models, const gbr_model_desc *models, const
     k_batch<<<grid, kBatchThreads, smem, st>>>(dsec.as<SectorDesc>(), (int)order.size(), dmod.as<ModelDev>(), d_start,
                                                K, lay, dctr.as<int>(), dE.as<double>(), dK.as<int>());
     GBR_LAUNCH_CHECK();
+    count_launches(1);
     std::vector<double> E(order.size());
     GBR_CUDA_TRY(cudaMemcpyAsync(E.data(), dE.p, E.size() * 8, cudaMemcpyDeviceToHost, st));
     GBR_CUDA_TRY(cudaStreamSynchronize(st));

@@ -49,6 +49,11 @@ struct DevBuf {
 
 int sm_count();
 
+// Process-wide count of kernel launches issued by the library.
+void count_launches(int64_t n);
+int64_t launch_count();
+void set_launch_count(int64_t v);
+
 // ------------------------------------------------------------- binomials
 
 // C(n, k) for 0 <= n, k <= 64 (0 for k > n), exact in 64 bits.

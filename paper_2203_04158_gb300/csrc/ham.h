@@ -53,11 +53,20 @@ struct gbr_ham {
     gbr::DevBuf bond_coef32;   // nbond floats
     gbr::DevBuf hcoef64;       // L x L doubles (fused path lookups)
     gbr::DevBuf binom;         // (L+1) x (L+1) uint32 binomials (CNS ranking)
-    // tuned launch shapes (0 = defaults)
+    // tuned launch shape (0 = default): rows per CTA of the gather passes
     int tune_up_rows[2] = {0, 0};
-    int tune_dn_threads[2] = {0, 0};
+    // scratch of the factored path (X^T and Z^T), grown on first use; one
+    // H·v at a time per handle
+    gbr::DevBuf ws_xt, ws_zt;
+    // Lanczos work buffers, kept between calls and grown when needed
+    gbr::DevBuf lz_state, lz_alpha, lz_beta, lz_part, lz_coef, lz_tri, lz_svec, lz_work, lz_ritz;
+    gbr::DevBuf lz_buf[3], lz_basis, lz_x, lz_hx;
 };
 
 namespace gbr {
-int hv_launch(const gbr_ham *H, const void *x, void *y, int fp, cudaStream_t st);
+// ev (optional): 5 events recorded at the stage boundaries (hop lists,
+// transpose, spin-down gather, spin-up gather with diagonal and combine);
+// the fused path records the first four before its single kernel.
+int hv_launch(const gbr_ham *H, const void *x, void *y, int fp, cudaStream_t st, cudaEvent_t *ev = nullptr);
+int hv_stage(const gbr_ham *H, const void *x, void *y, int fp, int stage, cudaStream_t st);
 }

@@ -2,6 +2,7 @@
 // staggered-table and packed-trie builders (Sec. III-B and IV of
 // Wallerberger & Held).
 #include <algorithm>
+#include <atomic>
 #include <cstdarg>
 #include <cstring>
 
@@ -46,6 +47,11 @@ void DevBuf::release() {
     p = nullptr;
     bytes = 0;
 }
+
+static std::atomic<int64_t> g_launches{0};
+void count_launches(int64_t n) { g_launches.fetch_add(n, std::memory_order_relaxed); }
+int64_t launch_count() { return g_launches.load(std::memory_order_relaxed); }
+void set_launch_count(int64_t v) { g_launches.store(v, std::memory_order_relaxed); }
 
 int sm_count() {
     int dev = 0, n = 0;
@@ -233,6 +239,8 @@ using namespace gbr;
 extern "C" const char *gbr_last_error(void) { return g_err; }
 
 extern "C" int gbr_version(void) { return 1; }
+
+extern "C" int64_t gbr_launch_count(void) { return launch_count(); }
 
 extern "C" int gbr_trie_build_host(const uint64_t *h_sorted, int64_t n, int M, int R, uint64_t *h_t, int64_t cap,
                                    int64_t *size_out) {

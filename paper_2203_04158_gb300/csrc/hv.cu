@@ -221,28 +221,57 @@ __global__ void __launch_bounds__(256) k_hv_fused(const SpinK su, const SpinK sd
 }
 
 // ------------------------------------------------------------ factored path
+//
+// Y = H_up X + Dg o X + (H_dn X^T)^T.  Both off-diagonal products are row
+// gathers of the same shape, Z[r, c] = sum_k coef_k(r) W[t_k(r), c]: for
+// H_up, W = X; for H_dn, W = X^T (an explicit transpose), whose result Z^T
+// is added back in the epilogue of the spin-up pass.  A CTA owns TR rows and
+// 128*VEC columns; its rows' hop lists are staged in shared memory, each
+// thread streams VEC consecutive columns of every gathered row (coalesced),
+// and consecutive CTAs share a column chunk so the gathered rows of that
+// chunk stay in L2.
 
-// Spin-up pass: Y[r, c] = sum_k coef_k(r) X[t_k(r), c] for a tile of TR rows
-// and 128*VEC columns.  Consecutive CTAs share a column chunk, so the rows of
-// X they gather stay in L2 while the chunk is being processed.
-template <typename T, int VEC>
-__global__ void __launch_bounds__(128) k_hv_up(const int64_t Dup, const int64_t Ddn, const int TR, const int hmax,
-                                               const int64_t nrb, const uint16_t *__restrict__ cnt,
-                                               const uint32_t *__restrict__ tgt, const uint16_t *__restrict__ bond,
-                                               const T *__restrict__ bcoef, const int uniform, const T hu,
-                                               const T *__restrict__ x, T *__restrict__ y) {
+template <typename T, int TILE>
+__global__ void __launch_bounds__(TILE * 4) k_transpose(const T *__restrict__ in, T *__restrict__ out, int64_t rows,
+                                                        int64_t cols) {
+    __shared__ T tile[TILE][TILE + 1];
+    const int64_t c0 = (int64_t)blockIdx.x * TILE, r0 = (int64_t)blockIdx.y * TILE;
+    for (int i = threadIdx.y; i < TILE; i += blockDim.y) {
+        const int64_t r = r0 + i, c = c0 + threadIdx.x;
+        if (r < rows && c < cols) tile[i][threadIdx.x] = __ldcs(in + r * cols + c);
+    }
+    __syncthreads();
+    for (int i = threadIdx.y; i < TILE; i += blockDim.y) {
+        const int64_t c = c0 + i, r = r0 + threadIdx.x;
+        if (r < rows && c < cols) out[c * rows + r] = tile[threadIdx.x][i];
+    }
+}
+
+struct CombineArgs {
+    const uint32_t *st_up, *st_dn;   // per-spin patterns (row and column states)
+    const void *dup, *ddn, *uval;     // per-spin diagonals, U class values (precision T)
+    const void *zt;                   // Z^T = H_dn X^T, D_dn x D_up
+    HamK hk;
+};
+
+template <typename T, int VEC, bool COMBINE>
+__global__ void __launch_bounds__(128) k_gather(const int64_t Drows, const int64_t Dcols, const int TR, const int hmax,
+                                                const int64_t nrb, const uint16_t *__restrict__ cnt,
+                                                const uint32_t *__restrict__ tgt, const uint16_t *__restrict__ bond,
+                                                const T *__restrict__ bcoef, const int uniform, const T hu,
+                                                const T *__restrict__ x, T *__restrict__ y, const CombineArgs ca) {
     extern __shared__ __align__(16) unsigned char smr[];
     uint32_t *st = reinterpret_cast<uint32_t *>(smr);
     T *sc = reinterpret_cast<T *>(smr + (((size_t)TR * hmax * 4 + 15) & ~(size_t)15));
     __shared__ int scnt[64];
     const int64_t rb = blockIdx.x % nrb, cc = blockIdx.x / nrb;
     const int64_t r0 = rb * TR;
-    for (int i = threadIdx.x; i < TR; i += blockDim.x) scnt[i] = (r0 + i < Dup) ? (int)cnt[r0 + i] : 0;
+    for (int i = threadIdx.x; i < TR; i += blockDim.x) scnt[i] = (r0 + i < Drows) ? (int)cnt[r0 + i] : 0;
     __syncthreads();
     for (int e = threadIdx.x; e < TR * hmax; e += blockDim.x) {
         const int i = e % TR, k = e / TR;
         if (k < scnt[i]) {
-            const int64_t g = (int64_t)k * Dup + r0 + i;
+            const int64_t g = (int64_t)k * Drows + r0 + i;
             const uint32_t w = tgt[g];
             const T c = uniform ? hu : bcoef[bond[g]];
             st[i * hmax + k] = w & 0x7FFFFFFFu;
@@ -251,91 +280,72 @@ __global__ void __launch_bounds__(128) k_hv_up(const int64_t Dup, const int64_t 
     }
     __syncthreads();
     const int64_t c0 = cc * (int64_t)(128 * VEC) + (int64_t)threadIdx.x * VEC;
-    if (c0 >= Ddn) return;
+    if (c0 >= Dcols) return;
+    // combine epilogue: column states and diagonals of this thread's columns
+    uint32_t ad[VEC];
+    T dd[VEC];
+    T uval[kMaxUClasses];
+    if (COMBINE) {
+        const T *ddn = (const T *)ca.ddn;
+#pragma unroll
+        for (int v = 0; v < VEC; ++v) {
+            ad[v] = ca.st_dn[c0 + v];
+            dd[v] = ddn[c0 + v];
+        }
+        for (int u = 0; u < kMaxUClasses; ++u) uval[u] = u < ca.hk.nucls ? ((const T *)ca.uval)[u] : T(0);
+    }
     for (int i = 0; i < TR; ++i) {
         const int64_t r = r0 + i;
-        if (r >= Dup) break;
+        if (r >= Drows) break;
         const int n = scnt[i];
         const uint32_t *ti = st + i * hmax;
         const T *ci = sc + i * hmax;
-        if (VEC == 4) {
-            float4 acc = make_float4(0.f, 0.f, 0.f, 0.f);
+        T acc[VEC];
+#pragma unroll
+        for (int v = 0; v < VEC; ++v) acc[v] = 0;
+        if (VEC == 4 && sizeof(T) == 4) {
+            float4 a4 = make_float4(0.f, 0.f, 0.f, 0.f);
 #pragma unroll 4
             for (int k = 0; k < n; ++k) {
-                const float4 v = __ldg(reinterpret_cast<const float4 *>(x + (int64_t)ti[k] * Ddn + c0));
+                const float4 v = __ldg(reinterpret_cast<const float4 *>(x + (int64_t)ti[k] * Dcols + c0));
                 const float c = (float)ci[k];
-                acc.x += c * v.x; acc.y += c * v.y; acc.z += c * v.z; acc.w += c * v.w;
+                a4.x += c * v.x; a4.y += c * v.y; a4.z += c * v.z; a4.w += c * v.w;
             }
-            __stcs(reinterpret_cast<float4 *>(y + r * Ddn + c0), acc);
+            acc[0] = a4.x; acc[1] = a4.y; acc[2] = a4.z; acc[3 % VEC] = a4.w;
         } else if (VEC == 2) {
             T a0 = 0, a1 = 0;
 #pragma unroll 4
             for (int k = 0; k < n; ++k) {
-                const T *px = x + (int64_t)ti[k] * Ddn + c0;
-                const typename Vec<T>::v2 v = __ldg(reinterpret_cast<const typename Vec<T>::v2 *>(px));
+                const typename Vec<T>::v2 v = __ldg(reinterpret_cast<const typename Vec<T>::v2 *>(x + (int64_t)ti[k] * Dcols + c0));
                 a0 += ci[k] * v.x; a1 += ci[k] * v.y;
             }
-            typename Vec<T>::v2 o; o.x = a0; o.y = a1;
-            __stcs(reinterpret_cast<typename Vec<T>::v2 *>(y + r * Ddn + c0), o);
+            acc[0] = a0; acc[1 % VEC] = a1;
         } else {
             T a0 = 0;
 #pragma unroll 4
-            for (int k = 0; k < n; ++k) a0 += ci[k] * __ldg(x + (int64_t)ti[k] * Ddn + c0);
-            y[r * Ddn + c0] = a0;
+            for (int k = 0; k < n; ++k) a0 += ci[k] * __ldg(x + (int64_t)ti[k] * Dcols + c0);
+            acc[0] = a0;
         }
-    }
-}
-
-// Spin-down pass plus diagonal: for TRD rows staged in shared memory,
-// Y[r, c] += Dg(r, c) X[r, c] + sum_k coef_k(c) X[r, t_k(c)].
-template <typename T, int TRD, bool STAGE>
-__global__ void __launch_bounds__(256) k_hv_dn(const int64_t Dup, const int64_t Ddn, const HamK hk,
-                                               const uint16_t *__restrict__ cnt, const uint32_t *__restrict__ tgt,
-                                               const uint16_t *__restrict__ bond, const T *__restrict__ bcoef,
-                                               const T hu, const uint32_t *__restrict__ st_up,
-                                               const uint32_t *__restrict__ st_dn, const T *__restrict__ dup,
-                                               const T *__restrict__ ddn, const T *__restrict__ uval_g,
-                                               const T *__restrict__ x, T *__restrict__ y) {
-    extern __shared__ __align__(16) unsigned char smr[];
-    T *xs = reinterpret_cast<T *>(smr);
-    const int64_t r0 = (int64_t)blockIdx.x * TRD;
-    const int nrow = (int)(Dup - r0 < (int64_t)TRD ? Dup - r0 : (int64_t)TRD);
-    if (STAGE) {
-        for (int i = 0; i < nrow; ++i) {
-            const T *src = x + (r0 + i) * Ddn;
-            for (int64_t c = threadIdx.x; c < Ddn; c += blockDim.x) xs[i * Ddn + c] = __ldcs(src + c);
-        }
-        __syncthreads();
-    }
-    T uval[kMaxUClasses];
-    for (int c = 0; c < kMaxUClasses; ++c) uval[c] = c < hk.nucls ? uval_g[c] : T(0);
-    uint32_t au[TRD];
+        if (COMBINE) {
+            const uint32_t au = ca.st_up[r];
+            const T du = ((const T *)ca.dup)[r];
+            const T *zt = (const T *)ca.zt;
 #pragma unroll
-    for (int i = 0; i < TRD; ++i) au[i] = i < nrow ? st_up[r0 + i] : 0u;
-    for (int64_t c = threadIdx.x; c < Ddn; c += blockDim.x) {
-        T acc[TRD];
-#pragma unroll
-        for (int i = 0; i < TRD; ++i) acc[i] = 0;
-        const int n = cnt[c];
-        for (int k = 0; k < n; ++k) {
-            const int64_t g = (int64_t)k * Ddn + c;
-            const uint32_t w = __ldg(tgt + g);
-            T cf = hk.uniform ? hu : __ldg(bcoef + __ldg(bond + g));
-            cf = (w >> 31) ? -cf : cf;
-            const int64_t t = w & 0x7FFFFFFFu;
-#pragma unroll
-            for (int i = 0; i < TRD; ++i)
-                if (i < nrow) acc[i] += cf * (STAGE ? xs[i * Ddn + t] : __ldg(x + (r0 + i) * Ddn + t));
-        }
-        const uint32_t ad = st_dn[c];
-#pragma unroll
-        for (int i = 0; i < TRD; ++i) {
-            if (i < nrow) {
-                const int64_t r = r0 + i;
-                const T xv = STAGE ? xs[i * Ddn + c] : x[r * Ddn + c];
-                const T dg = diag_value<T>(hk, dup, ddn, uval, r, c, au[i], ad);
-                y[r * Ddn + c] = y[r * Ddn + c] + dg * xv + acc[i];
+            for (int v = 0; v < VEC; ++v) {
+                const uint32_t both = au & ad[v];
+                T dg = du + dd[v];
+                for (int u = 0; u < ca.hk.nucls; ++u) dg += uval[u] * (T)__popc(both & ca.hk.umask[u]);
+                acc[v] += dg * x[r * Dcols + c0 + v] + __ldg(zt + (c0 + v) * Drows + r);
             }
+        }
+        if (VEC == 4 && sizeof(T) == 4) {
+            __stcs(reinterpret_cast<float4 *>(y + r * Dcols + c0), make_float4((float)acc[0], (float)acc[1 % VEC], (float)acc[2 % VEC], (float)acc[3 % VEC]));
+        } else if (VEC == 2) {
+            typename Vec<T>::v2 o;
+            o.x = acc[0]; o.y = acc[1 % VEC];
+            __stcs(reinterpret_cast<typename Vec<T>::v2 *>(y + r * Dcols + c0), o);
+        } else {
+            y[r * Dcols + c0] = acc[0];
         }
     }
 }
@@ -361,6 +371,7 @@ static int launch_hop_lists(const gbr_ham *H, const SpinSector &s, cudaStream_t 
         reinterpret_cast<const uint16_t *>(H->bonds.p) + 2 * H->k.nbond, s.hop_cnt.as<uint16_t>(),
         s.hop_tgt.as<uint32_t>(), s.hop_bond.as<uint16_t>(), s.hmax);
     GBR_LAUNCH_CHECK();
+    count_launches(1);
     return GBR_OK;
 }
 
@@ -379,78 +390,113 @@ static int launch_fused(const gbr_ham *H, const T *x, T *y, cudaStream_t st, con
                                              H->binom.as<uint32_t>(), (const T *)hd.hcoef, (const T *)hd.dup,
                                              (const T *)hd.ddn, (const T *)hd.uval, x, y);
     GBR_LAUNCH_CHECK();
+    count_launches(1);
+    return GBR_OK;
+}
+
+// When N_up == N_dn both spin species share one sector and one set of hop
+// lists (the hopping is spin independent).
+static const SpinSector &dn_lists(const gbr_ham *H) { return H->Nup == H->Ndn ? H->up : H->dn; }
+
+template <typename T>
+static int stage_hop_lists(const gbr_ham *H, cudaStream_t st) {
+    int rc = launch_hop_lists<T>(H, H->up, st);
+    if (rc) return rc;
+    if (H->Nup != H->Ndn) rc = launch_hop_lists<T>(H, H->dn, st);
+    return rc;
+}
+
+// scratch of the factored path: X^T and Z^T, owned by the handle
+static int ensure_ws(const gbr_ham *H, size_t bytes) {
+    gbr_ham *h = const_cast<gbr_ham *>(H);
+    if (h->ws_xt.bytes >= bytes && h->ws_zt.bytes >= bytes) return GBR_OK;
+    int rc = h->ws_xt.alloc(bytes);
+    if (!rc) rc = h->ws_zt.alloc(bytes);
+    return rc;
+}
+
+// One row-gather pass Z = H_lists W (+ the combine epilogue).
+template <typename T, bool COMBINE>
+static int launch_gather(const gbr_ham *H, const SpinSector &lists, int64_t Drows, int64_t Dcols, const T *w, T *z,
+                         const CombineArgs &ca, cudaStream_t st, const HamDev &hd) {
+    const int fpi = sizeof(T) == 8 ? 1 : 0;
+    const bool aligned16 = (((uintptr_t)w | (uintptr_t)z) & 15u) == 0;
+    const int vmax = sizeof(T) == 4 ? 4 : 2;
+    int vec = 1;
+    // widest vector whose column chunk (all rows x 128*VEC columns) stays
+    // well inside L2
+    for (int v = vmax; v >= 2; v /= 2)
+        if (aligned16 && Dcols % v == 0 && (double)Drows * 128 * v * sizeof(T) <= 48e6) { vec = v; break; }
+    const int TR = H->tune_up_rows[fpi] ? H->tune_up_rows[fpi] : 8;
+    const int64_t nrb = (Drows + TR - 1) / TR;
+    const int64_t ncc = (Dcols + 128 * vec - 1) / (128 * vec);
+    const int hmax = std::max(1, lists.hmax);
+    const size_t smem = (((size_t)TR * hmax * 4 + 15) & ~(size_t)15) + (size_t)TR * hmax * sizeof(T);
+    const int64_t blocks = nrb * ncc;
+    if (blocks > 0x7FFFFFFF) return set_error(GBR_EINVAL, "sector too large for the gather grid");
+#define GBR_G(V)                                                                                             \
+    {                                                                                                        \
+        auto kern = k_gather<T, V, COMBINE>;                                                                 \
+        if (smem > 48 * 1024) GBR_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)); \
+        kern<<<(int)blocks, 128, smem, st>>>(Drows, Dcols, TR, hmax, nrb, lists.hop_cnt.as<uint16_t>(),      \
+                                             lists.hop_tgt.as<uint32_t>(), lists.hop_bond.as<uint16_t>(),    \
+                                             (const T *)hd.bcoef, H->k.uniform, (T)H->k.hu, w, z, ca);        \
+    }
+    if (vec == 4) GBR_G(4) else if (vec == 2) GBR_G(2) else GBR_G(1)
+#undef GBR_G
+    GBR_LAUNCH_CHECK();
+    count_launches(1);
     return GBR_OK;
 }
 
 template <typename T>
-static int launch_factored(const gbr_ham *H, const T *x, T *y, cudaStream_t st, const HamDev &hd) {
-    int rc = launch_hop_lists<T>(H, H->up, st);
+static int stage_transpose(const gbr_ham *H, const T *x, cudaStream_t st) {
+    int rc = ensure_ws(H, (size_t)H->D * sizeof(T));
     if (rc) return rc;
-    if (&H->dn != &H->up) {
-        rc = launch_hop_lists<T>(H, H->dn, st);
-        if (rc) return rc;
-    }
     const int64_t Dup = H->up.D, Ddn = H->dn.D;
-    const int fpi = sizeof(T) == 8 ? 1 : 0;
-    // ---- spin-up pass
-    {
-        const bool aligned16 = (((uintptr_t)x | (uintptr_t)y) & 15u) == 0;
-        int vec = 1;
-        const size_t s = sizeof(T);
-        const int vmax = sizeof(T) == 4 ? 4 : 2;
-        for (int v = vmax; v >= 2; v /= 2) {
-            if (aligned16 && Ddn % v == 0 && (double)Dup * 128 * v * s <= 48e6) { vec = v; break; }
-        }
-        if (vec == 1 && aligned16 && Ddn % 2 == 0) vec = 2;
-        const int TR = H->tune_up_rows[fpi] ? H->tune_up_rows[fpi] : 8;
-        const int64_t nrb = (Dup + TR - 1) / TR;
-        const int64_t ncc = (Ddn + 128 * vec - 1) / (128 * vec);
-        const int hmax = std::max(1, H->up.hmax);
-        const size_t smem = (((size_t)TR * hmax * 4 + 15) & ~(size_t)15) + (size_t)TR * hmax * sizeof(T);
-        const int64_t blocks = nrb * ncc;
-        if (blocks > 0x7FFFFFFF) return set_error(GBR_EINVAL, "sector too large for the spin-up pass grid");
-#define GBR_UP(V)                                                                                            \
-    {                                                                                                        \
-        auto kern = k_hv_up<T, V>;                                                                           \
-        if (smem > 48 * 1024) GBR_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)); \
-        kern<<<(int)blocks, 128, smem, st>>>(Dup, Ddn, TR, hmax, nrb, H->up.hop_cnt.as<uint16_t>(),          \
-                                             H->up.hop_tgt.as<uint32_t>(), H->up.hop_bond.as<uint16_t>(),    \
-                                             (const T *)hd.bcoef, H->k.uniform, (T)H->k.hu, x, y);            \
-    }
-        if (vec == 4) GBR_UP(4) else if (vec == 2) GBR_UP(2) else GBR_UP(1)
-#undef GBR_UP
-        GBR_LAUNCH_CHECK();
-    }
-    // ---- spin-down pass with the diagonal
-    {
-        const size_t row_bytes = (size_t)Ddn * sizeof(T);
-        const size_t budget = 200 * 1024;
-        int trd = 0;
-        for (int t : {8, 4, 2, 1})
-            if ((size_t)t * row_bytes <= budget) { trd = t; break; }
-        if (H->tune_dn_threads[fpi] > 0 && H->tune_dn_threads[fpi] <= trd) trd = H->tune_dn_threads[fpi];
-        const bool stage = trd > 0;
-        if (!stage) trd = 4;
-        const int64_t blocks = (Dup + trd - 1) / trd;
-        const size_t smem = stage ? (size_t)trd * row_bytes : 0;
-#define GBR_DN(TV, SV)                                                                                       \
-    {                                                                                                        \
-        auto kern = k_hv_dn<T, TV, SV>;                                                                      \
-        if (smem > 48 * 1024) GBR_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)); \
-        kern<<<(int)blocks, 256, smem, st>>>(Dup, Ddn, H->k, H->dn.hop_cnt.as<uint16_t>(),                   \
-                                             H->dn.hop_tgt.as<uint32_t>(), H->dn.hop_bond.as<uint16_t>(),    \
-                                             (const T *)hd.bcoef, (T)H->k.hu, H->up.states.as<uint32_t>(),   \
-                                             H->dn.states.as<uint32_t>(), (const T *)hd.dup,                 \
-                                             (const T *)hd.ddn, (const T *)hd.uval, x, y);                   \
-    }
-        if (!stage) GBR_DN(4, false)
-        else if (trd == 8) GBR_DN(8, true)
-        else if (trd == 4) GBR_DN(4, true)
-        else if (trd == 2) GBR_DN(2, true)
-        else GBR_DN(1, true)
-#undef GBR_DN
-        GBR_LAUNCH_CHECK();
-    }
+    constexpr int TILE = 64;
+    dim3 grid((unsigned)((Ddn + TILE - 1) / TILE), (unsigned)((Dup + TILE - 1) / TILE));
+    if (grid.y > 65535) return set_error(GBR_EINVAL, "sector too large for the transpose grid");
+    k_transpose<T, TILE><<<grid, dim3(TILE, 4), 0, st>>>(x, H->ws_xt.as<T>(), Dup, Ddn);
+    GBR_LAUNCH_CHECK();
+    count_launches(1);
+    return GBR_OK;
+}
+
+// Z^T = H_dn X^T (rows: spin-down states, columns: spin-up states)
+template <typename T>
+static int stage_dn(const gbr_ham *H, cudaStream_t st, const HamDev &hd) {
+    CombineArgs ca{};
+    return launch_gather<T, false>(H, dn_lists(H), H->dn.D, H->up.D, H->ws_xt.as<T>(), H->ws_zt.as<T>(), ca, st, hd);
+}
+
+// Y = H_up X + Dg o X + (Z^T)^T
+template <typename T>
+static int stage_up(const gbr_ham *H, const T *x, T *y, cudaStream_t st, const HamDev &hd) {
+    CombineArgs ca;
+    ca.st_up = H->up.states.as<uint32_t>();
+    ca.st_dn = H->dn.states.as<uint32_t>();
+    ca.dup = hd.dup;
+    ca.ddn = hd.ddn;
+    ca.uval = hd.uval;
+    ca.zt = H->ws_zt.p;
+    ca.hk = H->k;
+    return launch_gather<T, true>(H, H->up, H->up.D, H->dn.D, x, y, ca, st, hd);
+}
+
+template <typename T>
+static int launch_factored(const gbr_ham *H, const T *x, T *y, cudaStream_t st, const HamDev &hd,
+                           cudaEvent_t *ev = nullptr) {
+    if (ev) cudaEventRecord(ev[0], st);
+    int rc = stage_hop_lists<T>(H, st);
+    if (rc) return rc;
+    if (ev) cudaEventRecord(ev[1], st);
+    if ((rc = stage_transpose<T>(H, x, st))) return rc;
+    if (ev) cudaEventRecord(ev[2], st);
+    if ((rc = stage_dn<T>(H, st, hd))) return rc;
+    if (ev) cudaEventRecord(ev[3], st);
+    if ((rc = stage_up<T>(H, x, y, st, hd))) return rc;
+    if (ev) cudaEventRecord(ev[4], st);
     return GBR_OK;
 }
 
@@ -465,18 +511,39 @@ namespace gbr {
 
 static gbr_ham_prec *prec_bufs(const gbr_ham *H, int fpi);
 
-int hv_launch(const gbr_ham *H, const void *x, void *y, int fp, cudaStream_t st) {
+int hv_launch(const gbr_ham *H, const void *x, void *y, int fp, cudaStream_t st, cudaEvent_t *ev) {
     const int fpi = fp == 64 ? 1 : 0;
     gbr_ham_prec *pb = prec_bufs(H, fpi);
     HamDev hd{pb->dup.p, pb->ddn.p, pb->uval.p, pb->bcoef.p, pb->hcoef.p};
     int path = H->path;
     if (path == GBR_HV_AUTO) path = H->D <= (1 << 17) ? GBR_HV_FUSED : GBR_HV_FACTORED;
-    if (fp == 64) {
-        if (path == GBR_HV_FUSED) return launch_fused<double>(H, (const double *)x, (double *)y, st, hd);
-        return launch_factored<double>(H, (const double *)x, (double *)y, st, hd);
+    if (path == GBR_HV_FUSED) {
+        int rc;
+        if (ev)
+            for (int e = 0; e < 4; ++e) cudaEventRecord(ev[e], st);
+        if (fp == 64) rc = launch_fused<double>(H, (const double *)x, (double *)y, st, hd);
+        else rc = launch_fused<float>(H, (const float *)x, (float *)y, st, hd);
+        if (ev) cudaEventRecord(ev[4], st);
+        return rc;
     }
-    if (path == GBR_HV_FUSED) return launch_fused<float>(H, (const float *)x, (float *)y, st, hd);
-    return launch_factored<float>(H, (const float *)x, (float *)y, st, hd);
+    if (fp == 64) return launch_factored<double>(H, (const double *)x, (double *)y, st, hd, ev);
+    return launch_factored<float>(H, (const float *)x, (float *)y, st, hd, ev);
+}
+
+int hv_stage(const gbr_ham *H, const void *x, void *y, int fp, int stage, cudaStream_t st) {
+    const int fpi = fp == 64 ? 1 : 0;
+    gbr_ham_prec *pb = prec_bufs(H, fpi);
+    HamDev hd{pb->dup.p, pb->ddn.p, pb->uval.p, pb->bcoef.p, pb->hcoef.p};
+    if (fp == 64) {
+        if (stage == 1) return stage_hop_lists<double>(H, st);
+        if (stage == 2) return stage_transpose<double>(H, (const double *)x, st);
+        if (stage == 3) return stage_dn<double>(H, st, hd);
+        return stage_up<double>(H, (const double *)x, (double *)y, st, hd);
+    }
+    if (stage == 1) return stage_hop_lists<float>(H, st);
+    if (stage == 2) return stage_transpose<float>(H, (const float *)x, st);
+    if (stage == 3) return stage_dn<float>(H, st, hd);
+    return stage_up<float>(H, (const float *)x, (float *)y, st, hd);
 }
 
 // ------------------------------------------------------------- host build
@@ -688,6 +755,22 @@ extern "C" int gbr_hv(const gbr_ham *H, const void *d_x, void *d_y, int fp, void
     return hv_launch(H, d_x, d_y, fp, (cudaStream_t)stream);
 }
 
+extern "C" int gbr_hv_stage(const gbr_ham *H, const void *d_x, void *d_y, int fp, int stage, void *stream) {
+    clear_error();
+    if (!H) return set_error(GBR_EINVAL, "NULL handle");
+    if (fp != 32 && fp != 64) return set_error(GBR_EINVAL, "fp=%d must be 32 or 64", fp);
+    if (stage < 1 || stage > 4) return set_error(GBR_EINVAL, "stage=%d must be 1..4", stage);
+    if (stage == 2 || stage == 4) {
+        if (!d_x || !d_y) return set_error(GBR_EINVAL, "NULL vector");
+        const size_t s = fp == 64 ? 8 : 4;
+        const uintptr_t xa = (uintptr_t)d_x, ya = (uintptr_t)d_y;
+        if ((xa | ya) % s) return set_error(GBR_EINVAL, "vectors must be aligned to their element size");
+        const uintptr_t bytes = (uintptr_t)H->D * s;
+        if (xa < ya + bytes && ya < xa + bytes) return set_error(GBR_EINVAL, "x and y overlap");
+    }
+    return hv_stage(H, d_x, d_y, fp, stage, (cudaStream_t)stream);
+}
+
 // Times the candidate launch shapes on scratch vectors and keeps the fastest
 // in the handle: the path (fused for sectors up to 2^22 states), the rows per
 // CTA of the spin-up pass, and the rows staged per CTA by the spin-down pass.
@@ -720,21 +803,14 @@ extern "C" int gbr_ham_tune(gbr_ham *H, int fp, void *stream) {
     };
     const int keep_path = H->path;
     float best = 1e30f, ms = 0.f;
-    int best_path = GBR_HV_FACTORED, best_tr = 8, best_trd = 0;
+    int best_path = GBR_HV_FACTORED, best_tr = 8;
     H->path = GBR_HV_FACTORED;
     for (int tr : {4, 8, 16}) {
         H->tune_up_rows[fpi] = tr;
-        H->tune_dn_threads[fpi] = 0;
         if ((rc = time_it(&ms))) goto done;
         if (ms < best) { best = ms; best_tr = tr; }
     }
     H->tune_up_rows[fpi] = best_tr;
-    for (int trd : {1, 2, 4, 8}) {
-        H->tune_dn_threads[fpi] = trd;
-        if ((rc = time_it(&ms))) goto done;
-        if (ms < best) { best = ms; best_trd = trd; }
-    }
-    H->tune_dn_threads[fpi] = best_trd;
     if (H->D <= ((int64_t)1 << 22)) {
         H->path = GBR_HV_FUSED;
         if ((rc = time_it(&ms))) goto done;

@@ -76,6 +76,14 @@ struct LzState {
     double scale;     // max_j(|alpha_j|, beta_j)
 };
 
+// 16-byte packs of vector elements for the streaming kernels: every vector
+// is a cudaMalloc'd buffer (256-byte aligned); elements past the last full
+// pack are handled one by one.
+template <typename T> struct alignas(16) Pack {
+    static constexpr int N = 16 / sizeof(T);
+    T e[N];
+};
+
 // w -= beta_k v_prev (k > 0); partial <w, v>
 template <typename T>
 __global__ void __launch_bounds__(kRedThreads) k_step1(const LzState *st, const double *beta, const T *__restrict__ vprev,
@@ -85,7 +93,26 @@ __global__ void __launch_bounds__(kRedThreads) k_step1(const LzState *st, const 
     const int k = st->k;
     const T b = k > 0 ? (T)beta[k] : T(0);
     DotAcc<T> acc;
-    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    constexpr int V = Pack<T>::N;
+    const int64_t np = n / V;
+    const int64_t tid = blockIdx.x * (int64_t)blockDim.x + threadIdx.x, stride = (int64_t)gridDim.x * blockDim.x;
+    const Pack<T> *VP = reinterpret_cast<const Pack<T> *>(vprev), *VV = reinterpret_cast<const Pack<T> *>(v);
+    Pack<T> *W = reinterpret_cast<Pack<T> *>(w);
+#pragma unroll 2
+    for (int64_t p = tid; p < np; p += stride) {
+        Pack<T> wp = W[p];
+        const Pack<T> vv = VV[p];
+        if (k > 0) {
+            const Pack<T> pp = VP[p];
+#pragma unroll
+            for (int j = 0; j < V; ++j) wp.e[j] -= b * pp.e[j];
+            W[p] = wp;
+        }
+        if (want_dot)
+#pragma unroll
+            for (int j = 0; j < V; ++j) acc.add(wp.e[j], vv.e[j]);
+    }
+    for (int64_t i = np * V + tid; i < n; i += stride) {
         T wi = w[i];
         if (k > 0) wi -= b * vprev[i];
         w[i] = wi;
@@ -103,7 +130,23 @@ __global__ void __launch_bounds__(kRedThreads) k_step2(const LzState *st, const 
     if (st->stop) return;
     const T a = (T)alpha[st->k];
     DotAcc<T> acc;
-    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    constexpr int V = Pack<T>::N;
+    const int64_t np = n / V;
+    const int64_t tid = blockIdx.x * (int64_t)blockDim.x + threadIdx.x, stride = (int64_t)gridDim.x * blockDim.x;
+    const Pack<T> *VV = reinterpret_cast<const Pack<T> *>(v);
+    Pack<T> *W = reinterpret_cast<Pack<T> *>(w);
+#pragma unroll 2
+    for (int64_t p = tid; p < np; p += stride) {
+        Pack<T> wp = W[p];
+        const Pack<T> vv = VV[p];
+#pragma unroll
+        for (int j = 0; j < V; ++j) wp.e[j] -= a * vv.e[j];
+        W[p] = wp;
+        if (want_dot)
+#pragma unroll
+            for (int j = 0; j < V; ++j) acc.add(wp.e[j], wp.e[j]);
+    }
+    for (int64_t i = np * V + tid; i < n; i += stride) {
         const T wi = w[i] - a * v[i];
         w[i] = wi;
         if (want_dot) acc.add(wi, wi);
@@ -149,7 +192,7 @@ __global__ void __launch_bounds__(kRedThreads) k_finalize(LzState *st, double *a
     }
 }
 
-// v_next = w / beta_{k+1} (also into the stored basis); advance k
+// v_next = w / beta_{k+1} (also into the stored basis)
 template <typename T>
 __global__ void __launch_bounds__(kRedThreads) k_step3(LzState *st, const double *beta, const T *__restrict__ w,
                                                        T *__restrict__ vnext, T *__restrict__ basis, int64_t n) {
@@ -157,7 +200,22 @@ __global__ void __launch_bounds__(kRedThreads) k_step3(LzState *st, const double
     const int k = st->k;
     const T inv = (T)(1.0 / beta[k + 1]);
     T *vb = basis ? basis + (int64_t)(k + 1) * n : nullptr;
-    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    constexpr int V = Pack<T>::N;
+    // the basis slot is aligned to 16 bytes only when n * sizeof(T) is
+    const bool vec_ok = !vb || ((uintptr_t)vb & 15u) == 0;
+    const int64_t np = vec_ok ? n / V : 0;
+    const int64_t tid = blockIdx.x * (int64_t)blockDim.x + threadIdx.x, stride = (int64_t)gridDim.x * blockDim.x;
+    const Pack<T> *W = reinterpret_cast<const Pack<T> *>(w);
+    Pack<T> *VN = reinterpret_cast<Pack<T> *>(vnext), *VB = reinterpret_cast<Pack<T> *>(vb);
+#pragma unroll 2
+    for (int64_t p = tid; p < np; p += stride) {
+        Pack<T> x = W[p];
+#pragma unroll
+        for (int j = 0; j < V; ++j) x.e[j] *= inv;
+        VN[p] = x;
+        if (vb) VB[p] = x;
+    }
+    for (int64_t i = np * V + tid; i < n; i += stride) {
         const T vi = w[i] * inv;
         vnext[i] = vi;
         if (vb) vb[i] = vi;
@@ -224,26 +282,39 @@ __global__ void k_copy_ritz(const LzState *st, const double *val, double *ritz) 
     if (threadIdx.x == 0) ritz[st->k] = val[0];
 }
 
-// x (FP64) += s_j v_j for j = 0..k-1 from the stored basis, accumulated per
-// element in a two-float (FP32) or FP64 sum
+// x (FP64) = sum_j s_j v_j over the stored basis.  FP64 basis: FMA chain.
+// FP32 basis: each s_j is split into two floats once (shared memory) and the
+// products are accumulated per element in a two-float sum.
 template <typename T>
 __global__ void __launch_bounds__(kRedThreads) k_ritz_from_basis(const T *__restrict__ basis, const double *s, int k,
                                                                  int64_t n, double *__restrict__ x) {
-    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
-        if (sizeof(T) == 8) {
-            double acc = 0.0;
-            for (int j = 0; j < k; ++j) acc = fma(s[j], (double)basis[(int64_t)j * n + i], acc);
-            x[i] = acc;
-        } else {
-            FF acc{0.f, 0.f};
-            for (int j = 0; j < k; ++j) {
-                const float sh = (float)s[j];
-                const float sl = (float)(s[j] - (double)sh);
-                const float v = (float)basis[(int64_t)j * n + i];
-                ff_add_prod(acc, sh, v);
-                acc.lo += sl * v;
+    __shared__ float sh[1024], sl[1024];
+    __shared__ double sd[1024];
+    const int64_t tid = blockIdx.x * (int64_t)blockDim.x + threadIdx.x, stride = (int64_t)gridDim.x * blockDim.x;
+    for (int j0 = 0; j0 < k; j0 += 1024) {
+        const int jn = min(1024, k - j0);
+        __syncthreads();
+        for (int j = threadIdx.x; j < jn; j += blockDim.x) {
+            const double v = s[j0 + j];
+            sd[j] = v;
+            sh[j] = (float)v;
+            sl[j] = (float)(v - (double)(float)v);
+        }
+        __syncthreads();
+        for (int64_t i = tid; i < n; i += stride) {
+            if (sizeof(T) == 8) {
+                double acc = j0 ? x[i] : 0.0;
+                for (int j = 0; j < jn; ++j) acc = fma(sd[j], (double)basis[(int64_t)(j0 + j) * n + i], acc);
+                x[i] = acc;
+            } else {
+                FF acc{0.f, 0.f};
+                for (int j = 0; j < jn; ++j) {
+                    const float v = (float)basis[(int64_t)(j0 + j) * n + i];
+                    ff_add_prod(acc, sh[j], v);
+                    acc.lo += sl[j] * v;
+                }
+                x[i] = (j0 ? x[i] : 0.0) + ((double)acc.hi + (double)acc.lo);
             }
-            x[i] = (double)acc.hi + (double)acc.lo;
         }
     }
 }
@@ -311,27 +382,42 @@ struct Lz {
     int iters, reorth, store;
     int grid;
     cudaStream_t st;
-    DevBuf state, alpha, beta, part, coef, tri, svec, work, ritz_tmp;
-    DevBuf buf[3];
-    DevBuf basis;
-    double hv_ms = 0.0;
+    // work buffers live in the handle (kept between calls)
+    DevBuf &state, &alpha, &beta, &part, &coef, &tri, &svec, &work, &ritz_tmp;
+    DevBuf *buf;
+    DevBuf &basis, &x, &hx;
+    std::vector<cudaEvent_t> evs;   // profile: 5 events per H·v (stage boundaries)
+    explicit Lz(gbr_ham *h)
+        : H(h), state(h->lz_state), alpha(h->lz_alpha), beta(h->lz_beta), part(h->lz_part), coef(h->lz_coef),
+          tri(h->lz_tri), svec(h->lz_svec), work(h->lz_work), ritz_tmp(h->lz_ritz), buf(h->lz_buf),
+          basis(h->lz_basis), x(h->lz_x), hx(h->lz_hx) {}
 };
 
+// grows a handle-owned buffer to at least bytes (contents not kept)
+static int grow(DevBuf &b, size_t bytes) {
+    if (b.p && b.bytes >= bytes) return GBR_OK;
+    return b.alloc(bytes);
+}
+
 template <typename T>
-static int lz_step(Lz &z, int phase, bool pass2, cudaEvent_t *ev_hv, bool want_ritz) {
+static int lz_step(Lz &z, int phase, bool pass2, cudaEvent_t *ev4, bool want_ritz) {
     // buffers: v_k in B[phase], v_{k-1} in B[1 - phase], w = H v_k in B[2];
     // v_{k+1} overwrites v_{k-1}, so the next step uses phase 1 - phase
     const int64_t n = z.n;
     T *v = z.buf[phase].as<T>(), *vprev = z.buf[1 - phase].as<T>(), *w = z.buf[2].as<T>();
     LzState *st = z.state.as<LzState>();
-    if (ev_hv) cudaEventRecord(ev_hv[0], z.st);
-    int rc = hv_launch(z.H, v, w, z.fp, z.st);
+    int rc = hv_launch(z.H, v, w, z.fp, z.st, ev4);
     if (rc) return rc;
-    if (ev_hv) cudaEventRecord(ev_hv[1], z.st);
     double *part = z.part.as<double>();
+    int64_t nk = 0;
     k_step1<T><<<z.grid, kRedThreads, 0, z.st>>>(st, z.beta.as<double>(), vprev, v, w, n, part, pass2 ? 0 : 1);
-    if (!pass2) k_finalize<<<1, kRedThreads, 0, z.st>>>(st, z.alpha.as<double>(), z.beta.as<double>(), part, z.grid, 0, z.iters);
+    ++nk;
+    if (!pass2) {
+        k_finalize<<<1, kRedThreads, 0, z.st>>>(st, z.alpha.as<double>(), z.beta.as<double>(), part, z.grid, 0, z.iters);
+        ++nk;
+    }
     k_step2<T><<<z.grid, kRedThreads, 0, z.st>>>(st, z.alpha.as<double>(), v, w, n, part, (pass2 || z.reorth) ? 0 : 1);
+    ++nk;
     if (z.reorth && !pass2) {
         T *basis = z.basis.as<T>();
         const int gj = std::max(1, std::min<int>(z.grid, (int)((n + kRedThreads - 1) / kRedThreads)));
@@ -340,17 +426,25 @@ static int lz_step(Lz &z, int phase, bool pass2, cudaEvent_t *ev_hv, bool want_r
             k_multidot<T><<<g, kRedThreads, 0, z.st>>>(st, basis, w, n, part);
             k_multidot_fin<<<z.iters, kRedThreads, 0, z.st>>>(st, part, gj, z.coef.as<double>());
             k_multiaxpy<T><<<z.grid, kRedThreads, 0, z.st>>>(st, basis, z.coef.as<double>(), w, n);
+            nk += 3;
         }
         k_norm2<T><<<z.grid, kRedThreads, 0, z.st>>>(st, w, n, part);
+        ++nk;
     }
-    if (!pass2) k_finalize<<<1, kRedThreads, 0, z.st>>>(st, z.alpha.as<double>(), z.beta.as<double>(), part, z.grid, 1, z.iters);
+    if (!pass2) {
+        k_finalize<<<1, kRedThreads, 0, z.st>>>(st, z.alpha.as<double>(), z.beta.as<double>(), part, z.grid, 1, z.iters);
+        ++nk;
+    }
     if (want_ritz) {
         k_tridiag<<<1, kRedThreads, 0, z.st>>>(st, z.alpha.as<double>(), z.beta.as<double>(), 0, z.tri.as<double>(),
                                                nullptr, nullptr);
         k_copy_ritz<<<1, 32, 0, z.st>>>(st, z.tri.as<double>(), z.ritz_tmp.as<double>());
+        nk += 2;
     }
     k_step3<T><<<z.grid, kRedThreads, 0, z.st>>>(st, z.beta.as<double>(), w, vprev, (z.store && !pass2) ? z.basis.as<T>() : nullptr, n);
     k_advance<<<1, 32, 0, z.st>>>(st);
+    nk += 2;
+    count_launches(nk);
     GBR_LAUNCH_CHECK();
     return GBR_OK;
 }
@@ -362,8 +456,8 @@ static int lz_run(Lz &z, const double *d_v0, gbr_lanczos_result *res, const gbr_
     cudaStream_t s = z.st;
     LzState zero{};
     GBR_CUDA_TRY(cudaMemcpyAsync(z.state.p, &zero, sizeof(zero), cudaMemcpyHostToDevice, s));
-    GBR_CUDA_TRY(cudaMemsetAsync(z.beta.p, 0, z.beta.bytes, s));
-    GBR_CUDA_TRY(cudaMemsetAsync(z.alpha.p, 0, z.alpha.bytes, s));
+    GBR_CUDA_TRY(cudaMemsetAsync(z.beta.p, 0, sizeof(double) * (size_t)(z.iters + 2), s));
+    GBR_CUDA_TRY(cudaMemsetAsync(z.alpha.p, 0, sizeof(double) * (size_t)(z.iters + 2), s));
     T *B0 = z.buf[0].as<T>();
     k_cast_start<T><<<z.grid, kRedThreads, 0, s>>>(d_v0, B0, n);
     k_norm2<T><<<z.grid, kRedThreads, 0, s>>>(z.state.as<LzState>(), B0, n, z.part.as<double>());
@@ -371,29 +465,34 @@ static int lz_run(Lz &z, const double *d_v0, gbr_lanczos_result *res, const gbr_
     k_scale_start<T><<<z.grid, kRedThreads, 0, s>>>(B0, z.tri.as<double>() + 1, n);
     if (z.store) GBR_CUDA_TRY(cudaMemcpyAsync(z.basis.p, B0, (size_t)n * sizeof(T), cudaMemcpyDeviceToDevice, s));
     GBR_LAUNCH_CHECK();
+    count_launches(4);
 
-    cudaEvent_t e0, e1, eh[2];
-    cudaEventCreate(&e0); cudaEventCreate(&e1); cudaEventCreate(&eh[0]); cudaEventCreate(&eh[1]);
+    cudaEvent_t e0, e1;
+    cudaEventCreate(&e0); cudaEventCreate(&e1);
     cudaEventRecord(e0, s);
-    double hv_ms = 0.0;
     // graph mode: one graph per buffer phase, captured on a private stream
     // after two eager steps (which also set kernel attributes), replayed on s
+    const bool graphs = o->use_graph && !o->profile;
     cudaGraphExec_t gexec[2] = {nullptr, nullptr};
+    int64_t gnodes[2] = {0, 0};
     cudaStream_t cap = nullptr;
-    if (o->use_graph) GBR_CUDA_TRY(cudaStreamCreateWithFlags(&cap, cudaStreamNonBlocking));
+    if (graphs) GBR_CUDA_TRY(cudaStreamCreateWithFlags(&cap, cudaStreamNonBlocking));
     int rc = GBR_OK;
     int phase = 0;
     const bool want_ritz = h_ritz != nullptr;
     for (int k = 0; k < z.iters; ++k) {
-        if (o->use_graph && k >= 2) {
+        if (graphs && k >= 2) {
             if (!gexec[phase]) {
                 cudaStream_t keep = z.st;
                 z.st = cap;
+                const int64_t before = launch_count();
                 GBR_CUDA_TRY(cudaStreamBeginCapture(cap, cudaStreamCaptureModeThreadLocal));
                 rc = lz_step<T>(z, phase, false, nullptr, want_ritz);
                 cudaGraph_t g = nullptr;
                 cudaError_t ce = cudaStreamEndCapture(cap, &g);
                 z.st = keep;
+                gnodes[phase] = launch_count() - before;   // captured, not yet run
+                set_launch_count(before);
                 if (rc) { if (g) cudaGraphDestroy(g); break; }
                 if (ce != cudaSuccess) { rc = set_error(GBR_ECUDA, "graph capture failed: %s", cudaGetErrorString(ce)); break; }
                 ce = cudaGraphInstantiate(&gexec[phase], g, 0);
@@ -402,16 +501,19 @@ static int lz_run(Lz &z, const double *d_v0, gbr_lanczos_result *res, const gbr_
             }
             cudaError_t le = cudaGraphLaunch(gexec[phase], s);
             if (le != cudaSuccess) { rc = set_error(GBR_ECUDA, "graph launch failed: %s", cudaGetErrorString(le)); break; }
+            count_launches(gnodes[phase]);
         } else {
-            const bool t = !o->use_graph && (k == 0 || k == z.iters / 2);
-            rc = lz_step<T>(z, phase, false, t ? eh : nullptr, want_ritz);
-            if (rc) break;
-            if (t) {
-                cudaEventSynchronize(eh[1]);
-                float ms = 0.f;
-                cudaEventElapsedTime(&ms, eh[0], eh[1]);
-                hv_ms = std::max(hv_ms, (double)ms);
+            cudaEvent_t *ev4 = nullptr;
+            if (o->profile) {
+                for (int e = 0; e < 5; ++e) {
+                    cudaEvent_t ev;
+                    GBR_CUDA_TRY(cudaEventCreate(&ev));
+                    z.evs.push_back(ev);
+                }
+                ev4 = z.evs.data() + z.evs.size() - 5;
             }
+            rc = lz_step<T>(z, phase, false, ev4, want_ritz);
+            if (rc) break;
         }
         phase = 1 - phase;
         if ((k & 31) == 31) {
@@ -439,6 +541,7 @@ static int lz_run(Lz &z, const double *d_v0, gbr_lanczos_result *res, const gbr_
     k_tridiag<<<1, kRedThreads, 0, s>>>(z.state.as<LzState>(), z.alpha.as<double>(), z.beta.as<double>(), kdone, tri,
                                        o->refine ? z.svec.as<double>() : nullptr, z.work.as<double>());
     GBR_LAUNCH_CHECK();
+    count_launches(1);
     double Er = 0.0;
     GBR_CUDA_TRY(cudaMemcpyAsync(&Er, tri, 8, cudaMemcpyDeviceToHost, s));
     GBR_CUDA_TRY(cudaStreamSynchronize(s));
@@ -446,12 +549,13 @@ static int lz_run(Lz &z, const double *d_v0, gbr_lanczos_result *res, const gbr_
     res->E0 = Er;
     res->residual = -1.0;
     if (o->refine) {
-        DevBuf x, hx;
-        if ((rc = x.alloc((size_t)n * 8))) return rc;
-        if ((rc = hx.alloc((size_t)n * 8))) return rc;
+        DevBuf &x = z.x, &hx = z.hx;
+        if ((rc = grow(x, (size_t)n * 8))) return rc;
+        if ((rc = grow(hx, (size_t)n * 8))) return rc;
         double *sv = z.svec.as<double>();
         if (z.store) {
             k_ritz_from_basis<T><<<z.grid, kRedThreads, 0, s>>>(z.basis.as<T>(), sv, kdone, n, x.as<double>());
+            count_launches(1);
         } else {
             // second pass of the same recurrence with the stored scalars
             LzState zero2{};
@@ -460,10 +564,12 @@ static int lz_run(Lz &z, const double *d_v0, gbr_lanczos_result *res, const gbr_
             k_norm2<T><<<z.grid, kRedThreads, 0, s>>>(z.state.as<LzState>(), B0, n, z.part.as<double>());
             k_sum<<<1, kRedThreads, 0, s>>>(z.part.as<double>(), z.grid, z.tri.as<double>() + 1);
             k_scale_start<T><<<z.grid, kRedThreads, 0, s>>>(B0, z.tri.as<double>() + 1, n);
+            count_launches(4);
             int ph = 0;
             for (int j = 0; j < kdone; ++j) {
                 T *v = z.buf[ph].as<T>();
                 k_ritz_accum<T><<<z.grid, kRedThreads, 0, s>>>(v, sv, j, n, x.as<double>());
+                count_launches(1);
                 if (j + 1 < kdone) {
                     rc = lz_step<T>(z, ph, true, nullptr, false);
                     if (rc) return rc;
@@ -479,6 +585,7 @@ static int lz_run(Lz &z, const double *d_v0, gbr_lanczos_result *res, const gbr_
         k_dot64<<<z.grid, kRedThreads, 0, s>>>(x.as<double>(), x.as<double>(), n, part);
         k_sum<<<1, kRedThreads, 0, s>>>(part, z.grid, tri + 3);
         GBR_LAUNCH_CHECK();
+        count_launches(4);
         double hd[2];
         GBR_CUDA_TRY(cudaMemcpyAsync(hd, tri + 2, 16, cudaMemcpyDeviceToHost, s));
         GBR_CUDA_TRY(cudaStreamSynchronize(s));
@@ -486,6 +593,7 @@ static int lz_run(Lz &z, const double *d_v0, gbr_lanczos_result *res, const gbr_
         GBR_CUDA_TRY(cudaMemcpyAsync(tri + 4, &E, 8, cudaMemcpyHostToDevice, s));
         k_resid64<<<z.grid, kRedThreads, 0, s>>>(hx.as<double>(), x.as<double>(), tri + 4, n, part);
         k_sum<<<1, kRedThreads, 0, s>>>(part, z.grid, tri + 5);
+        count_launches(2);
         double r2 = 0.0;
         GBR_CUDA_TRY(cudaMemcpyAsync(&r2, tri + 5, 8, cudaMemcpyDeviceToHost, s));
         GBR_CUDA_TRY(cudaStreamSynchronize(s));
@@ -497,8 +605,19 @@ static int lz_run(Lz &z, const double *d_v0, gbr_lanczos_result *res, const gbr_
     float ms = 0.f;
     cudaEventElapsedTime(&ms, e0, e1);
     res->seconds = ms * 1e-3;
-    res->hv_seconds = hv_ms * 1e-3 * kdone;
-    cudaEventDestroy(e0); cudaEventDestroy(e1); cudaEventDestroy(eh[0]); cudaEventDestroy(eh[1]);
+    res->hv_seconds = 0.0;
+    for (size_t e = 0; e + 4 < z.evs.size(); e += 5) {
+        for (int st3 = 0; st3 < 4; ++st3) {
+            float t = 0.f;
+            cudaEventElapsedTime(&t, z.evs[e + st3], z.evs[e + st3 + 1]);
+            res->stage_seconds[st3] += t * 1e-3;
+            res->stage_launches[st3] += 1;
+            res->hv_seconds += t * 1e-3;
+        }
+    }
+    for (cudaEvent_t ev : z.evs) cudaEventDestroy(ev);
+    z.evs.clear();
+    cudaEventDestroy(e0); cudaEventDestroy(e1);
     if (h_alpha) GBR_CUDA_TRY(cudaMemcpy(h_alpha, z.alpha.p, sizeof(double) * (size_t)kdone, cudaMemcpyDeviceToHost));
     if (h_beta && kdone > 1)
         GBR_CUDA_TRY(cudaMemcpy(h_beta, z.beta.as<double>() + 1, sizeof(double) * (size_t)(kdone - 1), cudaMemcpyDeviceToHost));
@@ -518,40 +637,46 @@ extern "C" int gbr_lanczos(const gbr_ham *H, const gbr_lanczos_opts *o, const do
     if (o->prec != GBR_PREC_FP64 && o->prec != GBR_PREC_MIXED) return set_error(GBR_EINVAL, "unknown prec %d", o->prec);
     if ((uintptr_t)d_v0 & 7u) return set_error(GBR_EINVAL, "v0 must be 8-byte aligned");
     memset(res, 0, sizeof(*res));
-    Lz z;
-    z.H = H;
+    Lz z(const_cast<gbr_ham *>(H));
     z.n = H->D;
     z.fp = o->prec == GBR_PREC_MIXED ? 32 : 64;
     z.iters = (int)std::min<int64_t>(o->iters, H->D);
     z.reorth = o->reorth ? 1 : 0;
     z.st = (cudaStream_t)stream;
     const size_t es = z.fp == 64 ? 8 : 4;
-    int store = o->store_basis;
     const size_t basis_bytes = (size_t)(z.iters + 1) * (size_t)z.n * es;
-    if (z.reorth) store = 1;
-    if (store < 0) {
-        size_t fr = 0, tot = 0;
-        GBR_CUDA_TRY(cudaMemGetInfo(&fr, &tot));
-        const size_t need = basis_bytes + (size_t)z.n * (3 * es + 16) + ((size_t)1 << 30);
-        store = need < fr ? 1 : 0;
+    // the basis is needed by re-orthogonalisation; with refinement it makes
+    // the Ritz vector one pass instead of a second run of the recurrence
+    int store = 0;
+    if (z.reorth) {
+        store = 1;
+    } else if (o->refine) {
+        store = o->store_basis;
+        if (store < 0) {
+            size_t fr = 0, tot = 0;
+            GBR_CUDA_TRY(cudaMemGetInfo(&fr, &tot));
+            fr += z.basis.bytes;   // the cached basis is released before a larger one is taken
+            const size_t need = basis_bytes + (size_t)z.n * (3 * es + 16) + ((size_t)2 << 30);
+            store = need < fr ? 1 : 0;
+        }
     }
     z.store = store;
     const int64_t blocks = (z.n + kRedThreads - 1) / kRedThreads;
     z.grid = (int)std::max<int64_t>(1, std::min<int64_t>(blocks, (int64_t)sm_count() * 4));
     int rc;
-    if ((rc = z.state.alloc(sizeof(LzState)))) return rc;
-    if ((rc = z.alpha.alloc(sizeof(double) * (size_t)(z.iters + 2)))) return rc;
-    if ((rc = z.beta.alloc(sizeof(double) * (size_t)(z.iters + 2)))) return rc;
+    if ((rc = grow(z.state, sizeof(LzState)))) return rc;
+    if ((rc = grow(z.alpha, sizeof(double) * (size_t)(z.iters + 2)))) return rc;
+    if ((rc = grow(z.beta, sizeof(double) * (size_t)(z.iters + 2)))) return rc;
     const size_t nparts = (size_t)z.grid * (size_t)(z.reorth ? z.iters + 1 : 1);
-    if ((rc = z.part.alloc(sizeof(double) * nparts))) return rc;
-    if ((rc = z.coef.alloc(sizeof(double) * (size_t)(z.iters + 2)))) return rc;
-    if ((rc = z.tri.alloc(sizeof(double) * 16))) return rc;
-    if ((rc = z.svec.alloc(sizeof(double) * (size_t)(z.iters + 2)))) return rc;
-    if ((rc = z.work.alloc(sizeof(double) * 3 * (size_t)(z.iters + 2)))) return rc;
-    if ((rc = z.ritz_tmp.alloc(sizeof(double) * (size_t)(z.iters + 2)))) return rc;
+    if ((rc = grow(z.part, sizeof(double) * nparts))) return rc;
+    if ((rc = grow(z.coef, sizeof(double) * (size_t)(z.iters + 2)))) return rc;
+    if ((rc = grow(z.tri, sizeof(double) * 16))) return rc;
+    if ((rc = grow(z.svec, sizeof(double) * (size_t)(z.iters + 2)))) return rc;
+    if ((rc = grow(z.work, sizeof(double) * 3 * (size_t)(z.iters + 2)))) return rc;
+    if ((rc = grow(z.ritz_tmp, sizeof(double) * (size_t)(z.iters + 2)))) return rc;
     for (int i = 0; i < 3; ++i)
-        if ((rc = z.buf[i].alloc((size_t)z.n * es))) return rc;
-    if (z.store && (rc = z.basis.alloc(basis_bytes))) return rc;
+        if ((rc = grow(z.buf[i], (size_t)z.n * es))) return rc;
+    if (z.store && (rc = grow(z.basis, basis_bytes))) return rc;
     if (z.fp == 64) return lz_run<double>(z, d_v0, res, o, h_alpha, h_beta, h_ritz);
     return lz_run<float>(z, d_v0, res, o, h_alpha, h_beta, h_ritz);
 }

@@ -99,6 +99,54 @@ __global__ void __launch_bounds__(kRankThreads) k_comb_rank(const uint64_t *__re
     }
 }
 
+// Same as k_comb_rank on 16-byte aligned input: pairs of patterns per
+// 16-byte load, four pairs in flight per thread, pairs of ranks per store.
+template <typename RT> struct Pair;
+template <> struct Pair<uint32_t> { typedef uint2 t; static __device__ __forceinline__ uint2 make(uint32_t a, uint32_t b) { return make_uint2(a, b); } };
+template <> struct Pair<uint64_t> { typedef ulonglong2 t; static __device__ __forceinline__ ulonglong2 make(uint64_t a, uint64_t b) { return make_ulonglong2(a, b); } };
+
+template <typename E, typename RT, int QT>
+__global__ void __launch_bounds__(kRankThreads) k_comb_rank_pairs(const ulonglong2 *__restrict__ pat2, RT *__restrict__ out,
+                                                                  int64_t n, const StagK d, const E *__restrict__ gtab,
+                                                                  int64_t entries, int use_smem, int check) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const E *tab = gtab;
+    if (use_smem) {
+        stage_table<E>(reinterpret_cast<E *>(smem_raw), gtab, entries);
+        tab = reinterpret_cast<const E *>(smem_raw);
+    }
+    typedef typename Pair<RT>::t P;
+    P *out2 = reinterpret_cast<P *>(out);
+    const int64_t np = n >> 1;
+    const int64_t tile = (int64_t)kRankThreads * kRankItems;
+    for (int64_t base = (int64_t)blockIdx.x * tile; base < np; base += (int64_t)gridDim.x * tile) {
+        ulonglong2 a[kRankItems];
+#pragma unroll
+        for (int j = 0; j < kRankItems; ++j) {
+            const int64_t p = base + threadIdx.x + (int64_t)j * kRankThreads;
+            a[j] = p < np ? __ldcs(pat2 + p) : make_ulonglong2(0ull, 0ull);
+        }
+#pragma unroll
+        for (int j = 0; j < kRankItems; ++j) {
+            const int64_t p = base + threadIdx.x + (int64_t)j * kRankThreads;
+            if (p >= np) break;
+            RT r0 = (RT)stag_rank<E, QT>(d, tab, a[j].x);
+            RT r1 = (RT)stag_rank<E, QT>(d, tab, a[j].y);
+            if (check) {
+                if (!((d.M == 64 || (a[j].x >> d.M) == 0ull) && __popcll(a[j].x) == d.N)) r0 = (RT)~(RT)0;
+                if (!((d.M == 64 || (a[j].y >> d.M) == 0ull) && __popcll(a[j].y) == d.N)) r1 = (RT)~(RT)0;
+            }
+            __stcs(out2 + p, Pair<RT>::make(r0, r1));
+        }
+    }
+    if ((n & 1) && blockIdx.x == 0 && threadIdx.x == 0) {
+        const uint64_t a = reinterpret_cast<const uint64_t *>(pat2)[n - 1];
+        RT r = (RT)stag_rank<E, QT>(d, tab, a);
+        if (check && !((d.M == 64 || (a >> d.M) == 0ull) && __popcll(a) == d.N)) r = (RT)~(RT)0;
+        out[n - 1] = r;
+    }
+}
+
 // Eq. unrank: greedy combinatorial-number-system decomposition, the k-th set
 // bit at the largest c with C(c, k) <= remaining rank.
 template <typename RT>
@@ -204,12 +252,21 @@ static int launch_comb_rank(const gbr_comb *c, const uint64_t *pat, RT *out, int
     const size_t smem = use_smem ? (size_t)tbytes : 0;
     int per_sm = use_smem ? std::max<int>(1, std::min<int>(8, (int)((200 * 1024) / std::max<int64_t>(tbytes, 1)))) : 8;
     const int grid = grid_for(n, (int64_t)kRankThreads * kRankItems, per_sm);
+    const int grid2 = grid_for((n >> 1) + 1, (int64_t)kRankThreads * kRankItems, per_sm);
     const E *tab = c->table.as<E>();
+    const bool pairs = (((uintptr_t)pat & 15u) == 0) && (((uintptr_t)out & (2 * sizeof(RT) - 1)) == 0);
 #define GBR_COMB_CASE(QV)                                                                                  \
     case QV: {                                                                                             \
-        auto kern = k_comb_rank<E, RT, QV>;                                                                \
-        if (smem > 48 * 1024) GBR_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)); \
-        kern<<<grid, kRankThreads, smem, st>>>(pat, out, n, d, tab, c->desc.entries, use_smem, check);     \
+        if (pairs) {                                                                                       \
+            auto kern = k_comb_rank_pairs<E, RT, QV>;                                                      \
+            if (smem > 48 * 1024) GBR_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)); \
+            kern<<<grid2, kRankThreads, smem, st>>>(reinterpret_cast<const ulonglong2 *>(pat), out, n, d, tab, \
+                                                    c->desc.entries, use_smem, check);                     \
+        } else {                                                                                           \
+            auto kern = k_comb_rank<E, RT, QV>;                                                            \
+            if (smem > 48 * 1024) GBR_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)); \
+            kern<<<grid, kRankThreads, smem, st>>>(pat, out, n, d, tab, c->desc.entries, use_smem, check); \
+        }                                                                                                  \
         break;                                                                                             \
     }
     switch (d.Q) {
@@ -225,6 +282,7 @@ static int launch_comb_rank(const gbr_comb *c, const uint64_t *pat, RT *out, int
     }
 #undef GBR_COMB_CASE
     GBR_LAUNCH_CHECK();
+    count_launches(1);
     return GBR_OK;
 }
 
@@ -256,6 +314,7 @@ static int launch_trie_rank(const gbr_trie *T, const uint64_t *pat, RT *out, int
     }
 #undef GBR_TRIE_CASE
     GBR_LAUNCH_CHECK();
+    count_launches(1);
     return GBR_OK;
 }
 
@@ -348,6 +407,7 @@ extern "C" int gbr_comb_unrank(const gbr_comb *c, const void *d_rank, int rank_b
         k_comb_unrank<uint64_t><<<grid, 256, 0, st>>>((const uint64_t *)d_rank, d_pat, n, c->desc.M, c->desc.N, c->dim,
                                                       c->binom.as<uint64_t>());
     GBR_LAUNCH_CHECK();
+    count_launches(1);
     return GBR_OK;
 }
 
@@ -440,5 +500,6 @@ extern "C" int gbr_trie_unrank(const gbr_trie *t, const void *d_rank, int rank_b
         k_list_unrank<uint64_t><<<grid, 256, 0, st>>>((const uint64_t *)d_rank, d_pat, n, t->members.as<uint64_t>(),
                                                       t->n_members);
     GBR_LAUNCH_CHECK();
+    count_launches(1);
     return GBR_OK;
 }

@@ -68,10 +68,14 @@ __device__ double tridiag_lowest_block(const double *a, const double *b, int k) 
 // with Thomas elimination (tiny pivots replaced), three sweeps, normalised.
 // One thread; work holds 3k doubles.
 __device__ void tridiag_vector_thread(const double *a, const double *b, int k, double lam, double *s, double *work) {
+    if (k == 1) {
+        s[0] = 1.0;
+        return;
+    }
     double *dd = work, *zz = work + 2 * k;
     double tn = 0.0;
     for (int i = 0; i < k; ++i) tn = fmax(tn, fabs(a[i]) + (i ? fabs(b[i]) : 0.0));
-    const double tiny = 1e-14 * fmax(tn, 1e-300);
+    const double tiny = fmax(1e-14 * tn, 1e-290);
     for (int i = 0; i < k; ++i) zz[i] = 1.0;
     for (int sweep = 0; sweep < 3; ++sweep) {
         double piv = a[0] - lam;
@@ -86,8 +90,18 @@ __device__ void tridiag_vector_thread(const double *a, const double *b, int k, d
         }
         zz[k - 1] /= dd[k - 1];
         for (int i = k - 2; i >= 0; --i) zz[i] = (zz[i] - b[i + 1] * zz[i + 1]) / dd[i];
+        // scale by the largest entry first so that the norm cannot overflow
+        double mx = 0.0;
+        for (int i = 0; i < k; ++i) mx = fmax(mx, fabs(zz[i]));
+        if (!(mx > 0.0) || !isfinite(mx)) {
+            for (int i = 0; i < k; ++i) zz[i] = i == 0 ? 1.0 : 0.0;
+            continue;
+        }
         double nrm = 0.0;
-        for (int i = 0; i < k; ++i) nrm += zz[i] * zz[i];
+        for (int i = 0; i < k; ++i) {
+            zz[i] /= mx;
+            nrm += zz[i] * zz[i];
+        }
         nrm = sqrt(nrm);
         for (int i = 0; i < k; ++i) zz[i] /= nrm;
     }

@@ -36,13 +36,13 @@ class GbrError(RuntimeError):
 
 class LanczosOpts(C.Structure):
     _fields_ = [("iters", C.c_int), ("reorth", C.c_int), ("prec", C.c_int), ("refine", C.c_int),
-                ("store_basis", C.c_int), ("use_graph", C.c_int)]
+                ("store_basis", C.c_int), ("use_graph", C.c_int), ("profile", C.c_int)]
 
 
 class LanczosResult(C.Structure):
     _fields_ = [("E0", C.c_double), ("E_ritz", C.c_double), ("residual", C.c_double), ("iters_done", C.c_int),
                 ("breakdown", C.c_int), ("stored_basis", C.c_int), ("seconds", C.c_double),
-                ("hv_seconds", C.c_double)]
+                ("hv_seconds", C.c_double), ("stage_seconds", C.c_double * 4), ("stage_launches", C.c_int * 4)]
 
 
 class ModelDesc(C.Structure):
@@ -78,6 +78,8 @@ def lib():
                 "gbr_ham_set_path": (i32, [vp, i32]),
                 "gbr_hv": (i32, [vp, vp, vp, i32, vp]),
                 "gbr_ham_tune": (i32, [vp, i32, vp]),
+                "gbr_hv_stage": (i32, [vp, vp, vp, i32, i32, vp]),
+                "gbr_launch_count": (i64, []),
                 "gbr_lanczos": (i32, [vp, vp, vp, vp, vp, vp, vp, vp]),
                 "gbr_batch_layout": (i32, [i32, vp, vp, vp]),
                 "gbr_batch_solve": (i32, [i32, vp, vp, i32, vp, vp, vp, vp]),
@@ -270,10 +272,25 @@ def gbr_hv(H: Ham, x, y, stream=None):
     return y
 
 
-def gbr_lanczos(H: Ham, v0, iters: int, reorth: bool = False, prec: int = GBR_PREC_MIXED, refine: bool = True,
-                store_basis: int = -1, use_graph: bool = False, want_ritz: bool = False, stream=None) -> dict:
+def gbr_hv_stage(H: Ham, x, y, stage: int, stream=None):
     import torch
-    o = LanczosOpts(iters, int(bool(reorth)), prec, int(bool(refine)), store_basis, int(bool(use_graph)))
+    fp = {torch.float32: 32, torch.float64: 64}.get(x.dtype)
+    if fp is None or y.dtype != x.dtype:
+        raise ValueError("x and y must both be float32 or float64")
+    _check(lib().gbr_hv_stage(H, _dptr(x), _dptr(y), fp, stage, _stream(stream)))
+    return y
+
+
+def gbr_launch_count() -> int:
+    return lib().gbr_launch_count()
+
+
+def gbr_lanczos(H: Ham, v0, iters: int, reorth: bool = False, prec: int = GBR_PREC_MIXED, refine: bool = True,
+                store_basis: int = -1, use_graph: bool = False, want_ritz: bool = False, profile: bool = False,
+                stream=None) -> dict:
+    import torch
+    o = LanczosOpts(iters, int(bool(reorth)), prec, int(bool(refine)), store_basis, int(bool(use_graph)),
+                    int(bool(profile)))
     r = LanczosResult()
     a = np.zeros(iters, dtype=np.float64)
     b = np.zeros(max(iters, 1), dtype=np.float64)
@@ -283,6 +300,7 @@ def gbr_lanczos(H: Ham, v0, iters: int, reorth: bool = False, prec: int = GBR_PR
     k = r.iters_done
     return dict(E0=r.E0, E_ritz=r.E_ritz, residual=r.residual, iters=k, breakdown=bool(r.breakdown),
                 stored_basis=bool(r.stored_basis), seconds=r.seconds, hv_seconds=r.hv_seconds,
+                stage_seconds=list(r.stage_seconds), stage_launches=list(r.stage_launches),
                 alpha=a[:k].copy(), beta=b[:max(k - 1, 0)].copy(), ritz=None if rz is None else rz[:k].copy())
 
 
