@@ -349,6 +349,25 @@ def run_ours(args, rank: int, world: int):
         print(json.dumps(line), flush=True)
 
 
+def profile_hv(n: int):
+    """A few FP32 H·v calls on the benchmark sector (no timing, no output):
+    the target of the ncu captures summarised under profiles/."""
+    import torch
+    import __graft_entry__
+    __graft_entry__.build()
+    import gbr_synth as S
+    import gbr_synth.gpu as SG
+    import paper_2203_04158_gb300 as G
+    h, U = model()
+    H = G.gbr_ham_create(L, h, U, NUP, NDN)
+    D, _ = G.gbr_ham_info(H)
+    x = SG.uniform(S.SEED_START, D).float()
+    y = torch.empty_like(x)
+    for _ in range(n):
+        G.gbr_hv(H, x, y)
+    torch.cuda.synchronize()
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -358,7 +377,12 @@ def main():
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--no-extras", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--profile-hv", type=int, default=0,
+                    help="run this many FP32 H·v calls on the workload sector and exit (for ncu captures)")
     args = ap.parse_args()
+    if args.profile_hv:
+        profile_hv(args.profile_hv)
+        return
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
     if args.impl == "reference":

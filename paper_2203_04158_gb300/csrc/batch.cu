@@ -219,17 +219,22 @@ __global__ void __launch_bounds__(kBatchThreads) k_batch(const SectorDesc *__res
         build_spin(L, sd.Ndn, sd.Ddn, hmax, hs, bidx, bin, dn);
         const int D = sd.Dup * sd.Ddn;
         const int K = min(iters, D);
-        // Two cycles: the second restarts from the (FP32-rounded) Ritz vector of
-        // the first, which removes what the FP32 recurrence lost.  Each cycle
-        // runs the recurrence twice: once for the scalars, once more (bit
-        // identical) to accumulate the Ritz vector x in FP64.
+        // Restarted Lanczos: each cycle stops as soon as the lowest Ritz pair
+        // of T has converged to FP32 level (residual estimate
+        // beta_{k+1} |s_k| <= 1e-6 max(|alpha|, beta)), which keeps the FP32
+        // recurrence from running on after convergence and spoiling the Ritz
+        // vector; a cycle that ends unconverged restarts from its Ritz vector
+        // (at most three cycles).  Each cycle runs the recurrence twice: once
+        // for the scalars, once more (bit identical) to accumulate the Ritz
+        // vector x in FP64.
+        __shared__ int conv_s;
         int kdone = 0;
-        for (int cyc = 0; cyc < 2; ++cyc) {
-            if (cyc == 1) {
+        for (int cyc = 0; cyc < 3; ++cyc) {
+            if (cyc > 0) {
                 for (int i = threadIdx.x; i < D; i += blockDim.x) hx[i] = x[i];
                 __syncthreads();
             }
-            const int Kc = cyc == 0 ? K : min(K, max(24, K / 2));
+            const int Kc = K;
             float fh = 0.f, fl = 0.f;
             for (int i = threadIdx.x; i < D; i += blockDim.x) {
                 const float s = (float)(cyc == 0 ? start[sd.off + i] : hx[i]);
@@ -238,6 +243,8 @@ __global__ void __launch_bounds__(kBatchThreads) k_batch(const SectorDesc *__res
             const double n0 = sqrt(bsum((double)fh + (double)fl, red));
             double scale = 0.0;
             kdone = 0;
+            if (threadIdx.x == 0) conv_s = 0;
+            __syncthreads();
             for (int pass = 0; pass < 2; ++pass) {
                 for (int i = threadIdx.x; i < D; i += blockDim.x) {
                     const float s = (float)(cyc == 0 ? start[sd.off + i] : hx[i]);
@@ -280,10 +287,16 @@ __global__ void __launch_bounds__(kBatchThreads) k_batch(const SectorDesc *__res
                         const double b = sqrt(fmax(bsum((double)bh + (double)bl, red), 0.0));
                         if (threadIdx.x == 0) beta[k + 1] = b;
                         kdone = k + 1;
-                        const bool stop = (k + 1 >= Kc) || (b <= 1e-13 * fmax(scale, b));
                         scale = fmax(scale, b);
                         __syncthreads();
-                        if (stop) break;
+                        // lowest Ritz pair of T_{k+1} and its residual estimate
+                        const double lam = tridiag_lowest_block(alpha, beta, kdone);
+                        if (threadIdx.x == 0) {
+                            tridiag_vector_thread(alpha, beta, kdone, lam, svec, work);
+                            if (b * fabs(svec[kdone - 1]) <= 1e-6 * scale || b <= 1e-13 * scale) conv_s = 1;
+                        }
+                        __syncthreads();
+                        if (conv_s || k + 1 >= Kc) break;
                     }
                     __syncthreads();
                     const float inv = (float)(1.0 / beta[k + 1]);
@@ -294,13 +307,9 @@ __global__ void __launch_bounds__(kBatchThreads) k_batch(const SectorDesc *__res
                     }
                     __syncthreads();
                 }
-                if (pass == 0) {
-                    const double lam = tridiag_lowest_block(alpha, beta, kdone);
-                    if (threadIdx.x == 0) tridiag_vector_thread(alpha, beta, kdone, lam, svec, work);
-                    __syncthreads();
-                }
             }
             __syncthreads();
+            if (conv_s) break;
         }
         __syncthreads();
         // FP64 Rayleigh quotient of the Ritz vector

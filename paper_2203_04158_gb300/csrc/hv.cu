@@ -330,12 +330,22 @@ __global__ void __launch_bounds__(128) k_gather(const int64_t Drows, const int64
             const uint32_t au = ca.st_up[r];
             const T du = ((const T *)ca.dup)[r];
             const T *zt = (const T *)ca.zt;
+            T xo[VEC];
+            if (VEC == 4 && sizeof(T) == 4) {
+                const float4 o = __ldg(reinterpret_cast<const float4 *>(x + r * Dcols + c0));
+                xo[0] = o.x; xo[1 % VEC] = o.y; xo[2 % VEC] = o.z; xo[3 % VEC] = o.w;
+            } else if (VEC == 2) {
+                const typename Vec<T>::v2 o = __ldg(reinterpret_cast<const typename Vec<T>::v2 *>(x + r * Dcols + c0));
+                xo[0] = o.x; xo[1 % VEC] = o.y;
+            } else {
+                xo[0] = __ldg(x + r * Dcols + c0);
+            }
 #pragma unroll
             for (int v = 0; v < VEC; ++v) {
                 const uint32_t both = au & ad[v];
                 T dg = du + dd[v];
                 for (int u = 0; u < ca.hk.nucls; ++u) dg += uval[u] * (T)__popc(both & ca.hk.umask[u]);
-                acc[v] += dg * x[r * Dcols + c0 + v] + __ldg(zt + (c0 + v) * Drows + r);
+                acc[v] += dg * xo[v] + __ldg(zt + (c0 + v) * Drows + r);
             }
         }
         if (VEC == 4 && sizeof(T) == 4) {
@@ -426,7 +436,7 @@ static int launch_gather(const gbr_ham *H, const SpinSector &lists, int64_t Drow
     // widest vector whose column chunk (all rows x 128*VEC columns) stays
     // well inside L2
     for (int v = vmax; v >= 2; v /= 2)
-        if (aligned16 && Dcols % v == 0 && (double)Drows * 128 * v * sizeof(T) <= 48e6) { vec = v; break; }
+        if (aligned16 && Dcols % v == 0 && (double)Drows * 128 * v * sizeof(T) <= 64e6) { vec = v; break; }
     const int TR = H->tune_up_rows[fpi] ? H->tune_up_rows[fpi] : 8;
     const int64_t nrb = (Drows + TR - 1) / TR;
     const int64_t ncc = (Dcols + 128 * vec - 1) / (128 * vec);

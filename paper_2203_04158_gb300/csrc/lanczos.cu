@@ -284,12 +284,17 @@ __global__ void k_copy_ritz(const LzState *st, const double *val, double *ritz) 
 
 // x (FP64) = sum_j s_j v_j over the stored basis.  FP64 basis: FMA chain.
 // FP32 basis: each s_j is split into two floats once (shared memory) and the
-// products are accumulated per element in a two-float sum.
+// products are accumulated per element in a two-float sum.  Each thread
+// takes 16-byte packs of consecutive elements, so one load per basis vector
+// serves several elements.
 template <typename T>
 __global__ void __launch_bounds__(kRedThreads) k_ritz_from_basis(const T *__restrict__ basis, const double *s, int k,
                                                                  int64_t n, double *__restrict__ x) {
     __shared__ float sh[1024], sl[1024];
     __shared__ double sd[1024];
+    constexpr int V = Pack<T>::N;
+    const bool vec_ok = (n % V) == 0;       // every basis slot then starts on a 16-byte boundary
+    const int64_t np = vec_ok ? n / V : 0;
     const int64_t tid = blockIdx.x * (int64_t)blockDim.x + threadIdx.x, stride = (int64_t)gridDim.x * blockDim.x;
     for (int j0 = 0; j0 < k; j0 += 1024) {
         const int jn = min(1024, k - j0);
@@ -301,7 +306,40 @@ __global__ void __launch_bounds__(kRedThreads) k_ritz_from_basis(const T *__rest
             sl[j] = (float)(v - (double)(float)v);
         }
         __syncthreads();
-        for (int64_t i = tid; i < n; i += stride) {
+        for (int64_t p = tid; p < np; p += stride) {
+            const Pack<T> *B = reinterpret_cast<const Pack<T> *>(basis + (int64_t)j0 * n) + p;
+            const int64_t sp = n / V;   // packs per basis vector
+            if (sizeof(T) == 8) {
+                double acc[V];
+#pragma unroll
+                for (int e = 0; e < V; ++e) acc[e] = j0 ? x[p * V + e] : 0.0;
+#pragma unroll 4
+                for (int j = 0; j < jn; ++j) {
+                    const Pack<T> b = B[(int64_t)j * sp];
+#pragma unroll
+                    for (int e = 0; e < V; ++e) acc[e] = fma(sd[j], (double)b.e[e], acc[e]);
+                }
+#pragma unroll
+                for (int e = 0; e < V; ++e) x[p * V + e] = acc[e];
+            } else {
+                FF acc[V];
+#pragma unroll
+                for (int e = 0; e < V; ++e) acc[e] = FF{0.f, 0.f};
+#pragma unroll 4
+                for (int j = 0; j < jn; ++j) {
+                    const Pack<T> b = B[(int64_t)j * sp];
+#pragma unroll
+                    for (int e = 0; e < V; ++e) {
+                        const float v = (float)b.e[e];
+                        ff_add_prod(acc[e], sh[j], v);
+                        acc[e].lo += sl[j] * v;
+                    }
+                }
+#pragma unroll
+                for (int e = 0; e < V; ++e) x[p * V + e] = (j0 ? x[p * V + e] : 0.0) + ((double)acc[e].hi + (double)acc[e].lo);
+            }
+        }
+        for (int64_t i = np * V + tid; i < n; i += stride) {
             if (sizeof(T) == 8) {
                 double acc = j0 ? x[i] : 0.0;
                 for (int j = 0; j < jn; ++j) acc = fma(sd[j], (double)basis[(int64_t)(j0 + j) * n + i], acc);
