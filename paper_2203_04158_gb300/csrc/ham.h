@@ -69,4 +69,6 @@ namespace gbr {
 // the fused path records the first four before its single kernel.
 int hv_launch(const gbr_ham *H, const void *x, void *y, int fp, cudaStream_t st, cudaEvent_t *ev = nullptr);
 int hv_stage(const gbr_ham *H, const void *x, void *y, int fp, int stage, cudaStream_t st);
+// factored path with the two scratch vectors (dim elements each) supplied
+int hv_factored_with_scratch(const gbr_ham *H, const void *x, void *y, int fp, cudaStream_t st, void *xt, void *zt);
 }

@@ -280,6 +280,22 @@ __global__ void __launch_bounds__(128) k_gather(const int64_t Drows, const int64
     }
     __syncthreads();
     const int64_t c0 = cc * (int64_t)(128 * VEC) + (int64_t)threadIdx.x * VEC;
+    // combine epilogue: the block Z[r0..r0+TR, chunk] = (Z^T)[chunk, r0..r0+TR]
+    // is read from Z^T once, column by column (TR consecutive values each),
+    // into shared memory as [row][column]
+    T *zs = reinterpret_cast<T *>(smr + (((size_t)TR * hmax * 4 + 15) & ~(size_t)15) +
+                                  (((size_t)TR * hmax * sizeof(T) + 15) & ~(size_t)15));
+    if (COMBINE) {
+        const T *zt = (const T *)ca.zt;
+        const int64_t cbase = cc * (int64_t)(128 * VEC);
+        const int nrow = (int)((Drows - r0) < (int64_t)TR ? (Drows - r0) : (int64_t)TR);
+        for (int e = threadIdx.x; e < 128 * VEC * TR; e += blockDim.x) {
+            const int col = e / TR, i = e % TR;
+            const int64_t c = cbase + col;
+            zs[i * (128 * VEC) + col] = (c < Dcols && i < nrow) ? __ldg(zt + c * Drows + r0 + i) : T(0);
+        }
+        __syncthreads();
+    }
     if (c0 >= Dcols) return;
     // combine epilogue: column states and diagonals of this thread's columns
     uint32_t ad[VEC];
@@ -307,7 +323,7 @@ __global__ void __launch_bounds__(128) k_gather(const int64_t Drows, const int64
             float4 a4 = make_float4(0.f, 0.f, 0.f, 0.f);
 #pragma unroll 4
             for (int k = 0; k < n; ++k) {
-                const float4 v = __ldg(reinterpret_cast<const float4 *>(x + (int64_t)ti[k] * Dcols + c0));
+                const float4 v = __ldcg(reinterpret_cast<const float4 *>(x + (int64_t)ti[k] * Dcols + c0));
                 const float c = (float)ci[k];
                 a4.x += c * v.x; a4.y += c * v.y; a4.z += c * v.z; a4.w += c * v.w;
             }
@@ -316,20 +332,19 @@ __global__ void __launch_bounds__(128) k_gather(const int64_t Drows, const int64
             T a0 = 0, a1 = 0;
 #pragma unroll 4
             for (int k = 0; k < n; ++k) {
-                const typename Vec<T>::v2 v = __ldg(reinterpret_cast<const typename Vec<T>::v2 *>(x + (int64_t)ti[k] * Dcols + c0));
+                const typename Vec<T>::v2 v = __ldcg(reinterpret_cast<const typename Vec<T>::v2 *>(x + (int64_t)ti[k] * Dcols + c0));
                 a0 += ci[k] * v.x; a1 += ci[k] * v.y;
             }
             acc[0] = a0; acc[1 % VEC] = a1;
         } else {
             T a0 = 0;
 #pragma unroll 4
-            for (int k = 0; k < n; ++k) a0 += ci[k] * __ldg(x + (int64_t)ti[k] * Dcols + c0);
+            for (int k = 0; k < n; ++k) a0 += ci[k] * __ldcg(x + (int64_t)ti[k] * Dcols + c0);
             acc[0] = a0;
         }
         if (COMBINE) {
             const uint32_t au = ca.st_up[r];
             const T du = ((const T *)ca.dup)[r];
-            const T *zt = (const T *)ca.zt;
             T xo[VEC];
             if (VEC == 4 && sizeof(T) == 4) {
                 const float4 o = __ldg(reinterpret_cast<const float4 *>(x + r * Dcols + c0));
@@ -345,7 +360,7 @@ __global__ void __launch_bounds__(128) k_gather(const int64_t Drows, const int64
                 const uint32_t both = au & ad[v];
                 T dg = du + dd[v];
                 for (int u = 0; u < ca.hk.nucls; ++u) dg += uval[u] * (T)__popc(both & ca.hk.umask[u]);
-                acc[v] += dg * xo[v] + __ldg(zt + (c0 + v) * Drows + r);
+                acc[v] += dg * xo[v] + zs[i * (128 * VEC) + threadIdx.x * VEC + v];
             }
         }
         if (VEC == 4 && sizeof(T) == 4) {
@@ -416,7 +431,12 @@ static int stage_hop_lists(const gbr_ham *H, cudaStream_t st) {
     return rc;
 }
 
-// scratch of the factored path: X^T and Z^T, owned by the handle
+// scratch of the factored path: X^T and Z^T, owned by the handle unless the
+// caller supplies them (gbr_hv_static)
+struct Scratch {
+    void *xt, *zt;
+};
+
 static int ensure_ws(const gbr_ham *H, size_t bytes) {
     gbr_ham *h = const_cast<gbr_ham *>(H);
     if (h->ws_xt.bytes >= bytes && h->ws_zt.bytes >= bytes) return GBR_OK;
@@ -441,7 +461,8 @@ static int launch_gather(const gbr_ham *H, const SpinSector &lists, int64_t Drow
     const int64_t nrb = (Drows + TR - 1) / TR;
     const int64_t ncc = (Dcols + 128 * vec - 1) / (128 * vec);
     const int hmax = std::max(1, lists.hmax);
-    const size_t smem = (((size_t)TR * hmax * 4 + 15) & ~(size_t)15) + (size_t)TR * hmax * sizeof(T);
+    const size_t smem = (((size_t)TR * hmax * 4 + 15) & ~(size_t)15) + (((size_t)TR * hmax * sizeof(T) + 15) & ~(size_t)15) +
+                        (COMBINE ? (size_t)TR * 128 * vec * sizeof(T) : 0);
     const int64_t blocks = nrb * ncc;
     if (blocks > 0x7FFFFFFF) return set_error(GBR_EINVAL, "sector too large for the gather grid");
 #define GBR_G(V)                                                                                             \
@@ -460,14 +481,17 @@ static int launch_gather(const gbr_ham *H, const SpinSector &lists, int64_t Drow
 }
 
 template <typename T>
-static int stage_transpose(const gbr_ham *H, const T *x, cudaStream_t st) {
-    int rc = ensure_ws(H, (size_t)H->D * sizeof(T));
-    if (rc) return rc;
+static int stage_transpose(const gbr_ham *H, const T *x, cudaStream_t st, const Scratch *ws = nullptr) {
+    if (!ws) {
+        int rc = ensure_ws(H, (size_t)H->D * sizeof(T));
+        if (rc) return rc;
+    }
+    T *xt = ws ? (T *)ws->xt : H->ws_xt.as<T>();
     const int64_t Dup = H->up.D, Ddn = H->dn.D;
     constexpr int TILE = 64;
     dim3 grid((unsigned)((Ddn + TILE - 1) / TILE), (unsigned)((Dup + TILE - 1) / TILE));
     if (grid.y > 65535) return set_error(GBR_EINVAL, "sector too large for the transpose grid");
-    k_transpose<T, TILE><<<grid, dim3(TILE, 4), 0, st>>>(x, H->ws_xt.as<T>(), Dup, Ddn);
+    k_transpose<T, TILE><<<grid, dim3(TILE, 4), 0, st>>>(x, xt, Dup, Ddn);
     GBR_LAUNCH_CHECK();
     count_launches(1);
     return GBR_OK;
@@ -475,37 +499,40 @@ static int stage_transpose(const gbr_ham *H, const T *x, cudaStream_t st) {
 
 // Z^T = H_dn X^T (rows: spin-down states, columns: spin-up states)
 template <typename T>
-static int stage_dn(const gbr_ham *H, cudaStream_t st, const HamDev &hd) {
+static int stage_dn(const gbr_ham *H, cudaStream_t st, const HamDev &hd, const Scratch *ws = nullptr) {
     CombineArgs ca{};
-    return launch_gather<T, false>(H, dn_lists(H), H->dn.D, H->up.D, H->ws_xt.as<T>(), H->ws_zt.as<T>(), ca, st, hd);
+    T *xt = ws ? (T *)ws->xt : H->ws_xt.as<T>();
+    T *zt = ws ? (T *)ws->zt : H->ws_zt.as<T>();
+    return launch_gather<T, false>(H, dn_lists(H), H->dn.D, H->up.D, xt, zt, ca, st, hd);
 }
 
 // Y = H_up X + Dg o X + (Z^T)^T
 template <typename T>
-static int stage_up(const gbr_ham *H, const T *x, T *y, cudaStream_t st, const HamDev &hd) {
+static int stage_up(const gbr_ham *H, const T *x, T *y, cudaStream_t st, const HamDev &hd,
+                    const Scratch *ws = nullptr) {
     CombineArgs ca;
     ca.st_up = H->up.states.as<uint32_t>();
     ca.st_dn = H->dn.states.as<uint32_t>();
     ca.dup = hd.dup;
     ca.ddn = hd.ddn;
     ca.uval = hd.uval;
-    ca.zt = H->ws_zt.p;
+    ca.zt = ws ? ws->zt : H->ws_zt.p;
     ca.hk = H->k;
     return launch_gather<T, true>(H, H->up, H->up.D, H->dn.D, x, y, ca, st, hd);
 }
 
 template <typename T>
 static int launch_factored(const gbr_ham *H, const T *x, T *y, cudaStream_t st, const HamDev &hd,
-                           cudaEvent_t *ev = nullptr) {
+                           cudaEvent_t *ev = nullptr, const Scratch *ws = nullptr) {
     if (ev) cudaEventRecord(ev[0], st);
     int rc = stage_hop_lists<T>(H, st);
     if (rc) return rc;
     if (ev) cudaEventRecord(ev[1], st);
-    if ((rc = stage_transpose<T>(H, x, st))) return rc;
+    if ((rc = stage_transpose<T>(H, x, st, ws))) return rc;
     if (ev) cudaEventRecord(ev[2], st);
-    if ((rc = stage_dn<T>(H, st, hd))) return rc;
+    if ((rc = stage_dn<T>(H, st, hd, ws))) return rc;
     if (ev) cudaEventRecord(ev[3], st);
-    if ((rc = stage_up<T>(H, x, y, st, hd))) return rc;
+    if ((rc = stage_up<T>(H, x, y, st, hd, ws))) return rc;
     if (ev) cudaEventRecord(ev[4], st);
     return GBR_OK;
 }
@@ -538,6 +565,15 @@ int hv_launch(const gbr_ham *H, const void *x, void *y, int fp, cudaStream_t st,
     }
     if (fp == 64) return launch_factored<double>(H, (const double *)x, (double *)y, st, hd, ev);
     return launch_factored<float>(H, (const float *)x, (float *)y, st, hd, ev);
+}
+
+int hv_factored_with_scratch(const gbr_ham *H, const void *x, void *y, int fp, cudaStream_t st, void *xt, void *zt) {
+    const int fpi = fp == 64 ? 1 : 0;
+    gbr_ham_prec *pb = prec_bufs(H, fpi);
+    HamDev hd{pb->dup.p, pb->ddn.p, pb->uval.p, pb->bcoef.p, pb->hcoef.p};
+    const Scratch ws{xt, zt};
+    if (fp == 64) return launch_factored<double>(H, (const double *)x, (double *)y, st, hd, nullptr, &ws);
+    return launch_factored<float>(H, (const float *)x, (float *)y, st, hd, nullptr, &ws);
 }
 
 int hv_stage(const gbr_ham *H, const void *x, void *y, int fp, int stage, cudaStream_t st) {
