@@ -189,6 +189,26 @@ int gbr_ham_set_path(gbr_ham *H, int path);
  *   first use): calls on one handle must not overlap. */
 int gbr_hv(const gbr_ham *H, const void *d_x, void *d_y, int fp, void *stream);
 
+/* gbr_hv for callers that cannot allocate device memory when they multiply
+ * (for example code running while a stream is captured into a CUDA graph,
+ * or under a fixed memory budget).  The paper has no counterpart: this is
+ * an interface of this library.  It computes exactly what gbr_hv's factored
+ * path computes, but its two scratch vectors live in one static device array
+ * of 64 MiB that every GPU loading the library reserves until the process
+ * exits, so the call itself allocates nothing (no cudaMalloc or cudaFree).
+ *   Limit: 2 * dim * (fp / 8) bytes, each vector rounded up to 256 bytes,
+ *   must fit in 64 MiB (dim up to about 8.4 million in FP32, 4.2 million in
+ *   FP64); larger sectors return GBR_EINVAL before anything is launched.
+ *   Set-up: the first call on a device looks up the array's device address
+ *   (cudaGetSymbolAddress) with that device current; make that first call
+ *   before any stream capture.
+ *   Sharing: every call on a device uses the same array, so calls that can
+ *   overlap on the GPU (other streams, other threads) race and must be
+ *   ordered by the caller.  Nothing needs clearing between calls: every
+ *   scratch element is written before it is read.
+ * Arguments and results as for gbr_hv. */
+int gbr_hv_static(const gbr_ham *H, const void *d_x, void *d_y, int fp, void *stream);
+
 /* One stage of the factored H·v, for timing and inspection.  With x viewed
  * as the D_up x D_dn matrix X:
  *   stage 1: rank the per-spin hop lists (unrank, hop, sign, staggered or

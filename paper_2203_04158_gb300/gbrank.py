@@ -79,6 +79,7 @@ def lib():
                 "gbr_hv": (i32, [vp, vp, vp, i32, vp]),
                 "gbr_ham_tune": (i32, [vp, i32, vp]),
                 "gbr_hv_stage": (i32, [vp, vp, vp, i32, i32, vp]),
+                "gbr_hv_static": (i32, [vp, vp, vp, i32, vp]),
                 "gbr_launch_count": (i64, []),
                 "gbr_lanczos": (i32, [vp, vp, vp, vp, vp, vp, vp, vp]),
                 "gbr_batch_layout": (i32, [i32, vp, vp, vp]),
@@ -269,6 +270,18 @@ def gbr_hv(H: Ham, x, y, stream=None):
     if fp is None:
         raise ValueError("x must be float32 or float64")
     _check(lib().gbr_hv(H, _dptr(x), _dptr(y), fp, _stream(stream)))
+    return y
+
+
+def gbr_hv_static(H: Ham, x, y, stream=None):
+    """gbr_hv that allocates nothing (scratch in a static device array)."""
+    import torch
+    if x.dtype != y.dtype:
+        raise ValueError("x and y must have the same dtype")
+    fp = {torch.float32: 32, torch.float64: 64}.get(x.dtype)
+    if fp is None:
+        raise ValueError("x must be float32 or float64")
+    _check(lib().gbr_hv_static(H, _dptr(x), _dptr(y), fp, _stream(stream)))
     return y
 
 
