@@ -232,6 +232,59 @@ def ranking_extras(G, torch):
     return out
 
 
+def config_extras(G, torch):
+    """The other configurations, each solved once (outside the timed steps)."""
+    import numpy as np
+    import gbr_synth as S
+    import gbr_synth.gpu as SG
+    import oracle
+    out = {}
+    # L=8 ring, U=4, half filling, FP64 with full re-orthogonalisation, combinadics ranking
+    h8, U8 = S.chain(8), S.uniform_U(8, 4.0)
+    H8 = G.gbr_ham_create(8, h8, U8, 4, 4, G.GBR_RANK_CNS)
+    v0 = torch.from_numpy(S.start_vector(4900)).cuda()
+    r = G.gbr_lanczos(H8, v0, 100, reorth=True, prec=G.GBR_PREC_FP64, refine=True, use_graph=True)
+    E_dense = oracle.dense_E0(8, h8, U8, 4, 4)
+    out["ring8_fp64_reorth"] = {"E0": r["E0"], "E0_dense": E_dense, "rel_err": abs(r["E0"] - E_dense) / abs(E_dense),
+                                "seconds": r["seconds"], "iters": r["iters"]}
+    # 256 impurity models, every sector, one persistent launch
+    models = [S.siam(m) for m in range(256)]
+    ns, nst = G.gbr_batch_layout(models)
+    st = SG.uniform(S.SEED_START, nst)
+    G.gbr_batch_solve(models[:4], st[:G.gbr_batch_layout(models[:4])[1]], 150)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    b = G.gbr_batch_solve(models, st, 150)
+    dt = time.perf_counter() - t0
+    checks = []
+    for m in (0, 128, 255):
+        h, U = models[m]
+        L = h.shape[0]
+        best = min(oracle.dense_E0(L, h, U, a, c) if oracle.sector_dim(L, a, c) <= 600 else
+                   oracle.lanczos(L, h, U, a, c, S.start_vector(oracle.sector_dim(L, a, c), 77),
+                                  min(160, oracle.sector_dim(L, a, c)), True)["E0"]
+                   for a in range(L + 1) for c in range(L + 1))
+        checks.append(abs(b["E0"][m] - best) / max(1.0, abs(best)))
+    out["siam256_batch"] = {"models": 256, "sectors": ns, "states": nst, "seconds": dt, "sectors_per_s": ns / dt,
+                            "max_rel_err_sampled_models": max(checks)}
+    # L=18 ring, U=4, half filling: mixed (150 steps, FP64 refinement) vs all-FP64
+    h18, U18 = S.chain(18), S.uniform_U(18, 4.0)
+    H18 = G.gbr_ham_create(18, h18, U18, 9, 9)
+    D18, el18 = G.gbr_ham_info(H18)
+    s18 = SG.uniform(S.SEED_START, D18)
+    rm = G.gbr_lanczos(H18, s18, 150, prec=G.GBR_PREC_MIXED, refine=True, store_basis=-1)
+    rd = G.gbr_lanczos(H18, s18, 150, prec=G.GBR_PREC_FP64, refine=False, store_basis=0)
+    out["chain18_mixed_vs_fp64"] = {"dim": D18, "elements_per_hv": el18, "mixed_E0": rm["E0"], "mixed_s": rm["seconds"],
+                                    "mixed_basis": "stored" if rm["stored_basis"] else "recomputed",
+                                    "fp64_E0": rd["E0"], "fp64_s": rd["seconds"],
+                                    "rel_diff": abs(rm["E0"] - rd["E0"]) / abs(rd["E0"]),
+                                    "speedup_mixed_over_fp64": rd["seconds"] / rm["seconds"],
+                                    "E0_free_limit_check": oracle.free_E0(h18, 9, 9)}
+    del s18, H18
+    torch.cuda.empty_cache()
+    return out
+
+
 def run_ours(args, rank: int, world: int):
     import numpy as np
     import torch
@@ -342,6 +395,12 @@ def run_ours(args, rank: int, world: int):
             line["ranking"] = ranking_extras(G, torch)
         except Exception as ex:  # report rather than hide
             line["ranking"] = {"error": repr(ex)}
+        H.close()
+        torch.cuda.empty_cache()
+        try:
+            line["configs"] = config_extras(G, torch)
+        except Exception as ex:
+            line["configs"] = {"error": repr(ex)}
     if rank == 0 and world == 1 and not args.no_cpu:
         v, desc, dt = oracle_sample(args.cpu_seconds)
         line["cpu_baseline"] = {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": desc}

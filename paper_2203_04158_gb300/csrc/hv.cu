@@ -254,8 +254,8 @@ struct CombineArgs {
     HamK hk;
 };
 
-template <typename T, int VEC, bool COMBINE>
-__global__ void __launch_bounds__(128) k_gather(const int64_t Drows, const int64_t Dcols, const int TR, const int hmax,
+template <typename T, int VEC, bool COMBINE, int TR>
+__global__ void __launch_bounds__(128) k_gather(const int64_t Drows, const int64_t Dcols, const int hmax,
                                                 const int64_t nrb, const uint16_t *__restrict__ cnt,
                                                 const uint32_t *__restrict__ tgt, const uint16_t *__restrict__ bond,
                                                 const T *__restrict__ bcoef, const int uniform, const T hu,
@@ -457,7 +457,8 @@ static int launch_gather(const gbr_ham *H, const SpinSector &lists, int64_t Drow
     // well inside L2
     for (int v = vmax; v >= 2; v /= 2)
         if (aligned16 && Dcols % v == 0 && (double)Drows * 128 * v * sizeof(T) <= 64e6) { vec = v; break; }
-    const int TR = H->tune_up_rows[fpi] ? H->tune_up_rows[fpi] : 8;
+    const int tr_req = H->tune_up_rows[fpi] ? H->tune_up_rows[fpi] : 8;
+    const int TR = (tr_req == 4 || tr_req == 16) ? tr_req : 8;
     const int64_t nrb = (Drows + TR - 1) / TR;
     const int64_t ncc = (Dcols + 128 * vec - 1) / (128 * vec);
     const int hmax = std::max(1, lists.hmax);
@@ -465,15 +466,20 @@ static int launch_gather(const gbr_ham *H, const SpinSector &lists, int64_t Drow
                         (COMBINE ? (size_t)TR * 128 * vec * sizeof(T) : 0);
     const int64_t blocks = nrb * ncc;
     if (blocks > 0x7FFFFFFF) return set_error(GBR_EINVAL, "sector too large for the gather grid");
-#define GBR_G(V)                                                                                             \
+#define GBR_G(V, R)                                                                                          \
     {                                                                                                        \
-        auto kern = k_gather<T, V, COMBINE>;                                                                 \
+        auto kern = k_gather<T, V, COMBINE, R>;                                                              \
         if (smem > 48 * 1024) GBR_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)); \
-        kern<<<(int)blocks, 128, smem, st>>>(Drows, Dcols, TR, hmax, nrb, lists.hop_cnt.as<uint16_t>(),      \
+        kern<<<(int)blocks, 128, smem, st>>>(Drows, Dcols, hmax, nrb, lists.hop_cnt.as<uint16_t>(),          \
                                              lists.hop_tgt.as<uint32_t>(), lists.hop_bond.as<uint16_t>(),    \
                                              (const T *)hd.bcoef, H->k.uniform, (T)H->k.hu, w, z, ca);        \
     }
-    if (vec == 4) GBR_G(4) else if (vec == 2) GBR_G(2) else GBR_G(1)
+#define GBR_GV(V)                                                                                            \
+    {                                                                                                        \
+        if (TR == 4) GBR_G(V, 4) else if (TR == 16) GBR_G(V, 16) else GBR_G(V, 8)                           \
+    }
+    if (vec == 4) GBR_GV(4) else if (vec == 2) GBR_GV(2) else GBR_GV(1)
+#undef GBR_GV
 #undef GBR_G
     GBR_LAUNCH_CHECK();
     count_launches(1);

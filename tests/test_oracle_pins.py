@@ -272,3 +272,11 @@ def test_lanczos_breakdown_on_tiny_sector():
     r = oracle.lanczos(2, h, U, 1, 0, np.array([0.3, -0.8]), 10, False)
     assert r["k"] == 2
     assert abs(r["E0"] - np.linalg.eigvalsh(oracle.dense(2, h, U, 1, 0))[0]) < 1e-13
+
+
+def test_seeded_rows_equal_rows_of_the_seeded_vector():
+    h, U = ham(6, 2.0, kind="square", Lx=3, Ly=2, tp=-0.3)
+    D = oracle.sector_dim(6, 3, 2)
+    x = S.start_vector(D)
+    rows = np.arange(0, D, 5)
+    assert np.array_equal(oracle.hv_rows_seeded(6, h, U, 3, 2, S.SEED_START, rows), oracle.hv_rows(6, h, U, 3, 2, x, rows))
