@@ -249,6 +249,9 @@ typedef struct {
                          run of the recurrence, -1 = decide from free memory */
     int use_graph;    /* 1 = replay each iteration as a captured CUDA graph */
     int profile;      /* 1 = time every H·v stage with CUDA events (no graphs) */
+    double tol;       /* > 0: every 8 steps, stop once the lowest Ritz pair of T
+                         has residual estimate beta_{k+1} |s_k| <= tol * max_j(|alpha_j|,
+                         beta_j); 0 = run all iters steps */
 } gbr_lanczos_opts;
 
 typedef struct {
@@ -265,6 +268,7 @@ typedef struct {
                                 spin-up gather with diagonal; the fused path
                                 is counted in the last slot) */
     int stage_launches[4];   /* profile: launches of each stage */
+    int converged;           /* 1 if the tol test stopped the recurrence */
 } gbr_lanczos_result;
 
 /* Runs Lanczos from the start vector d_v0 (dim doubles on the device, not

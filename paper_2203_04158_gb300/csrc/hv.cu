@@ -152,7 +152,11 @@ __device__ __forceinline__ T diag_value(const HamK &hk, const T *dup, const T *d
                                         int64_t rd, uint32_t au, uint32_t ad) {
     T d = dup[ru] + ddn[rd];
     const uint32_t both = au & ad;
-    for (int c = 0; c < hk.nucls; ++c) d += uval[c] * (T)__popc(both & hk.umask[c]);
+#pragma unroll
+    for (int c = 0; c < kMaxUClasses; ++c) {
+        if (c >= hk.nucls) break;
+        d += uval[c] * (T)__popc(both & hk.umask[c]);
+    }
     return d;
 }
 
@@ -179,6 +183,7 @@ __global__ void __launch_bounds__(256) k_hv_fused(const SpinK su, const SpinK sd
     stage_u32(binom, gbinom, nb);
     for (int i = threadIdx.x; i < hk.L * hk.L; i += blockDim.x) hc[i] = hcoef[i];
     T uval[kMaxUClasses];
+#pragma unroll
     for (int c = 0; c < kMaxUClasses; ++c) uval[c] = c < hk.nucls ? uval_g[c] : T(0);
     __syncthreads();
     const int64_t D = su.D * sd.D;
@@ -308,6 +313,7 @@ __global__ void __launch_bounds__(128) k_gather(const int64_t Drows, const int64
             ad[v] = ca.st_dn[c0 + v];
             dd[v] = ddn[c0 + v];
         }
+#pragma unroll
         for (int u = 0; u < kMaxUClasses; ++u) uval[u] = u < ca.hk.nucls ? ((const T *)ca.uval)[u] : T(0);
     }
     for (int i = 0; i < TR; ++i) {
@@ -355,12 +361,26 @@ __global__ void __launch_bounds__(128) k_gather(const int64_t Drows, const int64
             } else {
                 xo[0] = __ldg(x + r * Dcols + c0);
             }
+            T zv[VEC];
+            if (VEC == 4 && sizeof(T) == 4) {
+                const float4 z4 = *reinterpret_cast<const float4 *>(zs + i * (128 * VEC) + threadIdx.x * VEC);
+                zv[0] = z4.x; zv[1 % VEC] = z4.y; zv[2 % VEC] = z4.z; zv[3 % VEC] = z4.w;
+            } else {
+#pragma unroll
+                for (int v = 0; v < VEC; ++v) zv[v] = zs[i * (128 * VEC) + threadIdx.x * VEC + v];
+            }
 #pragma unroll
             for (int v = 0; v < VEC; ++v) {
                 const uint32_t both = au & ad[v];
                 T dg = du + dd[v];
-                for (int u = 0; u < ca.hk.nucls; ++u) dg += uval[u] * (T)__popc(both & ca.hk.umask[u]);
-                acc[v] += dg * xo[v] + zs[i * (128 * VEC) + threadIdx.x * VEC + v];
+                // unrolled (uval stays in registers) with a uniform exit, so
+                // no FP64 work is spent on unused classes
+#pragma unroll
+                for (int u = 0; u < kMaxUClasses; ++u) {
+                    if (u >= ca.hk.nucls) break;
+                    dg += uval[u] * (T)__popc(both & ca.hk.umask[u]);
+                }
+                acc[v] += dg * xo[v] + zv[v];
             }
         }
         if (VEC == 4 && sizeof(T) == 4) {
@@ -457,7 +477,8 @@ static int launch_gather(const gbr_ham *H, const SpinSector &lists, int64_t Drow
     // well inside L2
     for (int v = vmax; v >= 2; v /= 2)
         if (aligned16 && Dcols % v == 0 && (double)Drows * 128 * v * sizeof(T) <= 64e6) { vec = v; break; }
-    const int tr_req = H->tune_up_rows[fpi] ? H->tune_up_rows[fpi] : 8;
+    const int tuned = COMBINE ? H->tune_up_rows[fpi] : H->tune_dn_rows[fpi];
+    const int tr_req = tuned ? tuned : 8;
     const int TR = (tr_req == 4 || tr_req == 16) ? tr_req : 8;
     const int64_t nrb = (Drows + TR - 1) / TR;
     const int64_t ncc = (Dcols + 128 * vec - 1) / (128 * vec);
@@ -855,14 +876,19 @@ extern "C" int gbr_ham_tune(gbr_ham *H, int fp, void *stream) {
     };
     const int keep_path = H->path;
     float best = 1e30f, ms = 0.f;
-    int best_path = GBR_HV_FACTORED, best_tr = 8;
+    int best_path = GBR_HV_FACTORED;
     H->path = GBR_HV_FACTORED;
-    for (int tr : {4, 8, 16}) {
-        H->tune_up_rows[fpi] = tr;
-        if ((rc = time_it(&ms))) goto done;
-        if (ms < best) { best = ms; best_tr = tr; }
+    // rows per CTA of the spin-up (combine) pass, then of the spin-down pass
+    for (int pass = 0; pass < 2; ++pass) {
+        int *knob = pass == 0 ? &H->tune_up_rows[fpi] : &H->tune_dn_rows[fpi];
+        int best_tr = 8;
+        for (int tr : {4, 8, 16}) {
+            *knob = tr;
+            if ((rc = time_it(&ms))) goto done;
+            if (ms < best || (tr == 8 && ms <= best)) { best = ms; best_tr = tr; }
+        }
+        *knob = best_tr;
     }
-    H->tune_up_rows[fpi] = best_tr;
     if (H->D <= ((int64_t)1 << 22)) {
         H->path = GBR_HV_FUSED;
         if ((rc = time_it(&ms))) goto done;

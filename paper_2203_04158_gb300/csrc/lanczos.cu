@@ -72,7 +72,7 @@ struct LzState {
     int k;            // current step
     int stop;         // 1 once the recurrence broke down or finished
     int breakdown;
-    int pad;
+    int converged;    // 1 once the residual test stopped the recurrence
     double scale;     // max_j(|alpha_j|, beta_j)
 };
 
@@ -277,6 +277,24 @@ __global__ void __launch_bounds__(kRedThreads) k_tridiag(const LzState *st, cons
     }
 }
 
+// Convergence test every 8 steps (after beta_{k+1} is known): residual
+// estimate of the lowest Ritz pair, beta_{k+1} |s_k|, against tol * scale.
+// One warp does the multisection; thread 0 the eigenvector.
+__global__ void __launch_bounds__(32) k_conv_check(LzState *st, const double *alpha, const double *beta, double tol,
+                                                   double *s, double *work) {
+    const int k = st->k + 1;
+    if (st->converged || (k % 8) != 0) return;
+    const double lam = tridiag_lowest_block(alpha, beta, k);
+    if (threadIdx.x == 0) {
+        tridiag_vector_thread(alpha, beta, k, lam, s, work);
+        const double res = beta[k] * fabs(s[k - 1]);
+        if (res <= tol * st->scale) {
+            st->stop = 1;
+            st->converged = 1;
+        }
+    }
+}
+
 // per-step Ritz value into ritz[k]
 __global__ void k_copy_ritz(const LzState *st, const double *val, double *ritz) {
     if (threadIdx.x == 0) ritz[st->k] = val[0];
@@ -419,6 +437,7 @@ struct Lz {
     int fp;            // 32 or 64
     int iters, reorth, store;
     int grid;
+    double tol = 0.0;
     cudaStream_t st;
     // work buffers live in the handle (kept between calls)
     DevBuf &state, &alpha, &beta, &part, &coef, &tri, &svec, &work, &ritz_tmp;
@@ -471,6 +490,11 @@ static int lz_step(Lz &z, int phase, bool pass2, cudaEvent_t *ev4, bool want_rit
     }
     if (!pass2) {
         k_finalize<<<1, kRedThreads, 0, z.st>>>(st, z.alpha.as<double>(), z.beta.as<double>(), part, z.grid, 1, z.iters);
+        ++nk;
+    }
+    if (z.tol > 0.0 && !pass2) {
+        k_conv_check<<<1, 32, 0, z.st>>>(st, z.alpha.as<double>(), z.beta.as<double>(), z.tol, z.svec.as<double>(),
+                                         z.work.as<double>());
         ++nk;
     }
     if (want_ritz) {
@@ -573,6 +597,7 @@ static int lz_run(Lz &z, const double *d_v0, gbr_lanczos_result *res, const gbr_
     const int kdone = std::min(z.iters, hs.k + 1);
     res->iters_done = kdone;
     res->breakdown = hs.breakdown;
+    res->converged = hs.converged;
     res->stored_basis = z.store;
     // lowest Ritz value and (if refining) its eigenvector
     double *tri = z.tri.as<double>();
@@ -680,6 +705,7 @@ extern "C" int gbr_lanczos(const gbr_ham *H, const gbr_lanczos_opts *o, const do
     z.fp = o->prec == GBR_PREC_MIXED ? 32 : 64;
     z.iters = (int)std::min<int64_t>(o->iters, H->D);
     z.reorth = o->reorth ? 1 : 0;
+    z.tol = o->tol > 0.0 ? o->tol : 0.0;
     z.st = (cudaStream_t)stream;
     const size_t es = z.fp == 64 ? 8 : 4;
     const size_t basis_bytes = (size_t)(z.iters + 1) * (size_t)z.n * es;

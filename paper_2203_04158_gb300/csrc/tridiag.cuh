@@ -17,13 +17,13 @@ __device__ __forceinline__ int tridiag_sturm_count(const double *a, const double
 }
 
 // Lowest eigenvalue by multisection of the Gershgorin interval: every round
-// the block's threads evaluate the Sturm count at blockDim equally spaced
-// points and keep the cell where the count first reaches 1, until the
-// interval no longer shrinks.  Called by every thread of the block; the
-// result is returned to all threads.
+// the first warp evaluates the Sturm count at 32 equally spaced points and
+// keeps the cell where the count first reaches 1, until the interval no
+// longer shrinks.  (One warp, not the whole block: the FP64 divisions of the
+// Sturm recurrence are slow, and 32 points per round already gain 5 bits.)
+// Called by every thread of the block; the result is returned to all.
 __device__ double tridiag_lowest_block(const double *a, const double *b, int k) {
     __shared__ double lo_s, hi_s;
-    __shared__ int first_s;
     __syncthreads();
     if (threadIdx.x == 0) {
         double lo = a[0], hi = a[0];
@@ -37,28 +37,28 @@ __device__ double tridiag_lowest_block(const double *a, const double *b, int k) 
         hi_s = hi + pad;
     }
     __syncthreads();
-    const int P = blockDim.x;
-    for (int round = 0; round < 64; ++round) {
-        const double lo = lo_s, hi = hi_s;
-        const double x = (threadIdx.x == P - 1) ? hi : lo + (hi - lo) * ((double)(threadIdx.x + 1) / (double)P);
-        const int c = tridiag_sturm_count(a, b, k, x);
-        if (threadIdx.x == 0) first_s = P - 1;
-        __syncthreads();
-        if (c >= 1) atomicMin(&first_s, (int)threadIdx.x);
-        __syncthreads();
-        if (threadIdx.x == 0) {
-            const int f = first_s;
-            const double nhi = (f == P - 1) ? hi : lo + (hi - lo) * ((double)(f + 1) / (double)P);
-            const double nlo = (f == 0) ? lo : lo + (hi - lo) * ((double)f / (double)P);
-            hi_s = fmin(hi, fmax(nhi, lo));
-            lo_s = fmax(lo, fmin(nlo, hi_s));
+    const int P = 32;
+    if (threadIdx.x < 32) {
+        for (int round = 0; round < 200; ++round) {
+            const double lo = lo_s, hi = hi_s;
+            const double x = (threadIdx.x == P - 1) ? hi : lo + (hi - lo) * ((double)(threadIdx.x + 1) / (double)P);
+            const int c = tridiag_sturm_count(a, b, k, x);
+            const unsigned m = __ballot_sync(0xFFFFFFFFu, c >= 1);
+            const int f = m ? __ffs(m) - 1 : P - 1;
+            if (threadIdx.x == 0) {
+                const double nhi = (f == P - 1) ? hi : lo + (hi - lo) * ((double)(f + 1) / (double)P);
+                const double nlo = (f == 0) ? lo : lo + (hi - lo) * ((double)f / (double)P);
+                hi_s = fmin(hi, fmax(nhi, lo));
+                lo_s = fmax(lo, fmin(nlo, hi_s));
+            }
+            __syncwarp();
+            const double nl = lo_s, nh = hi_s;
+            const bool done = !(nl < nh) || nextafter(nl, nh) >= nh || (nh == hi && nl == lo);
+            __syncwarp();
+            if (done) break;
         }
-        __syncthreads();
-        const double nl = lo_s, nh = hi_s;
-        const bool done = !(nl < nh) || nextafter(nl, nh) >= nh || (nh == hi && nl == lo);
-        __syncthreads();
-        if (done) break;
     }
+    __syncthreads();
     const double r = hi_s;
     __syncthreads();
     return r;

@@ -109,3 +109,16 @@ def test_hubbard_4x4_mixed_vs_fp64_and_free_limit(G):
     E_free = oracle.free_E0(h, 7, 7)
     assert abs(E_free - (-26.4)) < 1e-12
     assert abs(r0["E0"] - E_free) <= 1e-9 * abs(E_free), r0["E0"]
+
+
+def test_tolerance_stop_meets_the_bar_earlier(G):
+    """With tol the recurrence stops once the lowest Ritz pair has converged;
+    the refined mixed-precision energy still meets 1e-9."""
+    L, h, U, Nu, Nd = ring8()
+    H = G.gbr_ham_create(L, h, U, Nu, Nd)
+    E_dense = oracle.dense_E0(L, h, U, Nu, Nd)
+    r = G.gbr_lanczos(H, v0(4900), 300, prec=G.GBR_PREC_MIXED, refine=True, tol=1e-6)
+    assert r["converged"] and r["iters"] < 300 and r["iters"] % 8 == 0
+    assert abs(r["E0"] - E_dense) <= 1e-9 * abs(E_dense)
+    r64 = G.gbr_lanczos(H, v0(4900), 300, prec=G.GBR_PREC_FP64, refine=False, tol=1e-6)
+    assert r64["converged"] and abs(r64["E0"] - E_dense) <= 1e-9 * abs(E_dense)
