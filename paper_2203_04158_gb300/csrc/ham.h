@@ -37,6 +37,16 @@ struct HamK {
     uint32_t nbr[kMaxL];       // nbr[p]: sites q with h_pq != 0, q != p
 };
 
+// Fused first update of a Lanczos step, done in the epilogue of the spin-up
+// pass: w = H v_k - beta_k v_{k-1} (k read from device memory; no update when
+// k == 0) and per-CTA partial sums of <w, v_k> (part may be NULL).
+struct LzHook {
+    const void *vprev;
+    const double *beta;
+    const int *kstate;
+    double *part;
+};
+
 }  // namespace gbr
 
 struct gbr_ham {
@@ -72,4 +82,12 @@ int hv_launch(const gbr_ham *H, const void *x, void *y, int fp, cudaStream_t st,
 int hv_stage(const gbr_ham *H, const void *x, void *y, int fp, int stage, cudaStream_t st);
 // factored path with the two scratch vectors (dim elements each) supplied
 int hv_factored_with_scratch(const gbr_ham *H, const void *x, void *y, int fp, cudaStream_t st, void *xt, void *zt);
+// true if gbr_hv runs the factored path on this handle
+bool hv_is_factored(const gbr_ham *H);
+// factored H·v with the fused Lanczos epilogue; *nparts receives the number
+// of partial sums written (the grid of the spin-up pass)
+int hv_launch_lz(const gbr_ham *H, const void *x, void *y, int fp, cudaStream_t st, cudaEvent_t *ev, const LzHook &hook,
+                 int *nparts);
+// upper bound of the partial sums hv_launch_lz writes for precision fp
+int64_t hv_lz_parts(const gbr_ham *H, int fp);
 }

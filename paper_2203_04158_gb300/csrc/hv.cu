@@ -25,6 +25,7 @@
 #include <cstring>
 
 #include "ham.h"
+#include "dot.cuh"
 
 namespace gbr {
 
@@ -257,14 +258,20 @@ struct CombineArgs {
     const void *dup, *ddn, *uval;     // per-spin diagonals, U class values (precision T)
     const void *zt;                   // Z^T = H_dn X^T, D_dn x D_up
     HamK hk;
+    LzHook lz;                        // fused first Lanczos update (MODE 2)
 };
 
-template <typename T, int VEC, bool COMBINE, int TR>
+// MODE 0: Z = H_lists W.  MODE 1: y = H_up X + Dg o X + Z (combine).  MODE 2:
+// as 1, then the first update of a Lanczos step in the same epilogue,
+// w = y - beta_k v_{k-1} (k > 0) and the block's partial <w, x>.
+template <typename T, int VEC, int MODE, int TR>
 __global__ void __launch_bounds__(128) k_gather(const int64_t Drows, const int64_t Dcols, const int hmax,
                                                 const int64_t nrb, const uint16_t *__restrict__ cnt,
                                                 const uint32_t *__restrict__ tgt, const uint16_t *__restrict__ bond,
                                                 const T *__restrict__ bcoef, const int uniform, const T hu,
                                                 const T *__restrict__ x, T *__restrict__ y, const CombineArgs ca) {
+    constexpr bool COMBINE = MODE >= 1;
+    constexpr bool LZ = MODE == 2;
     extern __shared__ __align__(16) unsigned char smr[];
     uint32_t *st = reinterpret_cast<uint32_t *>(smr);
     T *sc = reinterpret_cast<T *>(smr + (((size_t)TR * hmax * 4 + 15) & ~(size_t)15));
@@ -301,12 +308,19 @@ __global__ void __launch_bounds__(128) k_gather(const int64_t Drows, const int64
         }
         __syncthreads();
     }
-    if (c0 >= Dcols) return;
+    const bool active = c0 < Dcols;
+    DotAcc<T> dacc;
+    int klz = 0;
+    T blz = T(0);
+    if (LZ) {
+        klz = *ca.lz.kstate;
+        blz = klz > 0 ? (T)ca.lz.beta[klz] : T(0);
+    }
     // combine epilogue: column states and diagonals of this thread's columns
     uint32_t ad[VEC];
     T dd[VEC];
     T uval[kMaxUClasses];
-    if (COMBINE) {
+    if (COMBINE && active) {
         const T *ddn = (const T *)ca.ddn;
 #pragma unroll
         for (int v = 0; v < VEC; ++v) {
@@ -316,7 +330,7 @@ __global__ void __launch_bounds__(128) k_gather(const int64_t Drows, const int64
 #pragma unroll
         for (int u = 0; u < kMaxUClasses; ++u) uval[u] = u < ca.hk.nucls ? ((const T *)ca.uval)[u] : T(0);
     }
-    for (int i = 0; i < TR; ++i) {
+    for (int i = 0; i < TR && active; ++i) {
         const int64_t r = r0 + i;
         if (r >= Drows) break;
         const int n = scnt[i];
@@ -382,6 +396,25 @@ __global__ void __launch_bounds__(128) k_gather(const int64_t Drows, const int64
                 }
                 acc[v] += dg * xo[v] + zv[v];
             }
+            if (LZ) {
+                const T *vpv = (const T *)ca.lz.vprev + r * Dcols + c0;
+                if (klz > 0) {
+                    T vp[VEC];
+                    if (VEC == 4 && sizeof(T) == 4) {
+                        const float4 o = __ldcs(reinterpret_cast<const float4 *>(vpv));
+                        vp[0] = o.x; vp[1 % VEC] = o.y; vp[2 % VEC] = o.z; vp[3 % VEC] = o.w;
+                    } else if (VEC == 2) {
+                        const typename Vec<T>::v2 o = __ldcs(reinterpret_cast<const typename Vec<T>::v2 *>(vpv));
+                        vp[0] = o.x; vp[1 % VEC] = o.y;
+                    } else {
+                        vp[0] = __ldcs(vpv);
+                    }
+#pragma unroll
+                    for (int v = 0; v < VEC; ++v) acc[v] -= blz * vp[v];
+                }
+#pragma unroll
+                for (int v = 0; v < VEC; ++v) dacc.add(acc[v], xo[v]);
+            }
         }
         if (VEC == 4 && sizeof(T) == 4) {
             __stcs(reinterpret_cast<float4 *>(y + r * Dcols + c0), make_float4((float)acc[0], (float)acc[1 % VEC], (float)acc[2 % VEC], (float)acc[3 % VEC]));
@@ -392,6 +425,10 @@ __global__ void __launch_bounds__(128) k_gather(const int64_t Drows, const int64
         } else {
             y[r * Dcols + c0] = acc[0];
         }
+    }
+    if (LZ && ca.lz.part) {
+        const double r = block_sum(dacc.value());
+        if (threadIdx.x == 0) ca.lz.part[blockIdx.x] = r;
     }
 }
 
@@ -465,21 +502,31 @@ static int ensure_ws(const gbr_ham *H, size_t bytes) {
     return rc;
 }
 
-// One row-gather pass Z = H_lists W (+ the combine epilogue).
-template <typename T, bool COMBINE>
-static int launch_gather(const gbr_ham *H, const SpinSector &lists, int64_t Drows, int64_t Dcols, const T *w, T *z,
-                         const CombineArgs &ca, cudaStream_t st, const HamDev &hd) {
+// Vector width and rows per CTA of a gather pass (shared by the launch and
+// the partial-sum sizing of the fused Lanczos epilogue).
+template <typename T>
+static void gather_shape(const gbr_ham *H, int64_t Drows, int64_t Dcols, bool aligned16, bool combine, int *vec_out,
+                         int *tr_out) {
     const int fpi = sizeof(T) == 8 ? 1 : 0;
-    const bool aligned16 = (((uintptr_t)w | (uintptr_t)z) & 15u) == 0;
     const int vmax = sizeof(T) == 4 ? 4 : 2;
     int vec = 1;
-    // widest vector whose column chunk (all rows x 128*VEC columns) stays
-    // well inside L2
     for (int v = vmax; v >= 2; v /= 2)
         if (aligned16 && Dcols % v == 0 && (double)Drows * 128 * v * sizeof(T) <= 64e6) { vec = v; break; }
-    const int tuned = COMBINE ? H->tune_up_rows[fpi] : H->tune_dn_rows[fpi];
+    const int tuned = combine ? H->tune_up_rows[fpi] : H->tune_dn_rows[fpi];
     const int tr_req = tuned ? tuned : 8;
-    const int TR = (tr_req == 4 || tr_req == 16) ? tr_req : 8;
+    *vec_out = vec;
+    *tr_out = (tr_req == 4 || tr_req == 16) ? tr_req : 8;
+}
+
+// One row-gather pass Z = H_lists W (+ the combine epilogue, + the Lanczos update).
+template <typename T, int MODE>
+static int launch_gather(const gbr_ham *H, const SpinSector &lists, int64_t Drows, int64_t Dcols, const T *w, T *z,
+                         const CombineArgs &ca, cudaStream_t st, const HamDev &hd, int *grid_out = nullptr) {
+    constexpr bool COMBINE = MODE >= 1;
+    bool aligned16 = (((uintptr_t)w | (uintptr_t)z) & 15u) == 0;
+    if (MODE == 2) aligned16 = aligned16 && (((uintptr_t)ca.lz.vprev) & 15u) == 0;
+    int vec = 1, TR = 8;
+    gather_shape<T>(H, Drows, Dcols, aligned16, COMBINE, &vec, &TR);
     const int64_t nrb = (Drows + TR - 1) / TR;
     const int64_t ncc = (Dcols + 128 * vec - 1) / (128 * vec);
     const int hmax = std::max(1, lists.hmax);
@@ -489,7 +536,7 @@ static int launch_gather(const gbr_ham *H, const SpinSector &lists, int64_t Drow
     if (blocks > 0x7FFFFFFF) return set_error(GBR_EINVAL, "sector too large for the gather grid");
 #define GBR_G(V, R)                                                                                          \
     {                                                                                                        \
-        auto kern = k_gather<T, V, COMBINE, R>;                                                              \
+        auto kern = k_gather<T, V, MODE, R>;                                                                 \
         if (smem > 48 * 1024) GBR_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)); \
         kern<<<(int)blocks, 128, smem, st>>>(Drows, Dcols, hmax, nrb, lists.hop_cnt.as<uint16_t>(),          \
                                              lists.hop_tgt.as<uint32_t>(), lists.hop_bond.as<uint16_t>(),    \
@@ -504,6 +551,7 @@ static int launch_gather(const gbr_ham *H, const SpinSector &lists, int64_t Drow
 #undef GBR_G
     GBR_LAUNCH_CHECK();
     count_launches(1);
+    if (grid_out) *grid_out = (int)blocks;
     return GBR_OK;
 }
 
@@ -530,14 +578,15 @@ static int stage_dn(const gbr_ham *H, cudaStream_t st, const HamDev &hd, const S
     CombineArgs ca{};
     T *xt = ws ? (T *)ws->xt : H->ws_xt.as<T>();
     T *zt = ws ? (T *)ws->zt : H->ws_zt.as<T>();
-    return launch_gather<T, false>(H, dn_lists(H), H->dn.D, H->up.D, xt, zt, ca, st, hd);
+    return launch_gather<T, 0>(H, dn_lists(H), H->dn.D, H->up.D, xt, zt, ca, st, hd);
 }
 
 // Y = H_up X + Dg o X + (Z^T)^T
 template <typename T>
 static int stage_up(const gbr_ham *H, const T *x, T *y, cudaStream_t st, const HamDev &hd,
-                    const Scratch *ws = nullptr) {
+                    const Scratch *ws = nullptr, const LzHook *hook = nullptr, int *nparts = nullptr) {
     CombineArgs ca;
+    ca.lz = hook ? *hook : LzHook{nullptr, nullptr, nullptr, nullptr};
     ca.st_up = H->up.states.as<uint32_t>();
     ca.st_dn = H->dn.states.as<uint32_t>();
     ca.dup = hd.dup;
@@ -545,12 +594,14 @@ static int stage_up(const gbr_ham *H, const T *x, T *y, cudaStream_t st, const H
     ca.uval = hd.uval;
     ca.zt = ws ? ws->zt : H->ws_zt.p;
     ca.hk = H->k;
-    return launch_gather<T, true>(H, H->up, H->up.D, H->dn.D, x, y, ca, st, hd);
+    if (hook) return launch_gather<T, 2>(H, H->up, H->up.D, H->dn.D, x, y, ca, st, hd, nparts);
+    return launch_gather<T, 1>(H, H->up, H->up.D, H->dn.D, x, y, ca, st, hd, nparts);
 }
 
 template <typename T>
 static int launch_factored(const gbr_ham *H, const T *x, T *y, cudaStream_t st, const HamDev &hd,
-                           cudaEvent_t *ev = nullptr, const Scratch *ws = nullptr) {
+                           cudaEvent_t *ev = nullptr, const Scratch *ws = nullptr, const LzHook *hook = nullptr,
+                           int *nparts = nullptr) {
     if (ev) cudaEventRecord(ev[0], st);
     int rc = stage_hop_lists<T>(H, st);
     if (rc) return rc;
@@ -559,7 +610,7 @@ static int launch_factored(const gbr_ham *H, const T *x, T *y, cudaStream_t st, 
     if (ev) cudaEventRecord(ev[2], st);
     if ((rc = stage_dn<T>(H, st, hd, ws))) return rc;
     if (ev) cudaEventRecord(ev[3], st);
-    if ((rc = stage_up<T>(H, x, y, st, hd, ws))) return rc;
+    if ((rc = stage_up<T>(H, x, y, st, hd, ws, hook, nparts))) return rc;
     if (ev) cudaEventRecord(ev[4], st);
     return GBR_OK;
 }
@@ -592,6 +643,27 @@ int hv_launch(const gbr_ham *H, const void *x, void *y, int fp, cudaStream_t st,
     }
     if (fp == 64) return launch_factored<double>(H, (const double *)x, (double *)y, st, hd, ev);
     return launch_factored<float>(H, (const float *)x, (float *)y, st, hd, ev);
+}
+
+bool hv_is_factored(const gbr_ham *H) {
+    return H->path == GBR_HV_FACTORED || (H->path == GBR_HV_AUTO && H->D > (1 << 17));
+}
+
+int hv_launch_lz(const gbr_ham *H, const void *x, void *y, int fp, cudaStream_t st, cudaEvent_t *ev, const LzHook &hook,
+                 int *nparts) {
+    const int fpi = fp == 64 ? 1 : 0;
+    gbr_ham_prec *pb = prec_bufs(H, fpi);
+    HamDev hd{pb->dup.p, pb->ddn.p, pb->uval.p, pb->bcoef.p, pb->hcoef.p};
+    if (fp == 64) return launch_factored<double>(H, (const double *)x, (double *)y, st, hd, ev, nullptr, &hook, nparts);
+    return launch_factored<float>(H, (const float *)x, (float *)y, st, hd, ev, nullptr, &hook, nparts);
+}
+
+int64_t hv_lz_parts(const gbr_ham *H, int fp) {
+    // the smallest launch shape (vector width 1, 4 rows per CTA) bounds every grid
+    const int64_t nrb = (H->up.D + 3) / 4;
+    const int64_t ncc = (H->dn.D + 127) / 128;
+    (void)fp;
+    return nrb * ncc;
 }
 
 int hv_factored_with_scratch(const gbr_ham *H, const void *x, void *y, int fp, cudaStream_t st, void *xt, void *zt) {

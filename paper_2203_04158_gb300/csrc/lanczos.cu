@@ -20,52 +20,9 @@
 #include <cstring>
 
 #include "ham.h"
+#include "dot.cuh"
 
 namespace gbr {
-
-constexpr int kRedThreads = 256;
-
-// two-float accumulator: hi + lo, updated with the exact product of a and b
-struct FF {
-    float hi, lo;
-};
-
-__device__ __forceinline__ void ff_add_prod(FF &s, float a, float b) {
-    const float p = a * b;
-    const float e = fmaf(a, b, -p);          // a*b = p + e exactly
-    const float t = s.hi + p;                // TwoSum(s.hi, p)
-    const float bp = t - s.hi;
-    const float err = (s.hi - (t - bp)) + (p - bp);
-    s.hi = t;
-    s.lo += err + e;
-}
-
-template <typename T> struct DotAcc;
-template <> struct DotAcc<double> {
-    double s = 0.0;
-    __device__ __forceinline__ void add(double a, double b) { s = fma(a, b, s); }
-    __device__ __forceinline__ double value() const { return s; }
-};
-template <> struct DotAcc<float> {
-    FF s{0.f, 0.f};
-    __device__ __forceinline__ void add(float a, float b) { ff_add_prod(s, a, b); }
-    __device__ __forceinline__ double value() const { return (double)s.hi + (double)s.lo; }
-};
-
-__device__ __forceinline__ double block_sum(double v) {
-    __shared__ double red[kRedThreads / 32];
-    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xFFFFFFFFu, v, o);
-    const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
-    __syncthreads();
-    if (l == 0) red[w] = v;
-    __syncthreads();
-    double r = 0.0;
-    if (threadIdx.x < 32) {
-        r = threadIdx.x < (blockDim.x >> 5) ? red[threadIdx.x] : 0.0;
-        for (int o = 16; o > 0; o >>= 1) r += __shfl_down_sync(0xFFFFFFFFu, r, o);
-    }
-    return r;   // valid in thread 0
-}
 
 // State shared by the step kernels (device memory).
 struct LzState {
@@ -463,14 +420,22 @@ static int lz_step(Lz &z, int phase, bool pass2, cudaEvent_t *ev4, bool want_rit
     const int64_t n = z.n;
     T *v = z.buf[phase].as<T>(), *vprev = z.buf[1 - phase].as<T>(), *w = z.buf[2].as<T>();
     LzState *st = z.state.as<LzState>();
-    int rc = hv_launch(z.H, v, w, z.fp, z.st, ev4);
-    if (rc) return rc;
     double *part = z.part.as<double>();
     int64_t nk = 0;
-    k_step1<T><<<z.grid, kRedThreads, 0, z.st>>>(st, z.beta.as<double>(), vprev, v, w, n, part, pass2 ? 0 : 1);
-    ++nk;
+    int nparts = z.grid;
+    if (hv_is_factored(z.H)) {
+        // w = H v - beta_k v_{k-1} and the partials of <w, v> in the H·v epilogue
+        const LzHook hook{vprev, z.beta.as<double>(), &st->k, pass2 ? nullptr : part};
+        int rc = hv_launch_lz(z.H, v, w, z.fp, z.st, ev4, hook, &nparts);
+        if (rc) return rc;
+    } else {
+        int rc = hv_launch(z.H, v, w, z.fp, z.st, ev4);
+        if (rc) return rc;
+        k_step1<T><<<z.grid, kRedThreads, 0, z.st>>>(st, z.beta.as<double>(), vprev, v, w, n, part, pass2 ? 0 : 1);
+        ++nk;
+    }
     if (!pass2) {
-        k_finalize<<<1, kRedThreads, 0, z.st>>>(st, z.alpha.as<double>(), z.beta.as<double>(), part, z.grid, 0, z.iters);
+        k_finalize<<<1, kRedThreads, 0, z.st>>>(st, z.alpha.as<double>(), z.beta.as<double>(), part, nparts, 0, z.iters);
         ++nk;
     }
     k_step2<T><<<z.grid, kRedThreads, 0, z.st>>>(st, z.alpha.as<double>(), v, w, n, part, (pass2 || z.reorth) ? 0 : 1);
@@ -731,7 +696,8 @@ extern "C" int gbr_lanczos(const gbr_ham *H, const gbr_lanczos_opts *o, const do
     if ((rc = grow(z.state, sizeof(LzState)))) return rc;
     if ((rc = grow(z.alpha, sizeof(double) * (size_t)(z.iters + 2)))) return rc;
     if ((rc = grow(z.beta, sizeof(double) * (size_t)(z.iters + 2)))) return rc;
-    const size_t nparts = (size_t)z.grid * (size_t)(z.reorth ? z.iters + 1 : 1);
+    size_t nparts = (size_t)z.grid * (size_t)(z.reorth ? z.iters + 1 : 1);
+    nparts = std::max(nparts, (size_t)hv_lz_parts(H, z.fp));
     if ((rc = grow(z.part, sizeof(double) * nparts))) return rc;
     if ((rc = grow(z.coef, sizeof(double) * (size_t)(z.iters + 2)))) return rc;
     if ((rc = grow(z.tri, sizeof(double) * 16))) return rc;
