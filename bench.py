@@ -115,6 +115,41 @@ def ncu_traffic(kernel: str):
     return e.get("dram_bytes_per_launch_full_size")
 
 
+# ------------------------------------------------------------------ replicas
+#
+# With torchrun every rank solves its own replica of the workload: nothing in
+# the path exchanges data, so the only collectives are the barriers around
+# the timed region and the max-over-ranks of its duration.
+
+def ranks_barrier(world: int, timeout_s: float = 300.0):
+    """Barrier over all ranks; with gloo a monitored barrier, which names a
+    rank that never arrives instead of waiting forever."""
+    if world <= 1:
+        return
+    import datetime
+    import torch.distributed as dist
+    if dist.get_backend() == "gloo":
+        dist.monitored_barrier(timeout=datetime.timedelta(seconds=timeout_s))
+    else:
+        dist.barrier()
+
+
+def max_over_ranks(t: float, world: int, device=None) -> float:
+    """Largest of the ranks' durations (the job's duration)."""
+    if world <= 1:
+        return t
+    import torch
+    import torch.distributed as dist
+    tt = torch.tensor([t], dtype=torch.float64, device=device)
+    dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+    return float(tt.item())
+
+
+def aggregate_rate(units_per_rank: float, steps: int, world: int, t_max: float) -> float:
+    """Whole-job throughput: every rank's units over the slowest rank's time."""
+    return units_per_rank * steps * world / t_max
+
+
 # --------------------------------------------------------------------- oracle
 
 def oracle_sample(seconds: float):
@@ -227,6 +262,17 @@ def ranking_extras(G, torch):
     torch.cuda.synchronize()
     t = e0.elapsed_time(e1) / 1e3 / reps
     out["trie_40bit_2p24_sorted"] = {"ranks_per_s": n / t, "ms": t * 1e3}
+    # the bisection baseline the paper compares against, on the same queries
+    for name, qq in (("bisection_40bit_2p24", q), ("bisection_40bit_2p24_sorted", qs)):
+        G.gbr_trie_rank_bisect(tr, qq, r)
+        e0.record()
+        for _ in range(reps):
+            G.gbr_trie_rank_bisect(tr, qq, r)
+        e1.record()
+        torch.cuda.synchronize()
+        tb = e0.elapsed_time(e1) / 1e3 / reps
+        ref = out["trie_40bit_2p24" + ("_sorted" if "sorted" in name else "")]["ms"]
+        out[name] = {"ranks_per_s": n / tb, "ms": tb * 1e3, "trie_speedup": tb * 1e3 / ref}
     del q, qs, r, mdev, tr
     torch.cuda.empty_cache()
     return out
@@ -291,9 +337,7 @@ def run_ours(args, rank: int, world: int):
     import __graft_entry__
     if rank == 0 or world == 1:
         __graft_entry__.build()
-    if world > 1:
-        import torch.distributed as dist
-        dist.barrier()
+    ranks_barrier(world)
     import gbr_synth as S
     import gbr_synth.gpu as SG
     import paper_2203_04158_gb300 as G
@@ -312,9 +356,7 @@ def run_ours(args, rank: int, world: int):
         return G.gbr_lanczos(H, s, ITERS, prec=prec, refine=refine, store_basis=-1, profile=profile)
 
     def barrier():
-        if world > 1:
-            import torch.distributed as dist
-            dist.barrier()
+        ranks_barrier(world)
         torch.cuda.synchronize()
 
     for _ in range(args.warmup):
@@ -331,15 +373,10 @@ def run_ours(args, rank: int, world: int):
         e1.record()
         barrier()
     launches = G.gbr_launch_count() - n0
-    t = e0.elapsed_time(e1) / 1e3
-    if world > 1:
-        import torch.distributed as dist
-        tt = torch.tensor([t], dtype=torch.float64, device="cuda")
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        t = tt.item()
+    t = max_over_ranks(e0.elapsed_time(e1) / 1e3, world, device="cuda")
     iters_done = results[-1]["iters"]
     elems_step = elems * (iters_done + 1)        # FP32 H·v per step plus the FP64 refinement H·v
-    value = elems_step * args.steps * world / t
+    value = aggregate_rate(elems_step, args.steps, world, t)
 
     # dominant kernel from the live per-stage event timings
     st = np.sum([r["stage_seconds"] for r in results], axis=0)

@@ -141,6 +141,13 @@ int gbr_trie_build_host(const uint64_t *h_sorted, int64_t n, int M, int R, uint6
 int gbr_trie_rank(const gbr_trie *t, const uint64_t *d_pat, void *d_rank, int rank_bits, int64_t n, int check,
                   void *stream);
 
+/* Ranks n patterns by bisection in the trie's sorted member list -- the
+ * established method the paper replaces with tries (Sec. II, last
+ * paragraph; Sec. V-A), kept as a comparison point.  Same arguments and
+ * results as gbr_trie_rank (check = 1 marks non-members GBR_NOT_FOUND_*). */
+int gbr_trie_rank_bisect(const gbr_trie *t, const uint64_t *d_pat, void *d_rank, int rank_bits, int64_t n, int check,
+                         void *stream);
+
 /* Unranks through the stored member list (Sec. II, unranking by a list);
  * out-of-range ranks give GBR_NOT_FOUND_U64. */
 int gbr_trie_unrank(const gbr_trie *t, const void *d_rank, int rank_bits, uint64_t *d_pat, int64_t n, void *stream);

@@ -229,6 +229,47 @@ __global__ void __launch_bounds__(kRankThreads) k_trie_rank(const uint64_t *__re
     }
 }
 
+// Bisection over the sorted member list -- the established method that the
+// paper's tries replace (Sec. II, last paragraph; Sec. V-A), kept as the
+// comparison point.  Fixed trip count (ceil log2(n+1) halvings) so that the
+// kRankItems searches of a thread interleave.
+template <typename RT>
+__global__ void __launch_bounds__(kRankThreads) k_list_rank(const uint64_t *__restrict__ pat, RT *__restrict__ out,
+                                                            int64_t n, const uint64_t *__restrict__ members,
+                                                            int64_t nm, int steps, int check) {
+    const int64_t tile = (int64_t)kRankThreads * kRankItems;
+    for (int64_t base = (int64_t)blockIdx.x * tile; base < n; base += (int64_t)gridDim.x * tile) {
+        uint64_t a[kRankItems];
+        int64_t lo[kRankItems], len[kRankItems];
+#pragma unroll
+        for (int j = 0; j < kRankItems; ++j) {
+            const int64_t i = base + threadIdx.x + (int64_t)j * kRankThreads;
+            a[j] = i < n ? __ldcs(pat + i) : 0ull;
+            lo[j] = 0;
+            len[j] = nm;
+        }
+        for (int s = 0; s < steps; ++s) {
+#pragma unroll
+            for (int j = 0; j < kRankItems; ++j) {
+                // lower bound: first index whose member is >= a
+                const int64_t half = len[j] >> 1;
+                if (len[j] > 0) {
+                    const uint64_t m = __ldg(members + lo[j] + half);
+                    if (m < a[j]) { lo[j] += half + 1; len[j] -= half + 1; } else { len[j] = half; }
+                }
+            }
+        }
+#pragma unroll
+        for (int j = 0; j < kRankItems; ++j) {
+            const int64_t i = base + threadIdx.x + (int64_t)j * kRankThreads;
+            if (i >= n) break;
+            RT r = (RT)lo[j];
+            if (check && !(lo[j] < nm && __ldg(members + lo[j]) == a[j])) r = (RT)~(RT)0;
+            __stcs(out + i, r);
+        }
+    }
+}
+
 template <typename RT>
 __global__ void k_list_unrank(const RT *__restrict__ rank, uint64_t *__restrict__ pat, int64_t n,
                               const uint64_t *__restrict__ members, int64_t n_members) {
@@ -480,6 +521,32 @@ extern "C" int gbr_trie_rank(const gbr_trie *t, const uint64_t *d_pat, void *d_r
     }
     if (rank_bits == 32) return launch_trie_rank<uint32_t, uint32_t>(t, d_pat, (uint32_t *)d_rank, n, check, st);
     return launch_trie_rank<uint32_t, uint64_t>(t, d_pat, (uint64_t *)d_rank, n, check, st);
+}
+
+extern "C" int gbr_trie_rank_bisect(const gbr_trie *t, const uint64_t *d_pat, void *d_rank, int rank_bits, int64_t n,
+                                    int check, void *stream) {
+    clear_error();
+    if (!t) return set_error(GBR_EINVAL, "NULL handle");
+    int rc = check_io(d_pat, d_rank, n, rank_bits);
+    if (rc) return rc;
+    if (((uintptr_t)d_pat & 7u) || (rank_bits == 64 && ((uintptr_t)d_rank & 7u)))
+        return set_error(GBR_EINVAL, "64-bit buffers must be 8-byte aligned");
+    if (rank_bits == 32 && t->n_members > (int64_t)0x100000000ll)
+        return set_error(GBR_EINVAL, "member count does not fit 32-bit ranks");
+    if (n == 0) return GBR_OK;
+    int steps = 0;
+    while (((int64_t)1 << steps) <= t->n_members) ++steps;
+    cudaStream_t st = (cudaStream_t)stream;
+    const int grid = grid_for(n, (int64_t)kRankThreads * kRankItems, 8);
+    if (rank_bits == 32)
+        k_list_rank<uint32_t><<<grid, kRankThreads, 0, st>>>(d_pat, (uint32_t *)d_rank, n, t->members.as<uint64_t>(),
+                                                             t->n_members, steps, check);
+    else
+        k_list_rank<uint64_t><<<grid, kRankThreads, 0, st>>>(d_pat, (uint64_t *)d_rank, n, t->members.as<uint64_t>(),
+                                                             t->n_members, steps, check);
+    GBR_LAUNCH_CHECK();
+    count_launches(1);
+    return GBR_OK;
 }
 
 extern "C" int gbr_trie_unrank(const gbr_trie *t, const void *d_rank, int rank_bits, uint64_t *d_pat, int64_t n,

@@ -73,6 +73,7 @@ def lib():
                 "gbr_trie_build_host": (i32, [vp, i64, i32, i32, vp, i64, vp]),
                 "gbr_trie_rank": (i32, [vp, vp, vp, i32, i64, i32, vp]),
                 "gbr_trie_unrank": (i32, [vp, vp, i32, vp, i64, vp]),
+                "gbr_trie_rank_bisect": (i32, [vp, vp, vp, i32, i64, i32, vp]),
                 "gbr_ham_create": (i32, [i32, vp, vp, i32, i32, i32, vp]),
                 "gbr_ham_destroy": (None, [vp]),
                 "gbr_ham_info": (i32, [vp, vp, vp]),
@@ -229,6 +230,13 @@ def gbr_trie_rank(t: Trie, pat, out, check: int = 0, stream=None):
     import torch
     _check(lib().gbr_trie_rank(t, _dptr(pat, (torch.int64,)), _dptr(out), _rank_bits(out), pat.numel(), int(check),
                                _stream(stream)))
+    return out
+
+
+def gbr_trie_rank_bisect(t: Trie, pat, out, check: int = 0, stream=None):
+    import torch
+    _check(lib().gbr_trie_rank_bisect(t, _dptr(pat, (torch.int64,)), _dptr(out), _rank_bits(out), pat.numel(),
+                                      int(check), _stream(stream)))
     return out
 
 

@@ -146,6 +146,13 @@ def test_trie_random_sets(G, M, R):
     for w, g in zip(want, got):
         assert (w >= 0 and int(g) == w) or (w < 0 and g == np.uint64(0xFFFFFFFFFFFFFFFF))
     G.gbr_trie_rank(t, to_dev_u64(q), r2, check=0)
+    # the bisection baseline over the same member list agrees bit for bit
+    r3 = torch.empty(q.size, dtype=torch.int64, device="cuda")
+    G.gbr_trie_rank_bisect(t, to_dev_u64(q), r3, check=1)
+    assert np.array_equal(as_u64(r3), got)
+    r4 = torch.empty(k, dtype=torch.int32, device="cuda")
+    G.gbr_trie_rank_bisect(t, to_dev_u64(members), r4, check=1)
+    assert np.array_equal(as_u32(r4), np.arange(k, dtype=np.uint32))
     torch.cuda.synchronize()
 
 
@@ -172,6 +179,9 @@ def test_trie_full_size_40bit(G):
     r = torch.empty(n, dtype=torch.int32, device="cuda")
     G.gbr_trie_rank(t, pats, r, check=1)
     assert torch.equal(r.to(torch.int64), j)
+    rb = torch.empty(n, dtype=torch.int32, device="cuda")
+    G.gbr_trie_rank_bisect(t, pats, rb, check=1)
+    assert torch.equal(rb, r)
     sel = np.unique(S.bounded(14, np.arange(2000, dtype=np.uint64), n)).astype(np.int64)
     ps = as_u64(pats[torch.from_numpy(sel).cuda()])
     assert np.array_equal(oracle.rank_bisect_many(members, ps), as_u32(r[torch.from_numpy(sel).cuda()]).astype(np.int64))
