@@ -328,7 +328,69 @@ def config_extras(G, torch):
                                     "E0_free_limit_check": oracle.free_E0(h18, 9, 9)}
     del s18, H18
     torch.cuda.empty_cache()
+    # every S_z of the 12-site ring at 12 particles, ranked by a packed trie
+    h12, U12 = S.chain(12), S.uniform_U(12, 4.0)
+    st12 = oracle.fixed_N_states(12, 12)
+    Sh = G.gbr_setham_create(12, h12, U12, st12, 8)
+    info = G.gbr_setham_info(Sh)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    res = {"dim": info["dim"], "elements_per_hv": info["elements"],
+           "trie_overhead_f": info["trie_elements"] / info["dim"]}
+    for fp, dt in ((32, torch.float32), (64, torch.float64)):
+        x = SG.uniform(S.SEED_START, info["dim"]).to(dt)
+        y = torch.empty_like(x)
+        G.gbr_setham_hv(Sh, x, y, check=1)
+        e0.record()
+        for _ in range(5):
+            G.gbr_setham_hv(Sh, x, y, check=1)
+        e1.record()
+        torch.cuda.synchronize()
+        t = e0.elapsed_time(e1) / 5 / 1e3
+        res[f"fp{fp}"] = {"ms": t * 1e3, "elements_per_s": info["elements"] / t}
+    out["ring12_allSz_trie_hv"] = res
     return out
+
+
+def ranking_sweep(G, torch):
+    """Analog of the paper's ranking microbenchmark (Sec. V-A: M = 28, every
+    filling, states drawn with replacement and sorted): staggered, trie and
+    bisection ranks/s on 2^26 queries per sector, sorted and unsorted."""
+    import numpy as np
+    import gbr_synth as S
+    import gbr_synth.gpu as SG
+    import oracle
+    M, n = 28, 1 << 26
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    rows = []
+
+    def timed(fn, reps=5):
+        fn()
+        e0.record()
+        for _ in range(reps):
+            fn()
+        e1.record()
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1) / reps / 1e3
+
+    for N in (1, 2, 5, 9, 14, 19, 23, 26, 27):
+        D = math.comb(M, N)
+        members = oracle.enumerate_sector(M, N)
+        c = G.gbr_comb_create(M, N, 8)
+        tr = G.gbr_trie_create(members, M, 8)
+        u = SG.bounded(S.SEED_COMB_QUERIES, n, D)
+        q = torch.empty(n, dtype=torch.int64, device="cuda")
+        G.gbr_comb_unrank(c, u, q)
+        qs, _ = torch.sort(q)
+        r = torch.empty(n, dtype=torch.int32, device="cuda")
+        row = {"N": N, "dim": D, "trie_f": G.gbr_trie_info(tr)["n_elements"] / D}
+        for tag, qq in (("", q), ("_sorted", qs)):
+            row["staggered" + tag] = n / timed(lambda: G.gbr_comb_rank(c, qq, r))
+            row["trie" + tag] = n / timed(lambda: G.gbr_trie_rank(tr, qq, r))
+            row["bisection" + tag] = n / timed(lambda: G.gbr_trie_rank_bisect(tr, qq, r))
+        rows.append(row)
+        del q, qs, u, r, tr, c
+        torch.cuda.empty_cache()
+    return rows
 
 
 def run_ours(args, rank: int, world: int):
@@ -486,11 +548,20 @@ def main():
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--no-extras", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--ranking-sweep", action="store_true",
+                    help="print the M=28 ranking sweep (every filling) as JSON and exit")
     ap.add_argument("--profile-hv", type=int, default=0,
                     help="run this many FP32 H·v calls on the workload sector and exit (for ncu captures)")
     args = ap.parse_args()
     if args.profile_hv:
         profile_hv(args.profile_hv)
+        return
+    if args.ranking_sweep:
+        import torch
+        import __graft_entry__
+        __graft_entry__.build()
+        import paper_2203_04158_gb300 as G
+        print(json.dumps({"ranking_sweep_M28": ranking_sweep(G, torch)}), flush=True)
         return
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))

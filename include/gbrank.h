@@ -238,6 +238,38 @@ int64_t gbr_launch_count(void);
 int gbr_ham_tune(gbr_ham *H, int fp, void *stream);
 
 /* ------------------------------------------------------------------------
+ * The same Hamiltonians on an arbitrary sorted set of 2L-bit states, ranked
+ * by a packed trie (Sec. IV: sectors cut by further quantum numbers, which
+ * combinadics cannot index; here also unions of spin sectors, e.g. every
+ * S_z at fixed total particle number).
+ * --------------------------------------------------------------------- */
+typedef struct gbr_setham gbr_setham;
+
+/* L: 1..32 sites; h, U as for gbr_ham_create; h_states: n distinct 2L-bit
+ * patterns in increasing order (spin down in the low L bits; host, copied);
+ * R: trie radix bits (1..16, 8 recommended).  Builds the packed trie of the
+ * set (gbr_trie_create's layout).
+ * Errors: GBR_EINVAL (unsorted set, bits at or above 2L, h not symmetric),
+ * GBR_ENOMEM, GBR_ECUDA. */
+int gbr_setham_create(int L, const double *h, const double *U, const uint64_t *h_states, int64_t n, int R,
+                      gbr_setham **out);
+void gbr_setham_destroy(gbr_setham *S);
+
+/* dim = n; elements = n plus every hop of every member (the matrix elements
+ * one H·v visits when the set is closed under H); trie_elements = packed
+ * trie size without padding. */
+int gbr_setham_info(const gbr_setham *S, int64_t *dim, int64_t *elements, int64_t *trie_elements);
+
+/* y = P H P x on the set (Eq. mvblock on the set, Eq. Talpha on the fly):
+ * one thread per member applies every term; each hop target is ranked by
+ * the trie walk of Fig. trielookup on the full pattern.  check = 1 drops
+ * targets outside the set (found by the member-list check of Sec. IV), which
+ * makes the result exact for any set; check = 0 trusts the set to be closed
+ * under H.  d_x, d_y: n floats (fp 32) or doubles (fp 64), not overlapping.
+ * Deterministic; asynchronous on stream. */
+int gbr_setham_hv(const gbr_setham *S, const void *d_x, void *d_y, int fp, int check, void *stream);
+
+/* ------------------------------------------------------------------------
  * Lanczos ground state (cited in Sec. I and V-B; the recurrence is the
  * textbook three-term one).
  * --------------------------------------------------------------------- */

@@ -61,6 +61,7 @@ def lib():
             L.ora_hv_rows_seeded.restype = i32
             L.ora_hv_rows_seeded.argtypes = [i32, vp, vp, i32, i32, u64, vp, i64, vp]
             L.ora_seeded_uniform.restype = dbl; L.ora_seeded_uniform.argtypes = [u64, u64]
+            L.ora_hv_set.restype = i32; L.ora_hv_set.argtypes = [i32, vp, vp, vp, i64, vp, vp, vp]
             L.ora_count_elements.restype = i64; L.ora_count_elements.argtypes = [i32, vp, i32, i32, i64, i64]
             L.ora_dense.restype = i32; L.ora_dense.argtypes = [i32, vp, vp, i32, i32, vp]
             L.ora_tridiag_lowest.restype = dbl; L.ora_tridiag_lowest.argtypes = [vp, vp, i32]
@@ -191,6 +192,22 @@ def hv_rows_seeded(L, h, U, Nup, Ndn, seed: int, rows) -> np.ndarray:
 
 def seeded_uniform(seed: int, i: int) -> float:
     return float(lib().ora_seeded_uniform(int(seed), int(i)))
+
+
+def hv_set(L, h, U, states, x):
+    """y = P H P x over the sorted set ``states``; returns (y, dropped terms)."""
+    h, U = _hU(L, h, U)
+    st = np.ascontiguousarray(states, dtype=np.uint64)
+    x = _f64(x)
+    y = np.empty(st.size, dtype=np.float64)
+    dropped = C.c_int64(0)
+    lib().ora_hv_set(L, _p(h), _p(U), _p(st), st.size, _p(x), _p(y), C.byref(dropped))
+    return y, dropped.value
+
+
+def fixed_N_states(L: int, N: int) -> np.ndarray:
+    """All 2L-bit states with N particles in total (every S_z), sorted."""
+    return enumerate_sector(2 * L, N)
 
 
 def count_elements(L, h, Nup, Ndn, row0: int = 0, row1: int = 0) -> int:

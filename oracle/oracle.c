@@ -480,6 +480,55 @@ int ora_hv_rows_seeded(int L, const double *h, const double *U, int Nup, int Ndn
     return c.bad ? -1 : 0;
 }
 
+/* y = P H P x over an arbitrary sorted set of 2L-bit states (Sec. IV: sets
+ * defined by further quantum numbers, ranked through a search structure):
+ * every term is applied literally to every member; the coefficient is
+ * scattered to the rank of the result, found by bisection in the set.
+ * Results outside the set are dropped (the set's projection of H; for a
+ * set closed under H nothing is dropped) and counted in *dropped. */
+int ora_hv_set(int L, const double *h, const double *U, const uint64_t *states, int64_t n, const double *x,
+               double *y, int64_t *dropped) {
+    typedef struct { const uint64_t *st; int64_t n; double *y; double xj; int64_t drop; } set_ctx;
+    for (int64_t i = 0; i < n; ++i) y[i] = 0.0;
+    int64_t drop = 0;
+    for (int64_t j = 0; j < n; ++j) {
+        /* apply every term to member j (same literal operator products as
+         * ora_apply_H, written out here for the set's own ranking) */
+        uint64_t alpha = states[j];
+        for (int spin = 0; spin < 2; ++spin) {
+            int off = spin ? L : 0;
+            for (int p = 0; p < L; ++p)
+                for (int q = 0; q < L; ++q) {
+                    double v = h[p * L + q];
+                    if (v == 0.0) continue;
+                    uint64_t b = alpha;
+                    int s1 = ora_c(&b, q + off);
+                    if (!s1) continue;
+                    int s2 = ora_cdag(&b, p + off);
+                    if (!s2) continue;
+                    int64_t i = ora_rank_bisect(states, n, b);
+                    if (i < 0) { ++drop; continue; }
+                    y[i] += v * s1 * s2 * x[j];
+                }
+        }
+        for (int p = 0; p < L; ++p) {
+            double v = U ? U[p] : 0.0;
+            if (v == 0.0) continue;
+            uint64_t b = alpha;
+            int s = ora_c(&b, p + L);
+            if (!s) continue;
+            int t2 = ora_c(&b, p); if (!t2) continue; s *= t2;
+            t2 = ora_cdag(&b, p); if (!t2) continue; s *= t2;
+            t2 = ora_cdag(&b, p + L); if (!t2) continue; s *= t2;
+            int64_t i = ora_rank_bisect(states, n, b);
+            if (i < 0) { ++drop; continue; }
+            y[i] += v * s * x[j];
+        }
+    }
+    if (dropped) *dropped = drop;
+    return 0;
+}
+
 /* Number of matrix elements one H x visits: the D diagonal entries plus every
  * off-diagonal (state, hop) pair that is non-zero.  Counted by applying the
  * off-diagonal hopping terms literally to every state; for rows only in

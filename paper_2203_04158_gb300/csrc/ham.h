@@ -82,6 +82,11 @@ int hv_launch(const gbr_ham *H, const void *x, void *y, int fp, cudaStream_t st,
 int hv_stage(const gbr_ham *H, const void *x, void *y, int fp, int stage, cudaStream_t st);
 // factored path with the two scratch vectors (dim elements each) supplied
 int hv_factored_with_scratch(const gbr_ham *H, const void *x, void *y, int fp, cudaStream_t st, void *xt, void *zt);
+// one-body bonds in (p, q) order, neighbour masks, U classes (shared by the
+// sector and the set Hamiltonians); pairs gets (p, q) per bond, bidx the bond
+// index of every (p, q)
+int build_hamk(int L, const double *h, const double *U, int rank_method, HamK *k, std::vector<uint16_t> *pairs,
+               std::vector<uint16_t> *bidx);
 // true if gbr_hv runs the factored path on this handle
 bool hv_is_factored(const gbr_ham *H);
 // factored H·v with the fused Lanczos epilogue; *nparts receives the number

@@ -768,6 +768,45 @@ static int upload_prec(gbr_ham *H, gbr_ham_prec *pb) {
     return GBR_OK;
 }
 
+int build_hamk(int L, const double *h, const double *U, int rank_method, HamK *kout, std::vector<uint16_t> *pairs,
+               std::vector<uint16_t> *bidx) {
+    HamK &k = *kout;
+    memset(&k, 0, sizeof(k));
+    k.L = L;
+    k.rank_method = rank_method;
+    pairs->clear();
+    bidx->assign((size_t)L * L, 0);
+    double first = 0.0;
+    k.uniform = 1;
+    for (int p = 0; p < L; ++p)
+        for (int q = 0; q < L; ++q) {
+            if (p == q) continue;
+            const double v = h[p * L + q];
+            if (v == 0.0) continue;
+            if (k.nbond == 0) first = v;
+            else if (v != first) k.uniform = 0;
+            (*bidx)[(size_t)(p * L + q)] = (uint16_t)k.nbond;
+            pairs->push_back((uint16_t)p);
+            pairs->push_back((uint16_t)q);
+            k.nbr[p] |= 1u << q;
+            ++k.nbond;
+        }
+    k.hu = first;
+    for (int p = 0; p < L; ++p) {
+        const double u = U ? U[p] : 0.0;
+        if (u == 0.0) continue;
+        int c = 0;
+        while (c < k.nucls && k.uval[c] != u) ++c;
+        if (c == k.nucls) {
+            if (k.nucls == kMaxUClasses) return set_error(GBR_EINVAL, "more than %d distinct U values", kMaxUClasses);
+            k.uval[c] = u;
+            ++k.nucls;
+        }
+        k.umask[c] |= 1u << p;
+    }
+    return GBR_OK;
+}
+
 }  // namespace gbr
 
 using namespace gbr;
@@ -815,38 +854,10 @@ extern "C" int gbr_ham_create(int L, const double *h, const double *U, int Nup, 
     H->U.assign(L, 0.0);
     if (U) H->U.assign(U, U + L);
     // one-body bonds in (p, q) order, neighbour masks, U classes
-    HamK &k = H->k;
-    memset(&k, 0, sizeof(k));
-    k.L = L;
-    k.rank_method = rank_method;
-    std::vector<uint16_t> pairs, bidx((size_t)L * L, 0);
-    double first = 0.0;
-    k.uniform = 1;
-    for (int p = 0; p < L; ++p)
-        for (int q = 0; q < L; ++q) {
-            if (p == q) continue;
-            const double v = h[p * L + q];
-            if (v == 0.0) continue;
-            if (k.nbond == 0) first = v;
-            else if (v != first) k.uniform = 0;
-            bidx[(size_t)(p * L + q)] = (uint16_t)k.nbond;
-            pairs.push_back((uint16_t)p);
-            pairs.push_back((uint16_t)q);
-            k.nbr[p] |= 1u << q;
-            ++k.nbond;
-        }
-    k.hu = first;
-    for (int p = 0; p < L; ++p) {
-        const double u = H->U[(size_t)p];
-        if (u == 0.0) continue;
-        int c = 0;
-        while (c < k.nucls && k.uval[c] != u) ++c;
-        if (c == k.nucls) {
-            if (k.nucls == kMaxUClasses) { delete H; return set_error(GBR_EINVAL, "more than %d distinct U values", kMaxUClasses); }
-            k.uval[c] = u;
-            ++k.nucls;
-        }
-        k.umask[c] |= 1u << p;
+    std::vector<uint16_t> pairs, bidx;
+    {
+        const int rck = build_hamk(L, h, H->U.data(), rank_method, &H->k, &pairs, &bidx);
+        if (rck) { delete H; return rck; }
     }
     std::vector<uint16_t> bonds_blob(pairs);
     bonds_blob.insert(bonds_blob.end(), bidx.begin(), bidx.end());

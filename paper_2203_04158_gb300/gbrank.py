@@ -84,6 +84,10 @@ def lib():
                 "gbr_hv_static": (i32, [vp, vp, vp, i32, vp]),
                 "gbr_launch_count": (i64, []),
                 "gbr_lanczos": (i32, [vp, vp, vp, vp, vp, vp, vp, vp]),
+                "gbr_setham_create": (i32, [i32, vp, vp, vp, i64, i32, vp]),
+                "gbr_setham_destroy": (None, [vp]),
+                "gbr_setham_info": (i32, [vp, vp, vp, vp]),
+                "gbr_setham_hv": (i32, [vp, vp, vp, i32, i32, vp]),
                 "gbr_batch_layout": (i32, [i32, vp, vp, vp]),
                 "gbr_batch_solve": (i32, [i32, vp, vp, i32, vp, vp, vp, vp]),
             }
@@ -171,6 +175,10 @@ class Trie(_Handle):
 
 class Ham(_Handle):
     _destroy = "gbr_ham_destroy"
+
+
+class SetHam(_Handle):
+    _destroy = "gbr_setham_destroy"
 
 
 # ---------------------------------------------------------------- combinations
@@ -325,6 +333,34 @@ def gbr_lanczos(H: Ham, v0, iters: int, reorth: bool = False, prec: int = GBR_PR
                 stage_seconds=list(r.stage_seconds), stage_launches=list(r.stage_launches),
                 converged=bool(r.converged),
                 alpha=a[:k].copy(), beta=b[:max(k - 1, 0)].copy(), ritz=None if rz is None else rz[:k].copy())
+
+
+# ------------------------------------------------------ set Hamiltonians
+
+def gbr_setham_create(L: int, h, U, states: np.ndarray, R: int = 8) -> SetHam:
+    hh = np.ascontiguousarray(h, dtype=np.float64).reshape(L * L)
+    uu = None if U is None else np.ascontiguousarray(U, dtype=np.float64).reshape(L)
+    st = np.ascontiguousarray(states, dtype=np.uint64)
+    p = C.c_void_p()
+    _check(lib().gbr_setham_create(L, _hptr(hh), None if uu is None else _hptr(uu), _hptr(st), st.size, R, C.byref(p)))
+    return SetHam(p)
+
+
+def gbr_setham_info(S: SetHam):
+    d, e, t = C.c_int64(), C.c_int64(), C.c_int64()
+    _check(lib().gbr_setham_info(S, C.byref(d), C.byref(e), C.byref(t)))
+    return dict(dim=d.value, elements=e.value, trie_elements=t.value)
+
+
+def gbr_setham_hv(S: SetHam, x, y, check: int = 1, stream=None):
+    import torch
+    if x.dtype != y.dtype:
+        raise ValueError("x and y must have the same dtype")
+    fp = {torch.float32: 32, torch.float64: 64}.get(x.dtype)
+    if fp is None:
+        raise ValueError("x must be float32 or float64")
+    _check(lib().gbr_setham_hv(S, _dptr(x), _dptr(y), fp, int(check), _stream(stream)))
+    return y
 
 
 # ---------------------------------------------------------------------- batch

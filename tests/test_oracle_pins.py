@@ -280,3 +280,39 @@ def test_seeded_rows_equal_rows_of_the_seeded_vector():
     x = S.start_vector(D)
     rows = np.arange(0, D, 5)
     assert np.array_equal(oracle.hv_rows_seeded(6, h, U, 3, 2, S.SEED_START, rows), oracle.hv_rows(6, h, U, 3, 2, x, rows))
+
+
+def test_set_hv_equals_sector_hv_and_union_of_sectors():
+    # on a sector the set form equals the sector form; on all S_z at fixed N it
+    # is block diagonal with the sector blocks
+    L = 5
+    h, U = ham(L, 3.0, kind="square", Lx=5, Ly=1)
+    st = oracle.sector_states(L, 2, 3)
+    x = S.start_vector(st.size)
+    y, drop = oracle.hv_set(L, h, U, st, x)
+    assert drop == 0 and np.allclose(y, oracle.hv(L, h, U, 2, 3, x), rtol=0, atol=1e-13)
+    allN = oracle.fixed_N_states(L, 5)
+    xa = S.start_vector(allN.size, 9)
+    ya, drop = oracle.hv_set(L, h, U, allN, xa)
+    assert drop == 0
+    for nu in range(0, 6):
+        sec = oracle.sector_states(L, nu, 5 - nu)
+        idx = np.searchsorted(allN, sec)
+        assert np.array_equal(allN[idx], sec)
+        assert np.allclose(ya[idx], oracle.hv(L, h, U, nu, 5 - nu, xa[idx]), rtol=0, atol=1e-13)
+
+
+def test_set_hv_projects_onto_open_sets():
+    # a random subset is not closed under H: the dropped terms are exactly the
+    # entries of the full product outside the subset
+    L = 4
+    h, U = ham(L, 2.0)
+    full = oracle.sector_states(L, 2, 2)
+    rng = np.random.default_rng(5)
+    keep = np.sort(rng.choice(full.size, size=20, replace=False))
+    sub = full[keep]
+    Hm = oracle.dense(L, h, U, 2, 2)
+    x = S.start_vector(sub.size)
+    y, drop = oracle.hv_set(L, h, U, sub, x)
+    assert np.allclose(y, Hm[np.ix_(keep, keep)] @ x, rtol=0, atol=1e-13)
+    assert drop > 0
