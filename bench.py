@@ -539,6 +539,53 @@ def profile_hv(n: int):
     torch.cuda.synchronize()
 
 
+def profile_lanczos(n: int):
+    """A short mixed-precision Lanczos (n steps) on the benchmark sector, with
+    the same handle set-up as the timed steps: the target of the ncu captures
+    of the kernels as the benchmark launches them (fused Lanczos epilogue)."""
+    import torch
+    import __graft_entry__
+    __graft_entry__.build()
+    import gbr_synth as S
+    import gbr_synth.gpu as SG
+    import paper_2203_04158_gb300 as G
+    h, U = model()
+    H = G.gbr_ham_create(L, h, U, NUP, NDN)
+    D, _ = G.gbr_ham_info(H)
+    G.gbr_ham_tune(H, 32)
+    s = SG.uniform(S.SEED_START, D)
+    G.gbr_lanczos(H, s, n, prec=G.GBR_PREC_MIXED, refine=False, store_basis=0, profile=True)
+    torch.cuda.synchronize()
+
+
+def profile_rank(n_launch: int):
+    """Ranking kernels on 2^26 queries (0.5 GB of patterns, beyond L2): the
+    staggered M=32, N=16 sector and the 40-bit trie over 2^24 members; the
+    target of the ncu captures of k_comb_rank_pairs and k_trie_rank."""
+    import numpy as np
+    import torch
+    import __graft_entry__
+    __graft_entry__.build()
+    import gbr_synth as S
+    import gbr_synth.gpu as SG
+    import paper_2203_04158_gb300 as G
+    n = 1 << 26
+    c = G.gbr_comb_create(32, 16, 8)
+    u = SG.bounded(S.SEED_COMB_QUERIES, n, math.comb(32, 16))
+    q = torch.empty(n, dtype=torch.int64, device="cuda")
+    G.gbr_comb_unrank(c, u, q)
+    r = torch.empty(n, dtype=torch.int32, device="cuda")
+    for _ in range(n_launch):
+        G.gbr_comb_rank(c, q, r)
+    members = S.trie_member_set(1 << 24, 40)
+    tr = G.gbr_trie_create(members, 40, 8)
+    mdev = torch.from_numpy(members.view(np.int64)).cuda()
+    qt = mdev[SG.bounded(S.SEED_TRIE_QUERIES, n, 1 << 24)]
+    for _ in range(n_launch):
+        G.gbr_trie_rank(tr, qt, r)
+    torch.cuda.synchronize()
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -548,6 +595,10 @@ def main():
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--no-extras", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--profile-lanczos", type=int, default=0,
+                    help="run this many mixed Lanczos steps on the workload sector and exit (for ncu captures)")
+    ap.add_argument("--profile-rank", type=int, default=0,
+                    help="run the ranking kernels this many times on 2^26 queries and exit (for ncu captures)")
     ap.add_argument("--ranking-sweep", action="store_true",
                     help="print the M=28 ranking sweep (every filling) as JSON and exit")
     ap.add_argument("--profile-hv", type=int, default=0,
@@ -555,6 +606,12 @@ def main():
     args = ap.parse_args()
     if args.profile_hv:
         profile_hv(args.profile_hv)
+        return
+    if args.profile_rank:
+        profile_rank(args.profile_rank)
+        return
+    if args.profile_lanczos:
+        profile_lanczos(args.profile_lanczos)
         return
     if args.ranking_sweep:
         import torch
