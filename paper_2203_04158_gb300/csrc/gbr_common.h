@@ -125,6 +125,7 @@ struct gbr_trie {
     int wide;
     int smem_levels;         // number of leading levels copied to shared memory
     int64_t smem_entries;    // entries in those levels
+    int64_t hot_entries;     // leading levels read with the L2 evict_last policy
     gbr::DevBuf t;
     gbr::DevBuf members;
 };

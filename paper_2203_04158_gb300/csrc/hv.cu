@@ -272,6 +272,9 @@ __global__ void __launch_bounds__(128) k_gather(const int64_t Drows, const int64
                                                 const T *__restrict__ x, T *__restrict__ y, const CombineArgs ca) {
     constexpr bool COMBINE = MODE >= 1;
     constexpr bool LZ = MODE == 2;
+    // row stride of the staged Z tile: 16 bytes of padding put the TR rows of
+    // one column in different banks when the tile is written column by column
+    constexpr int ZS = 128 * VEC + 16 / (int)sizeof(T);
     extern __shared__ __align__(16) unsigned char smr[];
     uint32_t *st = reinterpret_cast<uint32_t *>(smr);
     T *sc = reinterpret_cast<T *>(smr + (((size_t)TR * hmax * 4 + 15) & ~(size_t)15));
@@ -304,7 +307,7 @@ __global__ void __launch_bounds__(128) k_gather(const int64_t Drows, const int64
         for (int e = threadIdx.x; e < 128 * VEC * TR; e += blockDim.x) {
             const int col = e / TR, i = e % TR;
             const int64_t c = cbase + col;
-            zs[i * (128 * VEC) + col] = (c < Dcols && i < nrow) ? __ldg(zt + c * Drows + r0 + i) : T(0);
+            zs[i * ZS + col] = (c < Dcols && i < nrow) ? __ldg(zt + c * Drows + r0 + i) : T(0);
         }
         __syncthreads();
     }
@@ -377,11 +380,11 @@ __global__ void __launch_bounds__(128) k_gather(const int64_t Drows, const int64
             }
             T zv[VEC];
             if (VEC == 4 && sizeof(T) == 4) {
-                const float4 z4 = *reinterpret_cast<const float4 *>(zs + i * (128 * VEC) + threadIdx.x * VEC);
+                const float4 z4 = *reinterpret_cast<const float4 *>(zs + i * ZS + threadIdx.x * VEC);
                 zv[0] = z4.x; zv[1 % VEC] = z4.y; zv[2 % VEC] = z4.z; zv[3 % VEC] = z4.w;
             } else {
 #pragma unroll
-                for (int v = 0; v < VEC; ++v) zv[v] = zs[i * (128 * VEC) + threadIdx.x * VEC + v];
+                for (int v = 0; v < VEC; ++v) zv[v] = zs[i * ZS + threadIdx.x * VEC + v];
             }
 #pragma unroll
             for (int v = 0; v < VEC; ++v) {
@@ -531,7 +534,7 @@ static int launch_gather(const gbr_ham *H, const SpinSector &lists, int64_t Drow
     const int64_t ncc = (Dcols + 128 * vec - 1) / (128 * vec);
     const int hmax = std::max(1, lists.hmax);
     const size_t smem = (((size_t)TR * hmax * 4 + 15) & ~(size_t)15) + (((size_t)TR * hmax * sizeof(T) + 15) & ~(size_t)15) +
-                        (COMBINE ? (size_t)TR * 128 * vec * sizeof(T) : 0);
+                        (COMBINE ? (size_t)TR * (128 * vec * sizeof(T) + 16) : 0);
     const int64_t blocks = nrb * ncc;
     if (blocks > 0x7FFFFFFF) return set_error(GBR_EINVAL, "sector too large for the gather grid");
 #define GBR_G(V, R)                                                                                          \

@@ -32,7 +32,7 @@ static StagK to_kernel(const StagDesc &d) {
     return k;
 }
 
-constexpr int kRankThreads = 256;
+constexpr int kRankThreads = 512;
 constexpr int kRankItems = 4;           // patterns per thread per tile (independent chains)
 constexpr int kSmemTableMax = 96 * 1024;
 
@@ -178,6 +178,21 @@ struct TrieK {
     int width[kMaxChunks];
 };
 
+// Loads with an L2 eviction priority: the upper levels of a trie (a few tens
+// of MB, touched by every query) are kept in L2 with evict_last while the
+// deep levels, read once per query at random, go with evict_first.
+template <typename E> __device__ __forceinline__ E ld_policy(const E *p, uint64_t pol);
+template <> __device__ __forceinline__ uint32_t ld_policy<uint32_t>(const uint32_t *p, uint64_t pol) {
+    uint32_t v;
+    asm volatile("ld.global.nc.L2::cache_hint.u32 %0, [%1], %2;" : "=r"(v) : "l"(p), "l"(pol));
+    return v;
+}
+template <> __device__ __forceinline__ uint64_t ld_policy<uint64_t>(const uint64_t *p, uint64_t pol) {
+    uint64_t v;
+    asm volatile("ld.global.nc.L2::cache_hint.u64 %0, [%1], %2;" : "=l"(v) : "l"(p), "l"(pol));
+    return v;
+}
+
 // Fig. trielookup for kRankItems independent patterns per thread, the walks
 // interleaved so that their dependent loads overlap.  Entries are unsigned
 // and the pointer arithmetic wraps, so the stored (start - smallest child)
@@ -185,7 +200,7 @@ struct TrieK {
 template <typename E, typename RT, int HT>
 __global__ void __launch_bounds__(kRankThreads) k_trie_rank(const uint64_t *__restrict__ pat, RT *__restrict__ out,
                                                             int64_t n, const TrieK d, const E *__restrict__ t,
-                                                            int64_t padded, int64_t smem_entries,
+                                                            int64_t padded, int64_t smem_entries, int64_t hot_end,
                                                             const uint64_t *__restrict__ members, int64_t n_members,
                                                             int check) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -193,6 +208,10 @@ __global__ void __launch_bounds__(kRankThreads) k_trie_rank(const uint64_t *__re
     if (smem_entries > 0) stage_table<E>(s, t, smem_entries);
     const E last = (E)(padded - 1);
     const E sm_end = (E)smem_entries;
+    const E hot = (E)hot_end;
+    uint64_t pol_last, pol_first;
+    asm volatile("createpolicy.fractional.L2::evict_last.b64 %0, 1.0;" : "=l"(pol_last));
+    asm volatile("createpolicy.fractional.L2::evict_first.b64 %0, 1.0;" : "=l"(pol_first));
     const int H = HT > 0 ? HT : d.H;
     const int64_t tile = (int64_t)kRankThreads * kRankItems;
     for (int64_t base = (int64_t)blockIdx.x * tile; base < n; base += (int64_t)gridDim.x * tile) {
@@ -212,7 +231,7 @@ __global__ void __launch_bounds__(kRankThreads) k_trie_rank(const uint64_t *__re
             for (int j = 0; j < kRankItems; ++j) {
                 E idx = k[j] + (E)((uint32_t)(a[j] >> d.shift[lvl]) & mask);
                 idx = idx > last ? last : idx;
-                k[j] = idx < sm_end ? s[idx] : __ldg(t + idx);
+                k[j] = idx < sm_end ? s[idx] : ld_policy<E>(t + idx, idx < hot ? pol_last : pol_first);
             }
         }
 #pragma unroll
@@ -221,7 +240,7 @@ __global__ void __launch_bounds__(kRankThreads) k_trie_rank(const uint64_t *__re
             if (i >= n) break;
             RT r = (RT)k[j];
             if (check) {
-                const bool ok = (uint64_t)k[j] < (uint64_t)n_members && __ldg(members + (uint64_t)k[j]) == a[j];
+                const bool ok = (uint64_t)k[j] < (uint64_t)n_members && ld_policy<uint64_t>(members + (uint64_t)k[j], pol_first) == a[j];
                 if (!ok) r = (RT)~(RT)0;
             }
             __stcs(out + i, r);
@@ -291,7 +310,7 @@ static int launch_comb_rank(const gbr_comb *c, const uint64_t *pat, RT *out, int
     const int64_t tbytes = c->desc.entries * (int64_t)sizeof(E);
     const int use_smem = tbytes <= kSmemTableMax;
     const size_t smem = use_smem ? (size_t)tbytes : 0;
-    int per_sm = use_smem ? std::max<int>(1, std::min<int>(8, (int)((200 * 1024) / std::max<int64_t>(tbytes, 1)))) : 8;
+    int per_sm = use_smem ? std::max<int>(1, std::min<int>(4, (int)((200 * 1024) / std::max<int64_t>(tbytes, 1)))) : 4;
     const int grid = grid_for(n, (int64_t)kRankThreads * kRankItems, per_sm);
     const int grid2 = grid_for((n >> 1) + 1, (int64_t)kRankThreads * kRankItems, per_sm);
     const E *tab = c->table.as<E>();
@@ -334,12 +353,13 @@ static int launch_trie_rank(const gbr_trie *T, const uint64_t *pat, RT *out, int
     d.H = T->H;
     for (int l = 0; l < T->H; ++l) { d.shift[l] = T->shift[l]; d.width[l] = T->width[l]; }
     const size_t smem = (size_t)T->smem_entries * sizeof(E);
-    const int grid = grid_for(n, (int64_t)kRankThreads * kRankItems, 8);
+    const int grid = grid_for(n, (int64_t)kRankThreads * kRankItems, 4);
 #define GBR_TRIE_CASE(HV)                                                                                  \
     case HV: {                                                                                             \
         auto kern = k_trie_rank<E, RT, HV>;                                                                \
         if (smem > 48 * 1024) GBR_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)); \
         kern<<<grid, kRankThreads, smem, st>>>(pat, out, n, d, T->t.as<E>(), T->padded, T->smem_entries,   \
+                                               T->hot_entries,                                             \
                                                T->members.as<uint64_t>(), T->n_members, check);            \
         break;                                                                                             \
     }
@@ -476,6 +496,12 @@ extern "C" int gbr_trie_create(const uint64_t *h_sorted, int64_t n, int M, int R
         if (plan.level_off[l + 1] * eb > 32 * 1024) break;
         T->smem_levels = l + 1;
         T->smem_entries = plan.level_off[l + 1];
+    }
+    // leading whole levels that fit 96 MB (of the 126 MB L2): kept in L2 by the walk
+    T->hot_entries = 0;
+    for (int l = 0; l < plan.H; ++l) {
+        if (plan.level_off[l + 1] * eb > ((int64_t)96 << 20)) break;
+        T->hot_entries = plan.level_off[l + 1];
     }
     if (T->wide) {
         rc = T->t.upload(t.data(), t.size() * 8);
