@@ -348,6 +348,30 @@ def config_extras(G, torch):
         t = e0.elapsed_time(e1) / 5 / 1e3
         res[f"fp{fp}"] = {"ms": t * 1e3, "elements_per_s": info["elements"] / t}
     out["ring12_allSz_trie_hv"] = res
+    # momentum-basis ring (Eq. Hk): L = 12 (M = 24), N_up = N_dn = 6, K_tot = 0,
+    # O(M^3) two-body terms built by the product rule, trie vs bisection ranking
+    Lk = 12
+    tk = [G.gbr_term_product(o, c) for c, o in S.momentum_ring_terms(Lk, 1.0, 4.0)]
+    stk = S.momentum_sector_states(Lk, 6, 6, 0)
+    Tk = G.gbr_termham_create(2 * Lk, tk, stk, 8)
+    infk = G.gbr_termham_info(Tk)
+    resk = {"dim": infk["dim"], "terms": len(tk), "elements_per_hv": infk["elements"],
+            "trie_overhead_f": infk["trie_elements"] / infk["dim"]}
+    x = SG.uniform(S.SEED_START, infk["dim"]).float()
+    y = torch.empty_like(x)
+    for mode in ("trie", "bisection"):
+        G.gbr_termham_set_bisect(Tk, mode == "bisection")
+        G.gbr_termham_hv(Tk, x, y)
+        e0.record()
+        for _ in range(5):
+            G.gbr_termham_hv(Tk, x, y)
+        e1.record()
+        torch.cuda.synchronize()
+        t = e0.elapsed_time(e1) / 5 / 1e3
+        resk[mode] = {"ms_fp32": t * 1e3, "elements_per_s": infk["elements"] / t,
+                      "ns_per_state_per_M3": t * 1e9 / infk["dim"] / (2 * Lk) ** 3}
+    resk["trie_speedup_over_bisection"] = resk["bisection"]["ms_fp32"] / resk["trie"]["ms_fp32"]
+    out["momentum_ring12_K0"] = resk
     return out
 
 

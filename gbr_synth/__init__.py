@@ -184,3 +184,40 @@ def trie_member_set(n: int, bits: int, seed: int = SEED_TRIE_SET) -> np.ndarray:
 def trie_query_members(n: int, nset: int, seed: int = SEED_TRIE_QUERIES, offset: int = 0) -> np.ndarray:
     """Member indices j_q = bounded(seed, q, nset); the query is set[j_q]."""
     return bounded(seed, np.arange(offset, offset + n, dtype=np.uint64), nset)
+
+
+# ---------------------------------------------------------------------------
+# Momentum-basis Hubbard ring (operator-product form of the Hamiltonian).
+# Orbitals: momentum k_m = 2 pi m / L, m = 0..L-1; spin down m -> bit m,
+# spin up m -> bit L + m.  Operator code = 2 * orbital + 1 for a creator,
+# 2 * orbital for an annihilator; a term is (coefficient, [codes left to right]).
+# ---------------------------------------------------------------------------
+
+def momentum_ring_terms(L: int, t: float = 1.0, U: float = 4.0):
+    """H = sum_{m,s} -2t cos(k_m) n_{m s}
+         + (U/L) sum_{m,m',q} c^dag_{m+q,up} c^dag_{m'-q,dn} c_{m',dn} c_{m,up}
+    (momenta mod L): the Fourier transform of the periodic ring with on-site U."""
+    terms = []
+    for m in range(L):
+        e = -2.0 * t * np.cos(2.0 * np.pi * m / L)
+        for off in (0, L):
+            terms.append((float(e), [2 * (off + m) + 1, 2 * (off + m)]))
+    for m in range(L):
+        for mp in range(L):
+            for q in range(L):
+                a = L + (m + q) % L          # up, created
+                b = (mp - q) % L             # down, created
+                terms.append((U / L, [2 * a + 1, 2 * b + 1, 2 * mp, 2 * (L + m)]))
+    return terms
+
+
+def momentum_sector_states(L: int, Nup: int, Ndn: int, K: int) -> np.ndarray:
+    """Sorted 2L-bit states with N_up, N_dn particles and total momentum
+    sum of m over occupied orbitals = K (mod L)."""
+    import itertools
+    out = []
+    for up in itertools.combinations(range(L), Nup):
+        for dn in itertools.combinations(range(L), Ndn):
+            if (sum(up) + sum(dn)) % L == K % L:
+                out.append(sum(1 << d for d in dn) | (sum(1 << u for u in up) << L))
+    return np.array(sorted(out), dtype=np.uint64)

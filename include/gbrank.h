@@ -270,6 +270,55 @@ int gbr_setham_info(const gbr_setham *S, int64_t *dim, int64_t *elements, int64_
 int gbr_setham_hv(const gbr_setham *S, const void *d_x, void *d_y, int fp, int check, void *stream);
 
 /* ------------------------------------------------------------------------
+ * General operator-product terms (Appendix: Eqs. Talpha1, Talpha2, ci and
+ * Fig. mul) and their on-the-fly H·v over a trie-ranked set.
+ * --------------------------------------------------------------------- */
+
+/* The tuple of a product T of creators and annihilators with a scalar:
+ *   T|a> = v delta(a & m, r) (-1)^h(a & s) |a ^ x>     (Eq. Talpha1)
+ *   <a|T = v delta(a & m, l) (-1)^h(a & s) <a ^ x|     (Eq. Talpha2)
+ * with h the number of set bits; bit i = spin-orbital i. */
+typedef struct {
+    double v;
+    uint64_t m, l, r, x, s;
+} gbr_term;
+
+/* Tuple of coef * O_1 O_2 ... O_nops (O_1 leftmost) built from the blocks of
+ * Eqs. ci by the product rule of Fig. mul.  ops[k] = 2 * orbital + 1 for a
+ * creator, 2 * orbital for an annihilator (orbital 0..63).  Host only; a
+ * product that vanishes by the Pauli principle has v = 0. */
+int gbr_term_product(const int *ops, int nops, double coef, gbr_term *out);
+
+/* Tuple of the product a b (Fig. mul).  Host only. */
+int gbr_term_mul(const gbr_term *a, const gbr_term *b, gbr_term *out);
+
+typedef struct gbr_termham gbr_termham;
+
+/* H = sum of nterms tuples on M spin-orbitals (M 1..64), acting on the n
+ * sorted, distinct M-bit states h_states (host, copied), ranked by a packed
+ * trie of radix 2^R.  Terms must not touch orbitals at or above M.
+ * Errors: GBR_EINVAL, GBR_ENOMEM, GBR_ECUDA. */
+int gbr_termham_create(int M, const gbr_term *h_terms, int nterms, const uint64_t *h_states, int64_t n, int R,
+                       gbr_termham **out);
+void gbr_termham_destroy(gbr_termham *T);
+
+/* bisect = 1: rank hop targets by bisection in the sorted member list (the
+ * established method of Sec. II, kept as the comparison point; targets are
+ * always checked); 0 (default): by the trie. */
+int gbr_termham_set_bisect(gbr_termham *T, int bisect);
+
+/* dim = n; elements = the (member, term) pairs whose left demand holds (the
+ * matrix elements one H·v visits); trie_elements = trie size. */
+int gbr_termham_info(const gbr_termham *T, int64_t *dim, int64_t *elements, int64_t *trie_elements);
+
+/* y = P H P x on the set: each member applies every term from the left
+ * (Eq. Talpha2), so y is the true row action for any term list, Hermitian
+ * or not; targets are ranked by the trie walk (Fig. trielookup) and, with
+ * check = 1, verified against the member list and dropped when outside.
+ * d_x, d_y: n floats (fp 32) or doubles (fp 64).  Asynchronous. */
+int gbr_termham_hv(const gbr_termham *T, const void *d_x, void *d_y, int fp, int check, void *stream);
+
+/* ------------------------------------------------------------------------
  * Lanczos ground state (cited in Sec. I and V-B; the recurrence is the
  * textbook three-term one).
  * --------------------------------------------------------------------- */

@@ -62,6 +62,9 @@ def lib():
             L.ora_hv_rows_seeded.argtypes = [i32, vp, vp, i32, i32, u64, vp, i64, vp]
             L.ora_seeded_uniform.restype = dbl; L.ora_seeded_uniform.argtypes = [u64, u64]
             L.ora_hv_set.restype = i32; L.ora_hv_set.argtypes = [i32, vp, vp, vp, i64, vp, vp, vp]
+            L.ora_hv_ops.restype = i32
+            L.ora_hv_ops.argtypes = [vp, vp, vp, vp, i32, vp, i64, vp, vp, vp]
+            L.ora_apply_ops.restype = i32; L.ora_apply_ops.argtypes = [vp, i32, u64, vp]
             L.ora_count_elements.restype = i64; L.ora_count_elements.argtypes = [i32, vp, i32, i32, i64, i64]
             L.ora_dense.restype = i32; L.ora_dense.argtypes = [i32, vp, vp, i32, i32, vp]
             L.ora_tridiag_lowest.restype = dbl; L.ora_tridiag_lowest.argtypes = [vp, vp, i32]
@@ -208,6 +211,45 @@ def hv_set(L, h, U, states, x):
 def fixed_N_states(L: int, N: int) -> np.ndarray:
     """All 2L-bit states with N particles in total (every S_z), sorted."""
     return enumerate_sector(2 * L, N)
+
+
+def _flatten_terms(terms):
+    coef = np.array([c for c, _ in terms], dtype=np.float64)
+    nops = np.array([len(o) for _, o in terms], dtype=np.int32)
+    off = np.concatenate([[0], np.cumsum(nops)[:-1]]).astype(np.int32)
+    ops = np.array([code for _, o in terms for code in o] or [0], dtype=np.int32)
+    return coef, nops, off, ops
+
+
+def hv_ops(terms, states, x):
+    """y = P H P x for H = sum of operator products ``terms`` = [(coef, [op codes
+    left to right])], op code = 2*orbital + creator; returns (y, dropped)."""
+    coef, nops, off, ops = _flatten_terms(terms)
+    st = np.ascontiguousarray(states, dtype=np.uint64)
+    x = _f64(x)
+    y = np.empty(st.size)
+    dropped = C.c_int64(0)
+    lib().ora_hv_ops(_p(coef), _p(nops), _p(off), _p(ops), len(terms), _p(st), st.size, _p(x), _p(y),
+                     C.byref(dropped))
+    return y, dropped.value
+
+
+def apply_ops(ops, alpha: int):
+    """Literal product application: (sign, resulting pattern)."""
+    o = np.ascontiguousarray(ops, dtype=np.int32)
+    b = C.c_uint64(0)
+    sgn = lib().ora_apply_ops(_p(o), o.size, int(alpha), C.byref(b))
+    return sgn, b.value
+
+
+def dense_ops(terms, states) -> np.ndarray:
+    """Dense matrix of P H P on the set (columns by applying H to unit vectors)."""
+    n = len(states)
+    Hm = np.empty((n, n))
+    for j in range(n):
+        e = np.zeros(n); e[j] = 1.0
+        Hm[:, j] = hv_ops(terms, states, e)[0]
+    return Hm
 
 
 def count_elements(L, h, Nup, Ndn, row0: int = 0, row1: int = 0) -> int:

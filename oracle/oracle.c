@@ -529,6 +529,49 @@ int ora_hv_set(int L, const double *h, const double *U, const uint64_t *states, 
     return 0;
 }
 
+/* y = P H P x on a sorted set for H given as a list of operator products
+ * (Eq. H in general form).  Term t has coefficient coef[t] and nops[t]
+ * operators starting at ops[off[t]], written left to right as in the
+ * product; operator code = 2*orbital + (1 for a creator, 0 for an
+ * annihilator).  Each product is applied literally to each member, rightmost
+ * operator first, by Eq. cee; results outside the set are dropped and
+ * counted. */
+int ora_hv_ops(const double *coef, const int *nops, const int *off, const int *ops, int nterms,
+               const uint64_t *states, int64_t n, const double *x, double *y, int64_t *dropped) {
+    for (int64_t i = 0; i < n; ++i) y[i] = 0.0;
+    int64_t drop = 0;
+    for (int64_t j = 0; j < n; ++j) {
+        for (int t = 0; t < nterms; ++t) {
+            uint64_t b = states[j];
+            int sgn = 1;
+            for (int o = nops[t] - 1; o >= 0 && sgn; --o) {
+                const int code = ops[off[t] + o];
+                const int orb = code >> 1;
+                sgn *= (code & 1) ? ora_cdag(&b, orb) : ora_c(&b, orb);
+            }
+            if (!sgn) continue;
+            int64_t i = ora_rank_bisect(states, n, b);
+            if (i < 0) { ++drop; continue; }
+            y[i] += coef[t] * sgn * x[j];
+        }
+    }
+    if (dropped) *dropped = drop;
+    return 0;
+}
+
+/* Literal application of one operator product to one state: returns the sign
+ * (0 if the product annihilates the state) and the resulting pattern. */
+int ora_apply_ops(const int *ops, int nops, uint64_t alpha, uint64_t *beta) {
+    uint64_t b = alpha;
+    int sgn = 1;
+    for (int o = nops - 1; o >= 0 && sgn; --o) {
+        const int code = ops[o];
+        sgn *= (code & 1) ? ora_cdag(&b, code >> 1) : ora_c(&b, code >> 1);
+    }
+    *beta = b;
+    return sgn;
+}
+
 /* Number of matrix elements one H x visits: the D diagonal entries plus every
  * off-diagonal (state, hop) pair that is non-zero.  Counted by applying the
  * off-diagonal hopping terms literally to every state; for rows only in

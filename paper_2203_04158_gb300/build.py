@@ -16,7 +16,7 @@ OUT = os.path.join(HERE, "_build")
 LIB = os.path.join(OUT, "libgbrank.so")
 INCLUDE = os.path.join(ROOT, "include")
 
-SOURCES = ["host.cpp", "rank.cu", "hv.cu", "hv_static.cu", "setham.cu", "lanczos.cu", "batch.cu"]
+SOURCES = ["host.cpp", "rank.cu", "hv.cu", "hv_static.cu", "setham.cu", "terms.cu", "lanczos.cu", "batch.cu"]
 HEADERS = ["gbr_common.h", "ham.h", "tridiag.cuh"]
 ARCH = ["-gencode=arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-I", INCLUDE, "-I", CSRC]

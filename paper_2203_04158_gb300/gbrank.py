@@ -46,6 +46,12 @@ class LanczosResult(C.Structure):
                 ("converged", C.c_int)]
 
 
+class Term(C.Structure):
+    """Tuple (v, m, l, r, x, s) of Eqs. Talpha1/Talpha2."""
+    _fields_ = [("v", C.c_double), ("m", C.c_uint64), ("l", C.c_uint64), ("r", C.c_uint64), ("x", C.c_uint64),
+                ("s", C.c_uint64)]
+
+
 class ModelDesc(C.Structure):
     _fields_ = [("L", C.c_int), ("h", C.c_void_p), ("U", C.c_void_p)]
 
@@ -84,6 +90,13 @@ def lib():
                 "gbr_hv_static": (i32, [vp, vp, vp, i32, vp]),
                 "gbr_launch_count": (i64, []),
                 "gbr_lanczos": (i32, [vp, vp, vp, vp, vp, vp, vp, vp]),
+                "gbr_term_product": (i32, [vp, i32, C.c_double, vp]),
+                "gbr_term_mul": (i32, [vp, vp, vp]),
+                "gbr_termham_create": (i32, [i32, vp, i32, vp, i64, i32, vp]),
+                "gbr_termham_destroy": (None, [vp]),
+                "gbr_termham_info": (i32, [vp, vp, vp, vp]),
+                "gbr_termham_hv": (i32, [vp, vp, vp, i32, i32, vp]),
+                "gbr_termham_set_bisect": (i32, [vp, i32]),
                 "gbr_setham_create": (i32, [i32, vp, vp, vp, i64, i32, vp]),
                 "gbr_setham_destroy": (None, [vp]),
                 "gbr_setham_info": (i32, [vp, vp, vp, vp]),
@@ -179,6 +192,10 @@ class Ham(_Handle):
 
 class SetHam(_Handle):
     _destroy = "gbr_setham_destroy"
+
+
+class TermHam(_Handle):
+    _destroy = "gbr_termham_destroy"
 
 
 # ---------------------------------------------------------------- combinations
@@ -360,6 +377,51 @@ def gbr_setham_hv(S: SetHam, x, y, check: int = 1, stream=None):
     if fp is None:
         raise ValueError("x must be float32 or float64")
     _check(lib().gbr_setham_hv(S, _dptr(x), _dptr(y), fp, int(check), _stream(stream)))
+    return y
+
+
+# -------------------------------------------------------- operator terms
+
+def gbr_term_product(ops, coef: float = 1.0) -> Term:
+    o = np.ascontiguousarray(ops, dtype=np.int32)
+    t = Term()
+    _check(lib().gbr_term_product(_hptr(o) if o.size else None, o.size, float(coef), C.byref(t)))
+    return t
+
+
+def gbr_term_mul(a: Term, b: Term) -> Term:
+    t = Term()
+    _check(lib().gbr_term_mul(C.byref(a), C.byref(b), C.byref(t)))
+    return t
+
+
+def gbr_termham_create(M: int, terms, states: np.ndarray, R: int = 8) -> TermHam:
+    """terms: a sequence of Term tuples."""
+    arr = (Term * len(terms))(*terms)
+    st = np.ascontiguousarray(states, dtype=np.uint64)
+    p = C.c_void_p()
+    _check(lib().gbr_termham_create(M, arr, len(terms), _hptr(st), st.size, R, C.byref(p)))
+    return TermHam(p)
+
+
+def gbr_termham_set_bisect(T: TermHam, bisect: bool):
+    _check(lib().gbr_termham_set_bisect(T, int(bool(bisect))))
+
+
+def gbr_termham_info(T: TermHam):
+    d, e, t = C.c_int64(), C.c_int64(), C.c_int64()
+    _check(lib().gbr_termham_info(T, C.byref(d), C.byref(e), C.byref(t)))
+    return dict(dim=d.value, elements=e.value, trie_elements=t.value)
+
+
+def gbr_termham_hv(T: TermHam, x, y, check: int = 1, stream=None):
+    import torch
+    if x.dtype != y.dtype:
+        raise ValueError("x and y must have the same dtype")
+    fp = {torch.float32: 32, torch.float64: 64}.get(x.dtype)
+    if fp is None:
+        raise ValueError("x must be float32 or float64")
+    _check(lib().gbr_termham_hv(T, _dptr(x), _dptr(y), fp, int(check), _stream(stream)))
     return y
 
 

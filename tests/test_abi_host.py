@@ -116,3 +116,65 @@ def test_seeded_generator_twins_agree():
     py = S.uniform(1, idx)
     for i, v in zip(idx, py):
         assert oracle.seeded_uniform(1, int(i)) == v
+
+
+def tuple_apply_right(t, a):
+    """Eq. Talpha1 on a basis state: (coefficient, result) or (0, None)."""
+    if (a & t.m) != t.r or t.v == 0.0:
+        return 0.0, None
+    sgn = -1.0 if bin(a & t.s).count("1") & 1 else 1.0
+    return t.v * sgn, a ^ t.x
+
+
+def tuple_apply_left(t, a):
+    """Eq. Talpha2: <a| T = coefficient <result|."""
+    if (a & t.m) != t.l or t.v == 0.0:
+        return 0.0, None
+    sgn = -1.0 if bin(a & t.s).count("1") & 1 else 1.0
+    return t.v * sgn, a ^ t.x
+
+
+def test_building_blocks_follow_eqs_ci(G):
+    for i in (0, 3, 17, 63):
+        c = G.gbr_term_product([2 * i])
+        cd = G.gbr_term_product([2 * i + 1])
+        b = 1 << i
+        assert (c.v, c.m, c.l, c.r, c.x, c.s) == (1.0, b, 0, b, b, b - 1)
+        assert (cd.v, cd.m, cd.l, cd.r, cd.x, cd.s) == (1.0, b, b, 0, b, b - 1)
+
+
+@pytest.mark.parametrize("seed", range(6))
+def test_product_rule_matches_literal_operator_application(G, seed):
+    """Fig. mul, built up operator by operator, reproduces Eq. cee applied
+    literally for every basis state -- from the right (Talpha1) and, for the
+    transpose matrix element, from the left (Talpha2)."""
+    rng = np.random.default_rng(seed)
+    M = 7
+    for _ in range(60):
+        k = int(rng.integers(1, 7))
+        ops = [int(rng.integers(0, 2 * M)) for _ in range(k)]
+        coef = float(rng.normal())
+        t = G.gbr_term_product(ops, coef)
+        for a in range(1 << M):
+            sgn, b = oracle.apply_ops(ops, a)
+            cv, cb = tuple_apply_right(t, a)
+            if sgn == 0:
+                assert cv == 0.0
+            else:
+                assert cb == b and cv == pytest.approx(coef * sgn, abs=1e-15)
+                # <b| T |a> = coef*sgn: the left application of T to <b| lands on <a|
+                lv, lb = tuple_apply_left(t, b)
+                assert lb == a and lv == pytest.approx(coef * sgn, abs=1e-15)
+
+
+def test_mul_is_the_product_of_terms(G):
+    rng = np.random.default_rng(9)
+    for _ in range(100):
+        A = [int(x) for x in rng.integers(0, 12, size=int(rng.integers(1, 4)))]
+        B = [int(x) for x in rng.integers(0, 12, size=int(rng.integers(1, 4)))]
+        ab = G.gbr_term_mul(G.gbr_term_product(A, 2.0), G.gbr_term_product(B, -0.5))
+        ref = G.gbr_term_product(A + B, -1.0)
+        if ref.v == 0.0:
+            assert ab.v == 0.0
+        else:
+            assert (ab.v, ab.m, ab.l, ab.r, ab.x, ab.s) == (ref.v, ref.m, ref.l, ref.r, ref.x, ref.s)

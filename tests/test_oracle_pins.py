@@ -316,3 +316,39 @@ def test_set_hv_projects_onto_open_sets():
     y, drop = oracle.hv_set(L, h, U, sub, x)
     assert np.allclose(y, Hm[np.ix_(keep, keep)] @ x, rtol=0, atol=1e-13)
     assert drop > 0
+
+
+def test_momentum_ring_spectrum_equals_real_space_ring():
+    # the momentum-basis Hamiltonian is the real-space periodic ring in another
+    # basis: the union of its K_tot sectors has the ring's sector spectrum
+    for L, N, U in ((4, 2, 4.0), (5, 2, 3.0), (6, 3, 4.0)):
+        terms = S.momentum_ring_terms(L, 1.0, U)
+        ev = []
+        for K in range(L):
+            st = S.momentum_sector_states(L, N, N, K)
+            Hm = oracle.dense_ops(terms, st)
+            assert np.allclose(Hm, Hm.T, atol=1e-12)
+            ev.extend(np.linalg.eigvalsh(Hm))
+            _, drop = oracle.hv_ops(terms, st, np.ones(st.size))
+            assert drop == 0                         # K_tot is conserved
+        ref = np.linalg.eigvalsh(oracle.dense(L, S.chain(L), S.uniform_U(L, U), N, N))
+        assert np.allclose(np.sort(ev), ref, atol=1e-10)
+
+
+def test_operator_products_match_the_one_body_form():
+    # the hopping and U terms written as operator products give the same H·v
+    L = 5
+    h, U = S.square(5, 1, 1.0, 0.0) + np.diag(np.arange(5) * 0.25), np.array([1.0, 0.0, 2.0, 0.5, 0.0])
+    terms = []
+    for sp in (0, L):
+        for p in range(L):
+            for q in range(L):
+                if h[p, q] != 0.0:
+                    terms.append((h[p, q], [2 * (sp + p) + 1, 2 * (sp + q)]))
+    for p in range(L):
+        if U[p]:
+            terms.append((U[p], [2 * (L + p) + 1, 2 * p + 1, 2 * p, 2 * (L + p)]))
+    st = oracle.sector_states(L, 2, 3)
+    x = S.start_vector(st.size)
+    y, drop = oracle.hv_ops(terms, st, x)
+    assert drop == 0 and np.allclose(y, oracle.hv(L, h, U, 2, 3, x), rtol=0, atol=1e-13)
