@@ -221,7 +221,8 @@ __global__ void __launch_bounds__(kBatchThreads) k_batch(const SectorDesc *__res
         const int K = min(iters, D);
         // Restarted Lanczos: each cycle stops as soon as the lowest Ritz pair
         // of T has converged to FP32 level (residual estimate
-        // beta_{k+1} |s_k| <= 1e-6 max(|alpha|, beta)), which keeps the FP32
+        // beta_{k+1} |s_k| <= 1e-6 max(|alpha|, beta), tested every 4 steps and
+        // at the last step of the cycle), which keeps the FP32
         // recurrence from running on after convergence and spoiling the Ritz
         // vector; a cycle that ends unconverged restarts from its Ritz vector
         // (at most three cycles).  Each cycle runs the recurrence twice: once
@@ -289,13 +290,20 @@ __global__ void __launch_bounds__(kBatchThreads) k_batch(const SectorDesc *__res
                         kdone = k + 1;
                         scale = fmax(scale, b);
                         __syncthreads();
-                        // lowest Ritz pair of T_{k+1} and its residual estimate
-                        const double lam = tridiag_lowest_block(alpha, beta, kdone);
-                        if (threadIdx.x == 0) {
-                            tridiag_vector_thread(alpha, beta, kdone, lam, svec, work);
-                            if (b * fabs(svec[kdone - 1]) <= 1e-6 * scale || b <= 1e-13 * scale) conv_s = 1;
+                        // lowest Ritz pair of T_{k+1} and its residual estimate,
+                        // every 4 steps and at the end of the cycle
+                        if (b <= 1e-13 * scale) {
+                            if (threadIdx.x == 0) conv_s = 1;
                         }
                         __syncthreads();
+                        if (conv_s || (kdone & 3) == 0 || k + 1 >= Kc) {
+                            const double lam = tridiag_lowest_block(alpha, beta, kdone);
+                            if (threadIdx.x == 0) {
+                                tridiag_vector_thread(alpha, beta, kdone, lam, svec, work);
+                                if (b * fabs(svec[kdone - 1]) <= 1e-6 * scale) conv_s = 1;
+                            }
+                            __syncthreads();
+                        }
                         if (conv_s || k + 1 >= Kc) break;
                     }
                     __syncthreads();

@@ -178,3 +178,17 @@ def test_mul_is_the_product_of_terms(G):
             assert ab.v == 0.0
         else:
             assert (ab.v, ab.m, ab.l, ab.r, ab.x, ab.s) == (ref.v, ref.m, ref.l, ref.r, ref.x, ref.s)
+
+
+def test_term_and_set_hamiltonians_reject_bad_input_on_the_host(G):
+    t = G.gbr_term_product([2 * 9 + 1, 2 * 0])                 # touches orbital 9
+    with pytest.raises(G.GbrError) as e:
+        G.gbr_termham_create(8, [t], np.array([1, 2], dtype=np.uint64))
+    assert e.value.code == G.GBR_EINVAL and "orbitals" in str(e.value)
+    with pytest.raises(G.GbrError):
+        G.gbr_term_product([200])                               # orbital 100
+    with pytest.raises(G.GbrError):
+        G.gbr_termham_create(65, [t], np.array([1], dtype=np.uint64))
+    hbad = np.zeros((3, 3)); hbad[0, 1] = 1.0                   # not symmetric
+    with pytest.raises(G.GbrError):
+        G.gbr_setham_create(3, hbad, None, np.array([1, 2], dtype=np.uint64))

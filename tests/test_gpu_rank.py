@@ -203,3 +203,22 @@ def test_comb_unaligned_views_use_the_scalar_kernel(G):
     r64 = torch.empty(u.size + 1, dtype=torch.int64, device="cuda")
     G.gbr_comb_rank(c, pats[1:], r64[1:])
     assert np.array_equal(as_u64(r64[1:]), u)
+
+
+def test_trie_edge_cases(G):
+    """One member; 64-bit patterns; empty query batches."""
+    import torch
+    one = np.array([0b1011], dtype=np.uint64)
+    t = G.gbr_trie_create(one, 4, 3)
+    r = torch.empty(3, dtype=torch.int64, device="cuda")
+    G.gbr_trie_rank(t, to_dev_u64(np.array([0b1011, 0b0011, 0], dtype=np.uint64)), r, check=1)
+    assert list(as_u64(r)) == [0, 2**64 - 1, 2**64 - 1]
+    G.gbr_trie_rank(t, torch.empty(0, dtype=torch.int64, device="cuda"), torch.empty(0, dtype=torch.int64, device="cuda"))
+    rng = np.random.default_rng(64)
+    wide = np.unique(rng.integers(0, 2**63, size=3000, dtype=np.uint64) * np.uint64(2) + np.uint64(1))
+    t64 = G.gbr_trie_create(wide, 64, 8)
+    r64 = torch.empty(wide.size, dtype=torch.int64, device="cuda")
+    G.gbr_trie_rank(t64, to_dev_u64(wide), r64, check=1)
+    assert np.array_equal(as_u64(r64), np.arange(wide.size, dtype=np.uint64))
+    G.gbr_trie_rank_bisect(t64, to_dev_u64(wide), r64, check=1)
+    assert np.array_equal(as_u64(r64), np.arange(wide.size, dtype=np.uint64))
