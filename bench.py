@@ -278,6 +278,31 @@ def ranking_extras(G, torch):
     return out
 
 
+def hv_path_extras(G, torch, H, s):
+    """One H·v of the benchmark sector per path and precision (average of 10
+    launches after 3 warm-up, CUDA events), restoring the tuned path."""
+    keep = G.gbr_ham_get_path(H)
+    D, elems = G.gbr_ham_info(H)
+    out = {}
+    for fp, x in ((32, s.float()), (64, s)):
+        y = torch.empty_like(x)
+        for name, path in (("factored", G.GBR_HV_FACTORED), ("fused", G.GBR_HV_FUSED)):
+            G.gbr_ham_set_path(H, path)
+            for _ in range(3):
+                G.gbr_hv(H, x, y)
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            for _ in range(10):
+                G.gbr_hv(H, x, y)
+            e1.record()
+            torch.cuda.synchronize()
+            ms = e0.elapsed_time(e1) / 10
+            out[f"{name}_fp{fp}"] = {"ms": ms, "elements_per_s": elems / (ms / 1e3)}
+        del x, y
+    G.gbr_ham_set_path(H, keep)
+    return out
+
+
 def config_extras(G, torch):
     """The other configurations, each solved once (outside the timed steps)."""
     import numpy as np
@@ -475,11 +500,12 @@ def run_ours(args, rank: int, world: int):
     # dominant kernel from the live per-stage event timings
     st = np.sum([r["stage_seconds"] for r in results], axis=0)
     nl = np.sum([r["stage_launches"] for r in results], axis=0)
-    names = ["k_hop_lists", "k_transpose", "k_gather_dn", "k_gather_up_combine"]
+    path = G.gbr_ham_get_path(H)
     # algorithmic bytes of each kernel's own function: transpose reads and
     # writes a vector; the spin-down gather reads X^T once and writes Z^T;
     # the spin-up gather as launched by the Lanczos reads X once, Z^T and
     # v_{k-1} (fused first update) and writes w
+    names = ["k_hop_lists", "k_transpose", "k_gather_dn", "k_gather_up_combine"]
     bytes_per = [0, 2 * D * 4, 2 * D * 4, 4 * D * 4]
     k = int(np.argmax(st))
     avg = st[k] / max(nl[k], 1)
@@ -489,7 +515,8 @@ def run_ours(args, rank: int, world: int):
                 "traffic": ncu_traffic(names[k]), "kernel": names[k], "peak_source": src,
                 "avg_launch_ms": avg * 1e3,
                 "algorithmic_bytes_per_launch": bytes_per[k],
-                "stage_share": {names[i]: float(st[i] / st.sum()) for i in range(4)}}
+                "stage_share": {names[i]: float(st[i] / st.sum()) for i in range(4)},
+                "hv_path": {G.GBR_HV_FUSED: "fused", G.GBR_HV_FACTORED: "factored"}.get(path, str(path))}
 
     # end to end through the public API with host buffers
     s_host = s.cpu().pin_memory()
@@ -536,6 +563,7 @@ def run_ours(args, rank: int, world: int):
                                        "fp64_s": r6t["seconds"], "fp64_iters": r6t["iters"],
                                        "fp64_rel_err": abs(r6t["E0"] - ref) / abs(ref),
                                        "speedup": r6t["seconds"] / rmt["seconds"]}}
+        line["hv_paths"] = hv_path_extras(G, torch, H, s)
         try:
             line["ranking"] = ranking_extras(G, torch)
         except Exception as ex:  # report rather than hide

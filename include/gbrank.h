@@ -188,6 +188,10 @@ int gbr_ham_info(const gbr_ham *H, int64_t *dim, int64_t *elements);
 /* Selects the H·v implementation (GBR_HV_*) used by gbr_hv and gbr_lanczos. */
 int gbr_ham_set_path(gbr_ham *H, int path);
 
+/* The H·v implementation the handle currently uses (GBR_HV_*; GBR_HV_AUTO
+ * until set or tuned).  Errors: GBR_EINVAL for a NULL argument. */
+int gbr_ham_get_path(const gbr_ham *H, int *path);
+
 /* y = H x on the sector (Eq. mvblock with Eq. Talpha applied on the fly).
  *   d_x, d_y: dim elements (device), float when fp == 32, double when
  *   fp == 64; they must not overlap.  Deterministic: each y element has one

@@ -37,9 +37,11 @@ struct HamK {
     uint32_t nbr[kMaxL];       // nbr[p]: sites q with h_pq != 0, q != p
 };
 
-// Fused first update of a Lanczos step, done in the epilogue of the spin-up
-// pass: w = H v_k - beta_k v_{k-1} (k read from device memory; no update when
-// k == 0) and per-CTA partial sums of <w, v_k> (part may be NULL).
+// Fused first update of a Lanczos step on the unnormalised vectors
+// u_j = g_j v_j (g_0 = 1, g_j = beta_j), done in the epilogue of the spin-up
+// pass: w = H u_k / g_k - (beta_k / g_{k-1}) u_{k-1} (k read from device
+// memory; w = H u_0 when k == 0) and per-CTA partial sums of <w, u_k> (part
+// may be NULL).
 struct LzHook {
     const void *vprev;
     const double *beta;

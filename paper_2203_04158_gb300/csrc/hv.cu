@@ -262,8 +262,10 @@ struct CombineArgs {
 };
 
 // MODE 0: Z = H_lists W.  MODE 1: y = H_up X + Dg o X + Z (combine).  MODE 2:
-// as 1, then the first update of a Lanczos step in the same epilogue,
-// w = y - beta_k v_{k-1} (k > 0) and the block's partial <w, x>.
+// as 1, then the first update of a Lanczos step on unnormalised vectors
+// u_j = g_j v_j (g_0 = 1, g_j = beta_j) in the same epilogue,
+// w = y / g_k - (beta_k / g_{k-1}) u_{k-1} (k > 0; x = u_k) and the block's
+// partial <w, x>.
 template <typename T, int VEC, int MODE, int TR>
 __global__ void __launch_bounds__(128) k_gather(const int64_t Drows, const int64_t Dcols, const int hmax,
                                                 const int64_t nrb, const uint16_t *__restrict__ cnt,
@@ -314,10 +316,13 @@ __global__ void __launch_bounds__(128) k_gather(const int64_t Drows, const int64
     const bool active = c0 < Dcols;
     DotAcc<T> dacc;
     int klz = 0;
-    T blz = T(0);
+    T slz = T(1), blz = T(0);
     if (LZ) {
         klz = *ca.lz.kstate;
-        blz = klz > 0 ? (T)ca.lz.beta[klz] : T(0);
+        if (klz > 0) {
+            slz = (T)(1.0 / ca.lz.beta[klz]);
+            blz = (T)(ca.lz.beta[klz] / (klz > 1 ? ca.lz.beta[klz - 1] : 1.0));
+        }
     }
     // combine epilogue: column states and diagonals of this thread's columns
     uint32_t ad[VEC];
@@ -413,7 +418,7 @@ __global__ void __launch_bounds__(128) k_gather(const int64_t Drows, const int64
                         vp[0] = __ldcs(vpv);
                     }
 #pragma unroll
-                    for (int v = 0; v < VEC; ++v) acc[v] -= blz * vp[v];
+                    for (int v = 0; v < VEC; ++v) acc[v] = slz * acc[v] - blz * vp[v];
                 }
 #pragma unroll
                 for (int v = 0; v < VEC; ++v) dacc.add(acc[v], xo[v]);
@@ -898,6 +903,13 @@ extern "C" int gbr_ham_set_path(gbr_ham *H, int path) {
     if (path != GBR_HV_AUTO && path != GBR_HV_FUSED && path != GBR_HV_FACTORED)
         return set_error(GBR_EINVAL, "unknown path %d", path);
     H->path = path;
+    return GBR_OK;
+}
+
+extern "C" int gbr_ham_get_path(const gbr_ham *H, int *path) {
+    clear_error();
+    if (!H || !path) return set_error(GBR_EINVAL, "NULL argument");
+    *path = H->path;
     return GBR_OK;
 }
 

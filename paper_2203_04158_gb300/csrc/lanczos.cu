@@ -4,6 +4,11 @@
 //   w -= alpha_k v_k;  [two classical Gram-Schmidt passes against v_0..v_k];
 //   beta_{k+1} = |w|;  stop if beta_{k+1} <= 1e-13 max_j(|alpha_j|, beta_j);
 //   v_{k+1} = w / beta_{k+1};  E = lowest eigenvalue of T_k.
+// The vectors are kept unnormalised, u_j = g_j v_j with g_0 = 1 and
+// g_j = beta_j: the division by beta_{k+1} is folded into the next step
+// (w = H u_k / g_k - (beta_k / g_{k-1}) u_{k-1}, alpha_k = <w, u_k> / g_k,
+// w -= (alpha_k / g_k) u_k), which saves a full vector pass per step; the
+// scalars alpha, beta are those of the normalised recurrence.
 // All scalars stay on the device (no host round trip per step).  Reductions
 // use a fixed grid and a fixed summation tree, so every run is bit-identical
 // and the basis can be recomputed exactly in a second pass.
@@ -41,14 +46,19 @@ template <typename T> struct alignas(16) Pack {
     T e[N];
 };
 
-// w -= beta_k v_prev (k > 0); partial <w, v>
+// norm g_j of the unnormalised vector u_j (g_0 = 1, g_j = beta_j)
+__device__ __forceinline__ double lz_gamma(const double *beta, int j) { return j > 0 ? beta[j] : 1.0; }
+
+// w = H u_k / g_k - (beta_k / g_{k-1}) u_{k-1} (k > 0; w = H u_0 at k = 0),
+// with H u_k in w on entry; partial <w, u_k>
 template <typename T>
 __global__ void __launch_bounds__(kRedThreads) k_step1(const LzState *st, const double *beta, const T *__restrict__ vprev,
                                                        const T *__restrict__ v, T *__restrict__ w, int64_t n, double *part,
                                                        int want_dot) {
     if (st->stop) return;
     const int k = st->k;
-    const T b = k > 0 ? (T)beta[k] : T(0);
+    const T s1 = (T)(1.0 / lz_gamma(beta, k));
+    const T b = k > 0 ? (T)(beta[k] / lz_gamma(beta, k - 1)) : T(0);
     DotAcc<T> acc;
     constexpr int V = Pack<T>::N;
     const int64_t np = n / V;
@@ -62,7 +72,7 @@ __global__ void __launch_bounds__(kRedThreads) k_step1(const LzState *st, const 
         if (k > 0) {
             const Pack<T> pp = VP[p];
 #pragma unroll
-            for (int j = 0; j < V; ++j) wp.e[j] -= b * pp.e[j];
+            for (int j = 0; j < V; ++j) wp.e[j] = s1 * wp.e[j] - b * pp.e[j];
             W[p] = wp;
         }
         if (want_dot)
@@ -71,7 +81,7 @@ __global__ void __launch_bounds__(kRedThreads) k_step1(const LzState *st, const 
     }
     for (int64_t i = np * V + tid; i < n; i += stride) {
         T wi = w[i];
-        if (k > 0) wi -= b * vprev[i];
+        if (k > 0) wi = s1 * wi - b * vprev[i];
         w[i] = wi;
         if (want_dot) acc.add(wi, v[i]);
     }
@@ -80,18 +90,24 @@ __global__ void __launch_bounds__(kRedThreads) k_step1(const LzState *st, const 
     if (threadIdx.x == 0) part[blockIdx.x] = r;
 }
 
-// w -= alpha_k v; partial <w, w>
+// w -= (alpha_k / g_k) u_k, which makes w the next unnormalised vector
+// u_{k+1}; partial <w, w>; with a basis, u_{k+1} also into its slot k + 1
 template <typename T>
-__global__ void __launch_bounds__(kRedThreads) k_step2(const LzState *st, const double *alpha, const T *__restrict__ v,
-                                                       T *__restrict__ w, int64_t n, double *part, int want_dot) {
+__global__ void __launch_bounds__(kRedThreads) k_step2(const LzState *st, const double *alpha, const double *beta,
+                                                       const T *__restrict__ v, T *__restrict__ w, T *__restrict__ basis,
+                                                       int64_t n, double *part, int want_dot) {
     if (st->stop) return;
-    const T a = (T)alpha[st->k];
+    const int k = st->k;
+    const T a = (T)(alpha[k] / lz_gamma(beta, k));
+    T *vb = basis ? basis + (int64_t)(k + 1) * n : nullptr;
     DotAcc<T> acc;
     constexpr int V = Pack<T>::N;
-    const int64_t np = n / V;
+    // the basis slot is aligned to 16 bytes only when n * sizeof(T) is
+    const bool vec_ok = !vb || ((uintptr_t)vb & 15u) == 0;
+    const int64_t np = vec_ok ? n / V : 0;
     const int64_t tid = blockIdx.x * (int64_t)blockDim.x + threadIdx.x, stride = (int64_t)gridDim.x * blockDim.x;
     const Pack<T> *VV = reinterpret_cast<const Pack<T> *>(v);
-    Pack<T> *W = reinterpret_cast<Pack<T> *>(w);
+    Pack<T> *W = reinterpret_cast<Pack<T> *>(w), *VB = reinterpret_cast<Pack<T> *>(vb);
 #pragma unroll 2
     for (int64_t p = tid; p < np; p += stride) {
         Pack<T> wp = W[p];
@@ -99,6 +115,7 @@ __global__ void __launch_bounds__(kRedThreads) k_step2(const LzState *st, const 
 #pragma unroll
         for (int j = 0; j < V; ++j) wp.e[j] -= a * vv.e[j];
         W[p] = wp;
+        if (vb) VB[p] = wp;
         if (want_dot)
 #pragma unroll
             for (int j = 0; j < V; ++j) acc.add(wp.e[j], wp.e[j]);
@@ -106,6 +123,7 @@ __global__ void __launch_bounds__(kRedThreads) k_step2(const LzState *st, const 
     for (int64_t i = np * V + tid; i < n; i += stride) {
         const T wi = w[i] - a * v[i];
         w[i] = wi;
+        if (vb) vb[i] = wi;
         if (want_dot) acc.add(wi, wi);
     }
     if (!want_dot) return;
@@ -134,7 +152,8 @@ __global__ void __launch_bounds__(kRedThreads) k_finalize(LzState *st, double *a
     if (threadIdx.x != 0) return;
     const int k = st->k;
     if (which == 0) {
-        alpha[k] = s;
+        // the partials hold <w, u_k> = g_k alpha_k
+        alpha[k] = s / lz_gamma(beta, k);
         st->scale = fmax(st->scale, fabs(s));
     } else {
         const double b = sqrt(fmax(s, 0.0));
@@ -149,42 +168,13 @@ __global__ void __launch_bounds__(kRedThreads) k_finalize(LzState *st, double *a
     }
 }
 
-// v_next = w / beta_{k+1} (also into the stored basis)
-template <typename T>
-__global__ void __launch_bounds__(kRedThreads) k_step3(LzState *st, const double *beta, const T *__restrict__ w,
-                                                       T *__restrict__ vnext, T *__restrict__ basis, int64_t n) {
-    if (st->stop) return;
-    const int k = st->k;
-    const T inv = (T)(1.0 / beta[k + 1]);
-    T *vb = basis ? basis + (int64_t)(k + 1) * n : nullptr;
-    constexpr int V = Pack<T>::N;
-    // the basis slot is aligned to 16 bytes only when n * sizeof(T) is
-    const bool vec_ok = !vb || ((uintptr_t)vb & 15u) == 0;
-    const int64_t np = vec_ok ? n / V : 0;
-    const int64_t tid = blockIdx.x * (int64_t)blockDim.x + threadIdx.x, stride = (int64_t)gridDim.x * blockDim.x;
-    const Pack<T> *W = reinterpret_cast<const Pack<T> *>(w);
-    Pack<T> *VN = reinterpret_cast<Pack<T> *>(vnext), *VB = reinterpret_cast<Pack<T> *>(vb);
-#pragma unroll 2
-    for (int64_t p = tid; p < np; p += stride) {
-        Pack<T> x = W[p];
-#pragma unroll
-        for (int j = 0; j < V; ++j) x.e[j] *= inv;
-        VN[p] = x;
-        if (vb) VB[p] = x;
-    }
-    for (int64_t i = np * V + tid; i < n; i += stride) {
-        const T vi = w[i] * inv;
-        vnext[i] = vi;
-        if (vb) vb[i] = vi;
-    }
-}
-
 __global__ void k_advance(LzState *st) {
     if (threadIdx.x == 0 && blockIdx.x == 0 && !st->stop) st->k += 1;
 }
 
-// Re-orthogonalisation: c_j = <w, v_j> for j = 0..k (grid.y = j), then
-// w -= sum_j c_j v_j.
+// Re-orthogonalisation against the stored (unnormalised) basis u_j:
+// d_j = <w, u_j> for j = 0..k (grid.y = j), c_j = d_j / g_j^2, then
+// w -= sum_j c_j u_j (= sum_j <w, v_j> v_j).
 template <typename T>
 __global__ void __launch_bounds__(kRedThreads) k_multidot(const LzState *st, const T *__restrict__ basis,
                                                           const T *__restrict__ w, int64_t n, double *part) {
@@ -199,25 +189,30 @@ __global__ void __launch_bounds__(kRedThreads) k_multidot(const LzState *st, con
     if (threadIdx.x == 0) part[(int64_t)j * gridDim.x + blockIdx.x] = r;
 }
 
-__global__ void __launch_bounds__(kRedThreads) k_multidot_fin(const LzState *st, const double *part, int nparts, double *c) {
+__global__ void __launch_bounds__(kRedThreads) k_multidot_fin(const LzState *st, const double *beta, const double *part,
+                                                              int nparts, double *c) {
     if (st->stop) return;
     const int j = blockIdx.x;
     if (j > st->k) return;
     double v = 0.0;
     for (int i = threadIdx.x; i < nparts; i += blockDim.x) v += part[(int64_t)j * nparts + i];
     const double s = block_sum(v);
-    if (threadIdx.x == 0) c[j] = s;
+    const double g = lz_gamma(beta, j);
+    if (threadIdx.x == 0) c[j] = s / (g * g);
 }
 
+// w -= sum_j c_j u_j; the last pass also writes the result into slot k + 1
 template <typename T>
-__global__ void __launch_bounds__(kRedThreads) k_multiaxpy(const LzState *st, const T *__restrict__ basis, const double *c,
-                                                           T *__restrict__ w, int64_t n) {
+__global__ void __launch_bounds__(kRedThreads) k_multiaxpy(const LzState *st, T *__restrict__ basis, const double *c,
+                                                           T *__restrict__ w, int64_t n, int write_slot) {
     if (st->stop) return;
     const int k = st->k;
+    T *slot = write_slot ? basis + (int64_t)(k + 1) * n : nullptr;
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
         T wi = w[i];
         for (int j = 0; j <= k; ++j) wi -= (T)c[j] * basis[(int64_t)j * n + i];
         w[i] = wi;
+        if (slot) slot[i] = wi;
     }
 }
 
@@ -257,14 +252,16 @@ __global__ void k_copy_ritz(const LzState *st, const double *val, double *ritz) 
     if (threadIdx.x == 0) ritz[st->k] = val[0];
 }
 
-// x (FP64) = sum_j s_j v_j over the stored basis.  FP64 basis: FMA chain.
+// x (FP64) = sum_j s_j v_j = sum_j (s_j / g_j) u_j over the stored
+// (unnormalised) basis.  FP64 basis: FMA chain.
 // FP32 basis: each s_j is split into two floats once (shared memory) and the
 // products are accumulated per element in a two-float sum.  Each thread
 // takes 16-byte packs of consecutive elements, so one load per basis vector
 // serves several elements.
 template <typename T>
-__global__ void __launch_bounds__(kRedThreads) k_ritz_from_basis(const T *__restrict__ basis, const double *s, int k,
-                                                                 int64_t n, double *__restrict__ x) {
+__global__ void __launch_bounds__(kRedThreads) k_ritz_from_basis(const T *__restrict__ basis, const double *s,
+                                                                 const double *beta, int k, int64_t n,
+                                                                 double *__restrict__ x) {
     __shared__ float sh[1024], sl[1024];
     __shared__ double sd[1024];
     constexpr int V = Pack<T>::N;
@@ -275,7 +272,7 @@ __global__ void __launch_bounds__(kRedThreads) k_ritz_from_basis(const T *__rest
         const int jn = min(1024, k - j0);
         __syncthreads();
         for (int j = threadIdx.x; j < jn; j += blockDim.x) {
-            const double v = s[j0 + j];
+            const double v = s[j0 + j] / lz_gamma(beta, j0 + j);
             sd[j] = v;
             sh[j] = (float)v;
             sl[j] = (float)(v - (double)(float)v);
@@ -332,11 +329,11 @@ __global__ void __launch_bounds__(kRedThreads) k_ritz_from_basis(const T *__rest
     }
 }
 
-// x += s_j v (second pass, one step at a time); FP32 values enter exactly
+// x += (s_j / g_j) u_j (second pass, one step at a time); FP32 values enter exactly
 template <typename T>
-__global__ void __launch_bounds__(kRedThreads) k_ritz_accum(const T *__restrict__ v, const double *s, int j, int64_t n,
-                                                            double *__restrict__ x) {
-    const double sj = s[j];
+__global__ void __launch_bounds__(kRedThreads) k_ritz_accum(const T *__restrict__ v, const double *s, const double *beta,
+                                                            int j, int64_t n, double *__restrict__ x) {
+    const double sj = s[j] / lz_gamma(beta, j);
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
         x[i] = fma(sj, (double)v[i], j ? x[i] : 0.0);
 }
@@ -415,10 +412,11 @@ static int grow(DevBuf &b, size_t bytes) {
 
 template <typename T>
 static int lz_step(Lz &z, int phase, bool pass2, cudaEvent_t *ev4, bool want_ritz) {
-    // buffers: v_k in B[phase], v_{k-1} in B[1 - phase], w = H v_k in B[2];
-    // v_{k+1} overwrites v_{k-1}, so the next step uses phase 1 - phase
+    // three rotating buffers: u_k in B[phase], u_{k-1} in B[phase + 2],
+    // w (then u_{k+1}) in B[phase + 1] (indices mod 3), which held u_{k-2};
+    // the next step uses phase + 1
     const int64_t n = z.n;
-    T *v = z.buf[phase].as<T>(), *vprev = z.buf[1 - phase].as<T>(), *w = z.buf[2].as<T>();
+    T *v = z.buf[phase].as<T>(), *vprev = z.buf[(phase + 2) % 3].as<T>(), *w = z.buf[(phase + 1) % 3].as<T>();
     LzState *st = z.state.as<LzState>();
     double *part = z.part.as<double>();
     int64_t nk = 0;
@@ -438,7 +436,10 @@ static int lz_step(Lz &z, int phase, bool pass2, cudaEvent_t *ev4, bool want_rit
         k_finalize<<<1, kRedThreads, 0, z.st>>>(st, z.alpha.as<double>(), z.beta.as<double>(), part, nparts, 0, z.iters);
         ++nk;
     }
-    k_step2<T><<<z.grid, kRedThreads, 0, z.st>>>(st, z.alpha.as<double>(), v, w, n, part, (pass2 || z.reorth) ? 0 : 1);
+    // with re-orthogonalisation the basis slot is written after it
+    T *slot_basis = (z.store && !pass2 && !z.reorth) ? z.basis.as<T>() : nullptr;
+    k_step2<T><<<z.grid, kRedThreads, 0, z.st>>>(st, z.alpha.as<double>(), z.beta.as<double>(), v, w, slot_basis, n, part,
+                                                (pass2 || z.reorth) ? 0 : 1);
     ++nk;
     if (z.reorth && !pass2) {
         T *basis = z.basis.as<T>();
@@ -446,8 +447,8 @@ static int lz_step(Lz &z, int phase, bool pass2, cudaEvent_t *ev4, bool want_rit
         for (int pass = 0; pass < 2; ++pass) {
             dim3 g(gj, z.iters);
             k_multidot<T><<<g, kRedThreads, 0, z.st>>>(st, basis, w, n, part);
-            k_multidot_fin<<<z.iters, kRedThreads, 0, z.st>>>(st, part, gj, z.coef.as<double>());
-            k_multiaxpy<T><<<z.grid, kRedThreads, 0, z.st>>>(st, basis, z.coef.as<double>(), w, n);
+            k_multidot_fin<<<z.iters, kRedThreads, 0, z.st>>>(st, z.beta.as<double>(), part, gj, z.coef.as<double>());
+            k_multiaxpy<T><<<z.grid, kRedThreads, 0, z.st>>>(st, basis, z.coef.as<double>(), w, n, pass == 1);
             nk += 3;
         }
         k_norm2<T><<<z.grid, kRedThreads, 0, z.st>>>(st, w, n, part);
@@ -468,9 +469,8 @@ static int lz_step(Lz &z, int phase, bool pass2, cudaEvent_t *ev4, bool want_rit
         k_copy_ritz<<<1, 32, 0, z.st>>>(st, z.tri.as<double>(), z.ritz_tmp.as<double>());
         nk += 2;
     }
-    k_step3<T><<<z.grid, kRedThreads, 0, z.st>>>(st, z.beta.as<double>(), w, vprev, (z.store && !pass2) ? z.basis.as<T>() : nullptr, n);
     k_advance<<<1, 32, 0, z.st>>>(st);
-    nk += 2;
+    nk += 1;
     count_launches(nk);
     GBR_LAUNCH_CHECK();
     return GBR_OK;
@@ -500,8 +500,8 @@ static int lz_run(Lz &z, const double *d_v0, gbr_lanczos_result *res, const gbr_
     // graph mode: one graph per buffer phase, captured on a private stream
     // after two eager steps (which also set kernel attributes), replayed on s
     const bool graphs = o->use_graph && !o->profile;
-    cudaGraphExec_t gexec[2] = {nullptr, nullptr};
-    int64_t gnodes[2] = {0, 0};
+    cudaGraphExec_t gexec[3] = {nullptr, nullptr, nullptr};
+    int64_t gnodes[3] = {0, 0, 0};
     cudaStream_t cap = nullptr;
     if (graphs) GBR_CUDA_TRY(cudaStreamCreateWithFlags(&cap, cudaStreamNonBlocking));
     int rc = GBR_OK;
@@ -542,7 +542,7 @@ static int lz_run(Lz &z, const double *d_v0, gbr_lanczos_result *res, const gbr_
             rc = lz_step<T>(z, phase, false, ev4, want_ritz);
             if (rc) break;
         }
-        phase = 1 - phase;
+        phase = (phase + 1) % 3;
         if ((k & 31) == 31) {
             LzState hs;
             cudaError_t ce = cudaMemcpyAsync(&hs, z.state.p, sizeof(hs), cudaMemcpyDeviceToHost, s);
@@ -551,7 +551,7 @@ static int lz_run(Lz &z, const double *d_v0, gbr_lanczos_result *res, const gbr_
             if (hs.stop) break;
         }
     }
-    for (int p = 0; p < 2; ++p)
+    for (int p = 0; p < 3; ++p)
         if (gexec[p]) cudaGraphExecDestroy(gexec[p]);
     if (cap) cudaStreamDestroy(cap);
     if (rc) return rc;
@@ -582,7 +582,8 @@ static int lz_run(Lz &z, const double *d_v0, gbr_lanczos_result *res, const gbr_
         if ((rc = grow(hx, (size_t)n * 8))) return rc;
         double *sv = z.svec.as<double>();
         if (z.store) {
-            k_ritz_from_basis<T><<<z.grid, kRedThreads, 0, s>>>(z.basis.as<T>(), sv, kdone, n, x.as<double>());
+            k_ritz_from_basis<T><<<z.grid, kRedThreads, 0, s>>>(z.basis.as<T>(), sv, z.beta.as<double>(), kdone, n,
+                                                                x.as<double>());
             count_launches(1);
         } else {
             // second pass of the same recurrence with the stored scalars
@@ -596,13 +597,13 @@ static int lz_run(Lz &z, const double *d_v0, gbr_lanczos_result *res, const gbr_
             int ph = 0;
             for (int j = 0; j < kdone; ++j) {
                 T *v = z.buf[ph].as<T>();
-                k_ritz_accum<T><<<z.grid, kRedThreads, 0, s>>>(v, sv, j, n, x.as<double>());
+                k_ritz_accum<T><<<z.grid, kRedThreads, 0, s>>>(v, sv, z.beta.as<double>(), j, n, x.as<double>());
                 count_launches(1);
                 if (j + 1 < kdone) {
                     rc = lz_step<T>(z, ph, true, nullptr, false);
                     if (rc) return rc;
                 }
-                ph = 1 - ph;
+                ph = (ph + 1) % 3;
             }
         }
         GBR_LAUNCH_CHECK();

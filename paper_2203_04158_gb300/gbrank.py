@@ -84,6 +84,7 @@ def lib():
                 "gbr_ham_destroy": (None, [vp]),
                 "gbr_ham_info": (i32, [vp, vp, vp]),
                 "gbr_ham_set_path": (i32, [vp, i32]),
+                "gbr_ham_get_path": (i32, [vp, C.POINTER(i32)]),
                 "gbr_hv": (i32, [vp, vp, vp, i32, vp]),
                 "gbr_ham_tune": (i32, [vp, i32, vp]),
                 "gbr_hv_stage": (i32, [vp, vp, vp, i32, i32, vp]),
@@ -290,6 +291,12 @@ def gbr_ham_info(H: Ham):
 
 def gbr_ham_set_path(H: Ham, path: int):
     _check(lib().gbr_ham_set_path(H, path))
+
+
+def gbr_ham_get_path(H: Ham) -> int:
+    p = C.c_int(0)
+    _check(lib().gbr_ham_get_path(H, C.byref(p)))
+    return p.value
 
 
 def gbr_ham_tune(H: Ham, fp: int = 32, stream=None):

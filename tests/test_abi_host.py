@@ -42,6 +42,14 @@ def test_library_exports_every_declared_symbol(G):
     assert G.gbr_version() == 1
 
 
+def test_null_handles_are_rejected_on_the_host(G):
+    lib = C.CDLL(G.gbrank.LIB_PATH)
+    path = C.c_int(-1)
+    assert lib.gbr_ham_get_path(None, C.byref(path)) == G.GBR_EINVAL and path.value == -1
+    assert lib.gbr_ham_set_path(None, 0) == G.GBR_EINVAL
+    assert lib.gbr_ham_info(None, None, None) == G.GBR_EINVAL
+
+
 def test_host_argument_errors(G):
     with pytest.raises(G.GbrError) as e:
         G.gbr_comb_create(65, 3, 8)

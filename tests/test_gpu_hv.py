@@ -85,8 +85,10 @@ def test_hv_tuned_shapes_keep_parity(G):
     H = G.gbr_ham_create(L, h, U, Nu, Nd)
     x = S.start_vector(oracle.sector_dim(L, Nu, Nd))
     y_ref = oracle.hv(L, h, U, Nu, Nd, x)
+    assert G.gbr_ham_get_path(H) == G.GBR_HV_AUTO
     for fp in (32, 64):
         G.gbr_ham_tune(H, fp)
+    assert G.gbr_ham_get_path(H) in (G.GBR_HV_FUSED, G.GBR_HV_FACTORED)
     x64 = torch.from_numpy(x).cuda()
     y64 = torch.empty_like(x64)
     G.gbr_hv(H, x64, y64)
