@@ -35,8 +35,9 @@ template <> struct DotAcc<float> {
     __device__ __forceinline__ double value() const { return (double)s.hi + (double)s.lo; }
 };
 
+template <int MAXT = kRedThreads>
 __device__ __forceinline__ double block_sum(double v) {
-    __shared__ double red[kRedThreads / 32];
+    __shared__ double red[MAXT / 32];
     for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xFFFFFFFFu, v, o);
     const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
     __syncthreads();

@@ -40,11 +40,12 @@ struct HamK {
 // Fused first update of a Lanczos step on the unnormalised vectors
 // u_j = g_j v_j (g_0 = 1, g_j = beta_j), done in the epilogue of the spin-up
 // pass: w = H u_k / g_k - (beta_k / g_{k-1}) u_{k-1} (k read from device
-// memory; w = H u_0 when k == 0) and per-CTA partial sums of <w, u_k> (part
-// may be NULL).
+// memory) and per-CTA partial sums of <w, u_k> (part may be NULL).  The two
+// factors are precomputed: scal[4k] = 1/g_k, scal[4k+1] = beta_k / g_{k-1}
+// (0 at k = 0).
 struct LzHook {
     const void *vprev;
-    const double *beta;
+    const double *scal;
     const int *kstate;
     double *part;
 };
@@ -72,7 +73,7 @@ struct gbr_ham {
     // H·v at a time per handle
     gbr::DevBuf ws_xt, ws_zt;
     // Lanczos work buffers, kept between calls and grown when needed
-    gbr::DevBuf lz_state, lz_alpha, lz_beta, lz_part, lz_coef, lz_tri, lz_svec, lz_work, lz_ritz;
+    gbr::DevBuf lz_state, lz_alpha, lz_beta, lz_scal, lz_part, lz_coef, lz_tri, lz_svec, lz_work, lz_ritz;
     gbr::DevBuf lz_buf[3], lz_basis, lz_x, lz_hx;
 };
 

@@ -148,6 +148,11 @@ template <typename T> struct Vec;
 template <> struct Vec<float> { typedef float4 v4; typedef float2 v2; };
 template <> struct Vec<double> { typedef double2 v2; typedef double2 v4; };
 
+__device__ __forceinline__ void unpack16(const float4 &p, float *o) { o[0] = p.x; o[1] = p.y; o[2] = p.z; o[3] = p.w; }
+__device__ __forceinline__ void unpack16(const double2 &p, double *o) { o[0] = p.x; o[1] = p.y; }
+__device__ __forceinline__ float4 pack16(const float *o) { return make_float4(o[0], o[1], o[2], o[3]); }
+__device__ __forceinline__ double2 pack16(const double *o) { return make_double2(o[0], o[1]); }
+
 template <typename T>
 __device__ __forceinline__ T diag_value(const HamK &hk, const T *dup, const T *ddn, const T *uval, int64_t ru,
                                         int64_t rd, uint32_t au, uint32_t ad) {
@@ -253,6 +258,48 @@ __global__ void __launch_bounds__(TILE * 4) k_transpose(const T *__restrict__ in
     }
 }
 
+// The same transpose with 16-byte packs on both sides: a 64 x 64 tile is
+// read as row packs and written as packs of V consecutive elements of one
+// output row (V = 4 FP32, 2 FP64).  Needs cols and rows multiples of V and
+// 16-byte aligned vectors; partial edge tiles fall back to single elements.
+template <typename T>
+__global__ void __launch_bounds__(256) k_transpose16(const T *__restrict__ in, T *__restrict__ out, int64_t rows,
+                                                     int64_t cols) {
+    constexpr int TILE = 64, V = 16 / (int)sizeof(T), RP = TILE / V, PAD = 1;
+    typedef typename Vec<T>::v4 P16;
+    __shared__ T tile[TILE][TILE + PAD];
+    const int64_t c0 = (int64_t)blockIdx.x * TILE, r0 = (int64_t)blockIdx.y * TILE;
+    const bool full = r0 + TILE <= rows && c0 + TILE <= cols;
+    for (int idx = threadIdx.x; idx < TILE * RP; idx += blockDim.x) {
+        const int i = idx / RP, j = idx % RP;
+        const int64_t r = r0 + i, c = c0 + (int64_t)j * V;
+        T o[V];
+        if (full) {
+            unpack16(__ldcs(reinterpret_cast<const P16 *>(in + r * cols + c)), o);
+        } else {
+#pragma unroll
+            for (int e = 0; e < V; ++e) o[e] = (r < rows && c + e < cols) ? __ldcs(in + r * cols + c + e) : T(0);
+        }
+#pragma unroll
+        for (int e = 0; e < V; ++e) tile[i][j * V + e] = o[e];
+    }
+    __syncthreads();
+    for (int idx = threadIdx.x; idx < TILE * RP; idx += blockDim.x) {
+        const int c = idx / RP, j = idx % RP;
+        T o[V];
+#pragma unroll
+        for (int e = 0; e < V; ++e) o[e] = tile[j * V + e][c];
+        const int64_t oc = c0 + c, orow = r0 + (int64_t)j * V;
+        if (full) {
+            *reinterpret_cast<P16 *>(out + oc * rows + orow) = pack16(o);
+        } else if (oc < cols) {
+#pragma unroll
+            for (int e = 0; e < V; ++e)
+                if (orow + e < rows) out[oc * rows + orow + e] = o[e];
+        }
+    }
+}
+
 struct CombineArgs {
     const uint32_t *st_up, *st_dn;   // per-spin patterns (row and column states)
     const void *dup, *ddn, *uval;     // per-spin diagonals, U class values (precision T)
@@ -319,10 +366,8 @@ __global__ void __launch_bounds__(128) k_gather(const int64_t Drows, const int64
     T slz = T(1), blz = T(0);
     if (LZ) {
         klz = *ca.lz.kstate;
-        if (klz > 0) {
-            slz = (T)(1.0 / ca.lz.beta[klz]);
-            blz = (T)(ca.lz.beta[klz] / (klz > 1 ? ca.lz.beta[klz - 1] : 1.0));
-        }
+        slz = (T)ca.lz.scal[4 * klz];
+        blz = (T)ca.lz.scal[4 * klz + 1];
     }
     // combine epilogue: column states and diagonals of this thread's columns
     uint32_t ad[VEC];
@@ -521,7 +566,9 @@ static void gather_shape(const gbr_ham *H, int64_t Drows, int64_t Dcols, bool al
     for (int v = vmax; v >= 2; v /= 2)
         if (aligned16 && Dcols % v == 0 && (double)Drows * 128 * v * sizeof(T) <= 64e6) { vec = v; break; }
     const int tuned = combine ? H->tune_up_rows[fpi] : H->tune_dn_rows[fpi];
-    const int tr_req = tuned ? tuned : 8;
+    // untuned default: 4 rows for the FP32 combine pass (its registers limit
+    // occupancy; the tuner's pick on the 4x4 sector), 8 otherwise
+    const int tr_req = tuned ? tuned : ((combine && vec == 4) ? 4 : 8);
     *vec_out = vec;
     *tr_out = (tr_req == 4 || tr_req == 16) ? tr_req : 8;
 }
@@ -571,10 +618,12 @@ static int stage_transpose(const gbr_ham *H, const T *x, cudaStream_t st, const 
     }
     T *xt = ws ? (T *)ws->xt : H->ws_xt.as<T>();
     const int64_t Dup = H->up.D, Ddn = H->dn.D;
-    constexpr int TILE = 64;
+    constexpr int TILE = 64, V = 16 / (int)sizeof(T);
     dim3 grid((unsigned)((Ddn + TILE - 1) / TILE), (unsigned)((Dup + TILE - 1) / TILE));
     if (grid.y > 65535) return set_error(GBR_EINVAL, "sector too large for the transpose grid");
-    k_transpose<T, TILE><<<grid, dim3(TILE, 4), 0, st>>>(x, xt, Dup, Ddn);
+    const bool packs = ((((uintptr_t)x) | ((uintptr_t)xt)) & 15u) == 0 && Dup % V == 0 && Ddn % V == 0;
+    if (packs) k_transpose16<T><<<grid, 256, 0, st>>>(x, xt, Dup, Ddn);
+    else k_transpose<T, TILE><<<grid, dim3(TILE, 4), 0, st>>>(x, xt, Dup, Ddn);
     GBR_LAUNCH_CHECK();
     count_launches(1);
     return GBR_OK;

@@ -46,19 +46,23 @@ template <typename T> struct alignas(16) Pack {
     T e[N];
 };
 
-// norm g_j of the unnormalised vector u_j (g_0 = 1, g_j = beta_j)
-__device__ __forceinline__ double lz_gamma(const double *beta, int j) { return j > 0 ? beta[j] : 1.0; }
+// Per-step scalars of the unnormalised recurrence, 4 doubles per step j,
+// written once by the single-thread finalisation (so the vector kernels only
+// load them; FP64 division is slow on this GPU) and kept for the second
+// pass: [4j] = 1/g_j, [4j+1] = beta_j / g_{j-1} (0 at j = 0),
+// [4j+2] = alpha_j / g_j, where g_0 = 1 and g_j = beta_j.
+constexpr int kScal = 4;
 
 // w = H u_k / g_k - (beta_k / g_{k-1}) u_{k-1} (k > 0; w = H u_0 at k = 0),
 // with H u_k in w on entry; partial <w, u_k>
 template <typename T>
-__global__ void __launch_bounds__(kRedThreads) k_step1(const LzState *st, const double *beta, const T *__restrict__ vprev,
+__global__ void __launch_bounds__(kRedThreads) k_step1(const LzState *st, const double *scal, const T *__restrict__ vprev,
                                                        const T *__restrict__ v, T *__restrict__ w, int64_t n, double *part,
                                                        int want_dot) {
     if (st->stop) return;
     const int k = st->k;
-    const T s1 = (T)(1.0 / lz_gamma(beta, k));
-    const T b = k > 0 ? (T)(beta[k] / lz_gamma(beta, k - 1)) : T(0);
+    const T s1 = (T)scal[kScal * k];
+    const T b = (T)scal[kScal * k + 1];
     DotAcc<T> acc;
     constexpr int V = Pack<T>::N;
     const int64_t np = n / V;
@@ -93,12 +97,12 @@ __global__ void __launch_bounds__(kRedThreads) k_step1(const LzState *st, const 
 // w -= (alpha_k / g_k) u_k, which makes w the next unnormalised vector
 // u_{k+1}; partial <w, w>; with a basis, u_{k+1} also into its slot k + 1
 template <typename T>
-__global__ void __launch_bounds__(kRedThreads) k_step2(const LzState *st, const double *alpha, const double *beta,
-                                                       const T *__restrict__ v, T *__restrict__ w, T *__restrict__ basis,
-                                                       int64_t n, double *part, int want_dot) {
+__global__ void __launch_bounds__(kRedThreads) k_step2(const LzState *st, const double *scal, const T *__restrict__ v,
+                                                       T *__restrict__ w, T *__restrict__ basis, int64_t n, double *part,
+                                                       int want_dot) {
     if (st->stop) return;
     const int k = st->k;
-    const T a = (T)(alpha[k] / lz_gamma(beta, k));
+    const T a = (T)scal[kScal * k + 2];
     T *vb = basis ? basis + (int64_t)(k + 1) * n : nullptr;
     DotAcc<T> acc;
     constexpr int V = Pack<T>::N;
@@ -142,22 +146,39 @@ __global__ void __launch_bounds__(kRedThreads) k_norm2(const LzState *st, const 
     if (threadIdx.x == 0) part[blockIdx.x] = r;
 }
 
-// which: 0 = alpha_k = sum; 1 = beta_{k+1} = sqrt(sum) with the stopping test
-__global__ void __launch_bounds__(kRedThreads) k_finalize(LzState *st, double *alpha, double *beta, const double *part,
-                                                          int nparts, int which, int iters) {
+// which: 0 = alpha_k = sum / g_k; 1 = beta_{k+1} = sqrt(sum) with the
+// stopping test; each also stores the scalars the vector kernels need
+constexpr int kFinThreads = 1024;
+
+__global__ void __launch_bounds__(kFinThreads) k_finalize(LzState *st, double *alpha, double *beta, double *scal,
+                                                          const double *part, int nparts, int which, int iters) {
     if (st->stop) return;
-    double v = 0.0;
-    for (int i = threadIdx.x; i < nparts; i += blockDim.x) v += part[i];
-    const double s = block_sum(v);
+    // four independent running sums per thread (fixed order), so the loads
+    // of one thread are not one dependency chain
+    double v0 = 0.0, v1 = 0.0, v2 = 0.0, v3 = 0.0;
+    const int step = 4 * blockDim.x;
+    int i = threadIdx.x;
+    for (; i + 3 * (int)blockDim.x < nparts; i += step) {
+        v0 += part[i];
+        v1 += part[i + blockDim.x];
+        v2 += part[i + 2 * blockDim.x];
+        v3 += part[i + 3 * blockDim.x];
+    }
+    for (; i < nparts; i += blockDim.x) v0 += part[i];
+    const double s = block_sum<kFinThreads>((v0 + v1) + (v2 + v3));
     if (threadIdx.x != 0) return;
     const int k = st->k;
     if (which == 0) {
         // the partials hold <w, u_k> = g_k alpha_k
-        alpha[k] = s / lz_gamma(beta, k);
-        st->scale = fmax(st->scale, fabs(s));
+        const double a = s * scal[kScal * k];
+        alpha[k] = a;
+        scal[kScal * k + 2] = a * scal[kScal * k];
+        st->scale = fmax(st->scale, fabs(a));
     } else {
         const double b = sqrt(fmax(s, 0.0));
         beta[k + 1] = b;
+        scal[kScal * (k + 1)] = 1.0 / b;
+        scal[kScal * (k + 1) + 1] = b * scal[kScal * k];
         if (k + 1 >= iters) {
             st->stop = 1;
         } else if (b <= 1e-13 * st->scale) {
@@ -189,7 +210,7 @@ __global__ void __launch_bounds__(kRedThreads) k_multidot(const LzState *st, con
     if (threadIdx.x == 0) part[(int64_t)j * gridDim.x + blockIdx.x] = r;
 }
 
-__global__ void __launch_bounds__(kRedThreads) k_multidot_fin(const LzState *st, const double *beta, const double *part,
+__global__ void __launch_bounds__(kRedThreads) k_multidot_fin(const LzState *st, const double *scal, const double *part,
                                                               int nparts, double *c) {
     if (st->stop) return;
     const int j = blockIdx.x;
@@ -197,8 +218,8 @@ __global__ void __launch_bounds__(kRedThreads) k_multidot_fin(const LzState *st,
     double v = 0.0;
     for (int i = threadIdx.x; i < nparts; i += blockDim.x) v += part[(int64_t)j * nparts + i];
     const double s = block_sum(v);
-    const double g = lz_gamma(beta, j);
-    if (threadIdx.x == 0) c[j] = s / (g * g);
+    const double ig = scal[kScal * j];
+    if (threadIdx.x == 0) c[j] = s * ig * ig;
 }
 
 // w -= sum_j c_j u_j; the last pass also writes the result into slot k + 1
@@ -260,7 +281,7 @@ __global__ void k_copy_ritz(const LzState *st, const double *val, double *ritz) 
 // serves several elements.
 template <typename T>
 __global__ void __launch_bounds__(kRedThreads) k_ritz_from_basis(const T *__restrict__ basis, const double *s,
-                                                                 const double *beta, int k, int64_t n,
+                                                                 const double *scal, int k, int64_t n,
                                                                  double *__restrict__ x) {
     __shared__ float sh[1024], sl[1024];
     __shared__ double sd[1024];
@@ -272,7 +293,7 @@ __global__ void __launch_bounds__(kRedThreads) k_ritz_from_basis(const T *__rest
         const int jn = min(1024, k - j0);
         __syncthreads();
         for (int j = threadIdx.x; j < jn; j += blockDim.x) {
-            const double v = s[j0 + j] / lz_gamma(beta, j0 + j);
+            const double v = s[j0 + j] * scal[kScal * (j0 + j)];
             sd[j] = v;
             sh[j] = (float)v;
             sl[j] = (float)(v - (double)(float)v);
@@ -331,9 +352,9 @@ __global__ void __launch_bounds__(kRedThreads) k_ritz_from_basis(const T *__rest
 
 // x += (s_j / g_j) u_j (second pass, one step at a time); FP32 values enter exactly
 template <typename T>
-__global__ void __launch_bounds__(kRedThreads) k_ritz_accum(const T *__restrict__ v, const double *s, const double *beta,
+__global__ void __launch_bounds__(kRedThreads) k_ritz_accum(const T *__restrict__ v, const double *s, const double *scal,
                                                             int j, int64_t n, double *__restrict__ x) {
-    const double sj = s[j] / lz_gamma(beta, j);
+    const double sj = s[j] * scal[kScal * j];
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
         x[i] = fma(sj, (double)v[i], j ? x[i] : 0.0);
 }
@@ -394,12 +415,13 @@ struct Lz {
     double tol = 0.0;
     cudaStream_t st;
     // work buffers live in the handle (kept between calls)
-    DevBuf &state, &alpha, &beta, &part, &coef, &tri, &svec, &work, &ritz_tmp;
+    DevBuf &state, &alpha, &beta, &scal, &part, &coef, &tri, &svec, &work, &ritz_tmp;
     DevBuf *buf;
     DevBuf &basis, &x, &hx;
     std::vector<cudaEvent_t> evs;   // profile: 5 events per H·v (stage boundaries)
     explicit Lz(gbr_ham *h)
-        : H(h), state(h->lz_state), alpha(h->lz_alpha), beta(h->lz_beta), part(h->lz_part), coef(h->lz_coef),
+        : H(h), state(h->lz_state), alpha(h->lz_alpha), beta(h->lz_beta), scal(h->lz_scal), part(h->lz_part),
+          coef(h->lz_coef),
           tri(h->lz_tri), svec(h->lz_svec), work(h->lz_work), ritz_tmp(h->lz_ritz), buf(h->lz_buf),
           basis(h->lz_basis), x(h->lz_x), hx(h->lz_hx) {}
 };
@@ -423,22 +445,23 @@ static int lz_step(Lz &z, int phase, bool pass2, cudaEvent_t *ev4, bool want_rit
     int nparts = z.grid;
     if (hv_is_factored(z.H)) {
         // w = H v - beta_k v_{k-1} and the partials of <w, v> in the H·v epilogue
-        const LzHook hook{vprev, z.beta.as<double>(), &st->k, pass2 ? nullptr : part};
+        const LzHook hook{vprev, z.scal.as<double>(), &st->k, pass2 ? nullptr : part};
         int rc = hv_launch_lz(z.H, v, w, z.fp, z.st, ev4, hook, &nparts);
         if (rc) return rc;
     } else {
         int rc = hv_launch(z.H, v, w, z.fp, z.st, ev4);
         if (rc) return rc;
-        k_step1<T><<<z.grid, kRedThreads, 0, z.st>>>(st, z.beta.as<double>(), vprev, v, w, n, part, pass2 ? 0 : 1);
+        k_step1<T><<<z.grid, kRedThreads, 0, z.st>>>(st, z.scal.as<double>(), vprev, v, w, n, part, pass2 ? 0 : 1);
         ++nk;
     }
     if (!pass2) {
-        k_finalize<<<1, kRedThreads, 0, z.st>>>(st, z.alpha.as<double>(), z.beta.as<double>(), part, nparts, 0, z.iters);
+        k_finalize<<<1, kFinThreads, 0, z.st>>>(st, z.alpha.as<double>(), z.beta.as<double>(), z.scal.as<double>(), part,
+                                                nparts, 0, z.iters);
         ++nk;
     }
     // with re-orthogonalisation the basis slot is written after it
     T *slot_basis = (z.store && !pass2 && !z.reorth) ? z.basis.as<T>() : nullptr;
-    k_step2<T><<<z.grid, kRedThreads, 0, z.st>>>(st, z.alpha.as<double>(), z.beta.as<double>(), v, w, slot_basis, n, part,
+    k_step2<T><<<z.grid, kRedThreads, 0, z.st>>>(st, z.scal.as<double>(), v, w, slot_basis, n, part,
                                                 (pass2 || z.reorth) ? 0 : 1);
     ++nk;
     if (z.reorth && !pass2) {
@@ -447,7 +470,7 @@ static int lz_step(Lz &z, int phase, bool pass2, cudaEvent_t *ev4, bool want_rit
         for (int pass = 0; pass < 2; ++pass) {
             dim3 g(gj, z.iters);
             k_multidot<T><<<g, kRedThreads, 0, z.st>>>(st, basis, w, n, part);
-            k_multidot_fin<<<z.iters, kRedThreads, 0, z.st>>>(st, z.beta.as<double>(), part, gj, z.coef.as<double>());
+            k_multidot_fin<<<z.iters, kRedThreads, 0, z.st>>>(st, z.scal.as<double>(), part, gj, z.coef.as<double>());
             k_multiaxpy<T><<<z.grid, kRedThreads, 0, z.st>>>(st, basis, z.coef.as<double>(), w, n, pass == 1);
             nk += 3;
         }
@@ -455,7 +478,8 @@ static int lz_step(Lz &z, int phase, bool pass2, cudaEvent_t *ev4, bool want_rit
         ++nk;
     }
     if (!pass2) {
-        k_finalize<<<1, kRedThreads, 0, z.st>>>(st, z.alpha.as<double>(), z.beta.as<double>(), part, z.grid, 1, z.iters);
+        k_finalize<<<1, kFinThreads, 0, z.st>>>(st, z.alpha.as<double>(), z.beta.as<double>(), z.scal.as<double>(), part,
+                                                z.grid, 1, z.iters);
         ++nk;
     }
     if (z.tol > 0.0 && !pass2) {
@@ -485,6 +509,9 @@ static int lz_run(Lz &z, const double *d_v0, gbr_lanczos_result *res, const gbr_
     GBR_CUDA_TRY(cudaMemcpyAsync(z.state.p, &zero, sizeof(zero), cudaMemcpyHostToDevice, s));
     GBR_CUDA_TRY(cudaMemsetAsync(z.beta.p, 0, sizeof(double) * (size_t)(z.iters + 2), s));
     GBR_CUDA_TRY(cudaMemsetAsync(z.alpha.p, 0, sizeof(double) * (size_t)(z.iters + 2), s));
+    GBR_CUDA_TRY(cudaMemsetAsync(z.scal.p, 0, sizeof(double) * kScal * (size_t)(z.iters + 2), s));
+    static const double scal0 = 1.0;   // 1/g_0
+    GBR_CUDA_TRY(cudaMemcpyAsync(z.scal.p, &scal0, sizeof(double), cudaMemcpyHostToDevice, s));
     T *B0 = z.buf[0].as<T>();
     k_cast_start<T><<<z.grid, kRedThreads, 0, s>>>(d_v0, B0, n);
     k_norm2<T><<<z.grid, kRedThreads, 0, s>>>(z.state.as<LzState>(), B0, n, z.part.as<double>());
@@ -582,7 +609,7 @@ static int lz_run(Lz &z, const double *d_v0, gbr_lanczos_result *res, const gbr_
         if ((rc = grow(hx, (size_t)n * 8))) return rc;
         double *sv = z.svec.as<double>();
         if (z.store) {
-            k_ritz_from_basis<T><<<z.grid, kRedThreads, 0, s>>>(z.basis.as<T>(), sv, z.beta.as<double>(), kdone, n,
+            k_ritz_from_basis<T><<<z.grid, kRedThreads, 0, s>>>(z.basis.as<T>(), sv, z.scal.as<double>(), kdone, n,
                                                                 x.as<double>());
             count_launches(1);
         } else {
@@ -597,7 +624,7 @@ static int lz_run(Lz &z, const double *d_v0, gbr_lanczos_result *res, const gbr_
             int ph = 0;
             for (int j = 0; j < kdone; ++j) {
                 T *v = z.buf[ph].as<T>();
-                k_ritz_accum<T><<<z.grid, kRedThreads, 0, s>>>(v, sv, z.beta.as<double>(), j, n, x.as<double>());
+                k_ritz_accum<T><<<z.grid, kRedThreads, 0, s>>>(v, sv, z.scal.as<double>(), j, n, x.as<double>());
                 count_launches(1);
                 if (j + 1 < kdone) {
                     rc = lz_step<T>(z, ph, true, nullptr, false);
@@ -697,6 +724,7 @@ extern "C" int gbr_lanczos(const gbr_ham *H, const gbr_lanczos_opts *o, const do
     if ((rc = grow(z.state, sizeof(LzState)))) return rc;
     if ((rc = grow(z.alpha, sizeof(double) * (size_t)(z.iters + 2)))) return rc;
     if ((rc = grow(z.beta, sizeof(double) * (size_t)(z.iters + 2)))) return rc;
+    if ((rc = grow(z.scal, sizeof(double) * kScal * (size_t)(z.iters + 2)))) return rc;
     size_t nparts = (size_t)z.grid * (size_t)(z.reorth ? z.iters + 1 : 1);
     nparts = std::max(nparts, (size_t)hv_lz_parts(H, z.fp));
     if ((rc = grow(z.part, sizeof(double) * nparts))) return rc;
