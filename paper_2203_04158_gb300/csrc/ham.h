@@ -69,6 +69,7 @@ struct gbr_ham {
     // tuned launch shape (0 = default): rows per CTA of the gather passes
     int tune_up_rows[2] = {0, 0};
     int tune_dn_rows[2] = {0, 0};
+    int tune_lz_rows[2] = {0, 0};   // the spin-up pass with the fused Lanczos update
     // scratch of the factored path (X^T and Z^T), grown on first use; one
     // H·v at a time per handle
     gbr::DevBuf ws_xt, ws_zt;

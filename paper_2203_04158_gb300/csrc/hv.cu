@@ -313,8 +313,12 @@ struct CombineArgs {
 // u_j = g_j v_j (g_0 = 1, g_j = beta_j) in the same epilogue,
 // w = y / g_k - (beta_k / g_{k-1}) u_{k-1} (k > 0; x = u_k) and the block's
 // partial <w, x>.
+// The FP32 combine passes are held to 10 CTAs per SM (48 registers): left
+// free the compiler takes up to 60 registers and the occupancy drops; at 12
+// or 16 CTAs it spills.  Measured on the 4x4 sector: 1.16 ms (10) against
+// 1.21 ms (free) and 1.25 ms (16).
 template <typename T, int VEC, int MODE, int TR>
-__global__ void __launch_bounds__(128) k_gather(const int64_t Drows, const int64_t Dcols, const int hmax,
+__global__ void __launch_bounds__(128, ((MODE >= 1 && sizeof(T) == 4) ? 10 : 1)) k_gather(const int64_t Drows, const int64_t Dcols, const int hmax,
                                                 const int64_t nrb, const uint16_t *__restrict__ cnt,
                                                 const uint32_t *__restrict__ tgt, const uint16_t *__restrict__ bond,
                                                 const T *__restrict__ bcoef, const int uniform, const T hu,
@@ -328,9 +332,13 @@ __global__ void __launch_bounds__(128) k_gather(const int64_t Drows, const int64
     uint32_t *st = reinterpret_cast<uint32_t *>(smr);
     T *sc = reinterpret_cast<T *>(smr + (((size_t)TR * hmax * 4 + 15) & ~(size_t)15));
     __shared__ int scnt[64];
+    // U class values (combine), in shared memory to keep registers for occupancy
+    __shared__ T suv[kMaxUClasses];
     const int64_t rb = blockIdx.x % nrb, cc = blockIdx.x / nrb;
     const int64_t r0 = rb * TR;
     for (int i = threadIdx.x; i < TR; i += blockDim.x) scnt[i] = (r0 + i < Drows) ? (int)cnt[r0 + i] : 0;
+    if (COMBINE && threadIdx.x < kMaxUClasses)
+        suv[threadIdx.x] = threadIdx.x < ca.hk.nucls ? ((const T *)ca.uval)[threadIdx.x] : T(0);
     __syncthreads();
     for (int e = threadIdx.x; e < TR * hmax; e += blockDim.x) {
         const int i = e % TR, k = e / TR;
@@ -372,7 +380,6 @@ __global__ void __launch_bounds__(128) k_gather(const int64_t Drows, const int64
     // combine epilogue: column states and diagonals of this thread's columns
     uint32_t ad[VEC];
     T dd[VEC];
-    T uval[kMaxUClasses];
     if (COMBINE && active) {
         const T *ddn = (const T *)ca.ddn;
 #pragma unroll
@@ -380,8 +387,6 @@ __global__ void __launch_bounds__(128) k_gather(const int64_t Drows, const int64
             ad[v] = ca.st_dn[c0 + v];
             dd[v] = ddn[c0 + v];
         }
-#pragma unroll
-        for (int u = 0; u < kMaxUClasses; ++u) uval[u] = u < ca.hk.nucls ? ((const T *)ca.uval)[u] : T(0);
     }
     for (int i = 0; i < TR && active; ++i) {
         const int64_t r = r0 + i;
@@ -440,12 +445,12 @@ __global__ void __launch_bounds__(128) k_gather(const int64_t Drows, const int64
             for (int v = 0; v < VEC; ++v) {
                 const uint32_t both = au & ad[v];
                 T dg = du + dd[v];
-                // unrolled (uval stays in registers) with a uniform exit, so
-                // no FP64 work is spent on unused classes
+                // unrolled with a uniform exit, so no FP64 work is spent on
+                // unused classes
 #pragma unroll
                 for (int u = 0; u < kMaxUClasses; ++u) {
                     if (u >= ca.hk.nucls) break;
-                    dg += uval[u] * (T)__popc(both & ca.hk.umask[u]);
+                    dg += suv[u] * (T)__popc(both & ca.hk.umask[u]);
                 }
                 acc[v] += dg * xo[v] + zv[v];
             }
@@ -558,14 +563,14 @@ static int ensure_ws(const gbr_ham *H, size_t bytes) {
 // Vector width and rows per CTA of a gather pass (shared by the launch and
 // the partial-sum sizing of the fused Lanczos epilogue).
 template <typename T>
-static void gather_shape(const gbr_ham *H, int64_t Drows, int64_t Dcols, bool aligned16, bool combine, int *vec_out,
-                         int *tr_out) {
+static void gather_shape(const gbr_ham *H, int64_t Drows, int64_t Dcols, bool aligned16, bool combine, bool lz,
+                         int *vec_out, int *tr_out) {
     const int fpi = sizeof(T) == 8 ? 1 : 0;
     const int vmax = sizeof(T) == 4 ? 4 : 2;
     int vec = 1;
     for (int v = vmax; v >= 2; v /= 2)
         if (aligned16 && Dcols % v == 0 && (double)Drows * 128 * v * sizeof(T) <= 64e6) { vec = v; break; }
-    const int tuned = combine ? H->tune_up_rows[fpi] : H->tune_dn_rows[fpi];
+    const int tuned = lz ? H->tune_lz_rows[fpi] : (combine ? H->tune_up_rows[fpi] : H->tune_dn_rows[fpi]);
     // untuned default: 4 rows for the FP32 combine pass (its registers limit
     // occupancy; the tuner's pick on the 4x4 sector), 8 otherwise
     const int tr_req = tuned ? tuned : ((combine && vec == 4) ? 4 : 8);
@@ -581,7 +586,7 @@ static int launch_gather(const gbr_ham *H, const SpinSector &lists, int64_t Drow
     bool aligned16 = (((uintptr_t)w | (uintptr_t)z) & 15u) == 0;
     if (MODE == 2) aligned16 = aligned16 && (((uintptr_t)ca.lz.vprev) & 15u) == 0;
     int vec = 1, TR = 8;
-    gather_shape<T>(H, Drows, Dcols, aligned16, COMBINE, &vec, &TR);
+    gather_shape<T>(H, Drows, Dcols, aligned16, COMBINE, MODE == 2, &vec, &TR);
     const int64_t nrb = (Drows + TR - 1) / TR;
     const int64_t ncc = (Dcols + 128 * vec - 1) / (128 * vec);
     const int hmax = std::max(1, lists.hmax);
@@ -993,7 +998,8 @@ extern "C" int gbr_hv_stage(const gbr_ham *H, const void *d_x, void *d_y, int fp
 
 // Times the candidate launch shapes on scratch vectors and keeps the fastest
 // in the handle: the path (fused for sectors up to 2^22 states), the rows per
-// CTA of the spin-up pass, and the rows staged per CTA by the spin-down pass.
+// CTA of the spin-up pass, the rows staged per CTA by the spin-down pass, and
+// the rows per CTA of the spin-up pass with the fused Lanczos update.
 extern "C" int gbr_ham_tune(gbr_ham *H, int fp, void *stream) {
     clear_error();
     if (!H) return set_error(GBR_EINVAL, "NULL handle");
@@ -1001,7 +1007,7 @@ extern "C" int gbr_ham_tune(gbr_ham *H, int fp, void *stream) {
     const size_t s = fp == 64 ? 8 : 4;
     const int fpi = fp == 64 ? 1 : 0;
     cudaStream_t st = (cudaStream_t)stream;
-    DevBuf x, y;
+    DevBuf x, y, lz_part, lz_scal, lz_k;
     int rc;
     if ((rc = x.alloc((size_t)H->D * s))) return rc;
     if ((rc = y.alloc((size_t)H->D * s))) return rc;
@@ -1035,6 +1041,41 @@ extern "C" int gbr_ham_tune(gbr_ham *H, int fp, void *stream) {
             if (ms < best || (tr == 8 && ms <= best)) { best = ms; best_tr = tr; }
         }
         *knob = best_tr;
+    }
+    // rows per CTA of the combine pass as the Lanczos launches it (fused
+    // first update, another kernel with its own best tile), timed on that
+    // kernel with a stand-in recurrence state (step 1, v_{k-1} = x)
+    {
+        const int64_t np = hv_lz_parts(H, fp);
+        if ((rc = lz_part.alloc(sizeof(double) * (size_t)np))) goto done;
+        if ((rc = lz_scal.alloc(sizeof(double) * 8))) goto done;
+        if ((rc = lz_k.alloc(sizeof(int)))) goto done;
+        const double scal[8] = {1.0, 0.0, 0.0, 0.0, 0.5, 0.5, 0.0, 0.0};
+        const int k1 = 1;
+        GBR_CUDA_TRY(cudaMemcpyAsync(lz_scal.p, scal, sizeof(scal), cudaMemcpyHostToDevice, st));
+        GBR_CUDA_TRY(cudaMemcpyAsync(lz_k.p, &k1, sizeof(int), cudaMemcpyHostToDevice, st));
+        const LzHook hook{x.p, lz_scal.as<double>(), lz_k.as<int>(), lz_part.as<double>()};
+        auto time_lz = [&](float *ms_out) -> int {
+            int np_out = 0;
+            int r = hv_launch_lz(H, x.p, y.p, fp, st, nullptr, hook, &np_out);
+            if (r) return r;
+            cudaEventRecord(e0, st);
+            for (int i = 0; i < 3; ++i)
+                if ((r = hv_launch_lz(H, x.p, y.p, fp, st, nullptr, hook, &np_out))) return r;
+            cudaEventRecord(e1, st);
+            cudaError_t ce = cudaEventSynchronize(e1);
+            if (ce != cudaSuccess) return set_error(GBR_ECUDA, "tune: %s", cudaGetErrorString(ce));
+            cudaEventElapsedTime(ms_out, e0, e1);
+            return GBR_OK;
+        };
+        float best_lz = 1e30f;
+        int best_tr = 0;
+        for (int tr : {4, 8, 16}) {
+            H->tune_lz_rows[fpi] = tr;
+            if ((rc = time_lz(&ms))) goto done;
+            if (ms < best_lz) { best_lz = ms; best_tr = tr; }
+        }
+        H->tune_lz_rows[fpi] = best_tr;
     }
     if (H->D <= ((int64_t)1 << 22)) {
         H->path = GBR_HV_FUSED;

@@ -93,6 +93,12 @@ def test_hv_tuned_shapes_keep_parity(G):
     y64 = torch.empty_like(x64)
     G.gbr_hv(H, x64, y64)
     assert rel_inf(y64.cpu().numpy(), y_ref) <= TOL64
+    # the tuned tile of the spin-up pass with the fused Lanczos update
+    G.gbr_ham_set_path(H, G.GBR_HV_FACTORED)
+    o = oracle.lanczos(L, h, U, Nu, Nd, x, 40, False)
+    r = G.gbr_lanczos(H, x64, 40, prec=G.GBR_PREC_FP64, refine=False)
+    assert np.max(np.abs(r["alpha"][:20] - o["alpha"][:20])) <= 1e-9
+    assert abs(r["E_ritz"] - o["E0"]) <= 1e-10 * abs(o["E0"])
 
 
 def test_hv_rejects_overlap_and_bad_dtype(G):
