@@ -176,22 +176,77 @@ def oracle_sample(seconds: float):
     return elems / dt, desc, dt
 
 
+def _oracle_rows(job):
+    """One worker's block of rows: (matrix elements, seconds)."""
+    r0, n = job
+    import numpy as np
+    import gbr_synth as S
+    import oracle
+    h, U = model()
+    rows = np.arange(r0, r0 + n, dtype=np.int64)
+    t0 = time.perf_counter()
+    oracle.hv_rows_seeded(L, h, U, NUP, NDN, S.SEED_START, rows)
+    dt = time.perf_counter() - t0
+    return oracle.count_elements(L, h, NUP, NDN, r0, r0 + n), dt
+
+
+class OraclePool:
+    """The oracle's H·v on every host core: disjoint blocks of rows of the
+    sector, one per worker process (started with spawn, so it is safe after
+    CUDA has been initialised)."""
+
+    def __init__(self, workers: int = 0):
+        import multiprocessing as mp
+        self.workers = workers or os.cpu_count() or 1
+        self.pool = mp.get_context("spawn").Pool(self.workers)
+        self.pool.map(_oracle_rows, [(0, 50)] * self.workers)       # import and load in every worker
+        self.rows_per_s = None
+
+    def sample(self, seconds: float):
+        """About ``seconds`` of work per worker; returns (elements/s, description)."""
+        import oracle
+        D = oracle.sector_dim(L, NUP, NDN)
+        if self.rows_per_s is None:
+            n0 = 2000
+            _, dt = _oracle_rows((D // 3, n0))
+            self.rows_per_s = n0 / max(dt, 1e-6)
+        n = max(100, int(self.rows_per_s * seconds))
+        r0 = D // 3
+        jobs = [(r0 + w * n, n) for w in range(self.workers)]
+        if jobs[-1][0] + n > D:
+            raise ValueError("sample larger than the sector")
+        t0 = time.perf_counter()
+        res = self.pool.map(_oracle_rows, jobs)
+        wall = time.perf_counter() - t0
+        elems = sum(e for e, _ in res)
+        desc = (f"rows [{r0}, {r0 + n * self.workers}) of the 4x4 sector in {self.workers} blocks of {n}, one per "
+                f"worker process: {elems} matrix elements by literal operator application (Eq. cee) with bisection "
+                f"ranking, {wall:.1f} s wall")
+        return elems / wall, desc
+
+    def close(self):
+        self.pool.close()
+        self.pool.join()
+
+
 def run_reference(args, rank: int):
     if rank != 0:
         return
     vals, descs = [], []
+    pool = OraclePool()
     for _ in range(args.warmup):
-        oracle_sample(2.0)
+        pool.sample(1.0)
     for _ in range(args.steps):
-        v, d, dt = oracle_sample(args.cpu_seconds / max(1, args.steps))
+        v, d = pool.sample(args.cpu_seconds / max(1, args.steps))
         vals.append(v)
         descs.append(d)
+    pool.close()
     v = statistics.median(vals)
     line = {"metric": METRIC, "value": v, "unit": UNIT, "impl": "reference", "n_gpus": 0, "steps": args.steps,
             "warmup": args.warmup, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
             "dtype": "f64", "data": "synthetic",
             "config": {"workload": WORKLOAD, "dim": math.comb(16, 7) ** 2},
-            "cpu_baseline": {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": descs[-1]},
+            "cpu_baseline": {"value": v, "unit": UNIT, "cores": pool.workers, "kind": "oracle", "sample": descs[-1]},
             "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
 
@@ -303,19 +358,25 @@ def hv_path_extras(G, torch, H, s):
     return out
 
 
+def reference_energies():
+    """Ground-state energies of the extra configurations, stored by
+    tests/golden/make_reference_energies.py (which runs the oracle only)."""
+    return json.load(open(os.path.join(ROOT, "tests", "golden", "reference_energies.json")))
+
+
 def config_extras(G, torch):
     """The other configurations, each solved once (outside the timed steps)."""
     import numpy as np
     import gbr_synth as S
     import gbr_synth.gpu as SG
-    import oracle
+    ref = reference_energies()
     out = {}
     # L=8 ring, U=4, half filling, FP64 with full re-orthogonalisation, combinadics ranking
     h8, U8 = S.chain(8), S.uniform_U(8, 4.0)
     H8 = G.gbr_ham_create(8, h8, U8, 4, 4, G.GBR_RANK_CNS)
     v0 = torch.from_numpy(S.start_vector(4900)).cuda()
     r = G.gbr_lanczos(H8, v0, 100, reorth=True, prec=G.GBR_PREC_FP64, refine=True, use_graph=True)
-    E_dense = oracle.dense_E0(8, h8, U8, 4, 4)
+    E_dense = ref["ring8_U4_N4_4_dense_E0"]
     out["ring8_fp64_reorth"] = {"E0": r["E0"], "E0_dense": E_dense, "rel_err": abs(r["E0"] - E_dense) / abs(E_dense),
                                 "seconds": r["seconds"], "iters": r["iters"]}
     # 256 impurity models, every sector, one persistent launch
@@ -328,14 +389,8 @@ def config_extras(G, torch):
     b = G.gbr_batch_solve(models, st, 150)
     dt = time.perf_counter() - t0
     checks = []
-    for m in (0, 128, 255):
-        h, U = models[m]
-        L = h.shape[0]
-        best = min(oracle.dense_E0(L, h, U, a, c) if oracle.sector_dim(L, a, c) <= 600 else
-                   oracle.lanczos(L, h, U, a, c, S.start_vector(oracle.sector_dim(L, a, c), 77),
-                                  min(160, oracle.sector_dim(L, a, c)), True)["E0"]
-                   for a in range(L + 1) for c in range(L + 1))
-        checks.append(abs(b["E0"][m] - best) / max(1.0, abs(best)))
+    for m, best in ref["siam_lowest_E0"].items():
+        checks.append(abs(b["E0"][int(m)] - best) / max(1.0, abs(best)))
     out["siam256_batch"] = {"models": 256, "sectors": ns, "states": nst, "seconds": dt, "sectors_per_s": ns / dt,
                             "max_rel_err_sampled_models": max(checks)}
     # L=18 ring, U=4, half filling: mixed (150 steps, FP64 refinement) vs all-FP64
@@ -358,12 +413,12 @@ def config_extras(G, torch):
                                                 "fp64_s": rdt["seconds"], "fp64_iters": rdt["iters"],
                                                 "fp64_rel_err": abs(rdt["E0"] - rd["E0"]) / abs(rd["E0"]),
                                                 "speedup": rdt["seconds"] / rmt["seconds"]},
-                                    "E0_free_limit_check": oracle.free_E0(h18, 9, 9)}
+                                    "E0_U0_closed_form": ref["chain18_U0_N9_9_free_E0"]}
     del s18, H18
     torch.cuda.empty_cache()
     # every S_z of the 12-site ring at 12 particles, ranked by a packed trie
     h12, U12 = S.chain(12), S.uniform_U(12, 4.0)
-    st12 = oracle.fixed_N_states(12, 12)
+    st12 = S.fixed_N_states(12, 12)
     Sh = G.gbr_setham_create(12, h12, U12, st12, 8)
     info = G.gbr_setham_info(Sh)
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -415,7 +470,6 @@ def ranking_sweep(G, torch):
     import numpy as np
     import gbr_synth as S
     import gbr_synth.gpu as SG
-    import oracle
     M, n = 28, 1 << 26
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     rows = []
@@ -431,7 +485,7 @@ def ranking_sweep(G, torch):
 
     for N in (1, 2, 5, 9, 14, 19, 23, 26, 27):
         D = math.comb(M, N)
-        members = oracle.enumerate_sector(M, N)
+        members = S.popcount_states(M, N)
         c = G.gbr_comb_create(M, N, 8)
         tr = G.gbr_trie_create(members, M, 8)
         u = SG.bounded(S.SEED_COMB_QUERIES, n, D)
@@ -448,6 +502,69 @@ def ranking_sweep(G, torch):
         del q, qs, u, r, tr, c
         torch.cuda.empty_cache()
     return rows
+
+
+def eig_timings(G, torch):
+    """Analog of the paper's Fig. eig-timings (Sec. V-B): one H·v of the open
+    Hubbard chain of Eq. Hring (t = 1, U = 4) per ranking strategy, as time
+    per state and per spin-orbital (ns), for S_z = 0 at half filling
+    (N = M/2, M = 4..32) and quarter filling (N = M/4, M = 8..32).
+    Strategies: the fused per-element kernel with staggered tables and with
+    combinadics (Fig. algr), the factored path, and per-element ranking of the
+    full 2L-bit pattern over the sector's state set by the trie (R = 8, 4)
+    and by bisection (the baseline)."""
+    import gbr_synth as S
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+
+    def timed(fn, reps):
+        fn()
+        torch.cuda.synchronize()
+        e0.record()
+        for _ in range(reps):
+            fn()
+        e1.record()
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1) / reps / 1e3
+
+    out = {"half": [], "quarter": []}
+    for filling, Ms in (("half", range(4, 33, 4)), ("quarter", (8, 16, 24, 32))):
+        for M in Ms:
+            L = M // 2
+            Ns = L // 2 if filling == "half" else L // 4
+            h, U = S.chain(L, pbc=False), S.uniform_U(L, 4.0)
+            D = math.comb(L, Ns) ** 2
+            reps = max(3, min(200, int(2e8 // max(D, 1))))
+            row = {"M": M, "N": 2 * Ns, "dim": D}
+            xs = {64: torch.from_numpy(S.start_vector(D)).cuda()}
+            xs[32] = xs[64].float()
+            ys = {fp: torch.empty_like(x) for fp, x in xs.items()}
+            for name, method, path in (("fused_staggered", G.GBR_RANK_STAGGERED, G.GBR_HV_FUSED),
+                                       ("fused_combinadics", G.GBR_RANK_CNS, G.GBR_HV_FUSED),
+                                       ("factored", G.GBR_RANK_STAGGERED, G.GBR_HV_FACTORED)):
+                H = G.gbr_ham_create(L, h, U, Ns, Ns, method)
+                G.gbr_ham_set_path(H, path)
+                for fp in (32, 64):
+                    t = timed(lambda: G.gbr_hv(H, xs[fp], ys[fp]), reps)
+                    row[f"{name}_fp{fp}_ns"] = t * 1e9 / D / M
+                H.close()
+            states = S.sector_states(L, Ns, Ns)
+            for name, R, bis in (("trie_R8", 8, False), ("trie_R4", 4, False), ("bisection", 8, True)):
+                Sh = G.gbr_setham_create(L, h, U, states, R)
+                if bis:
+                    G.gbr_setham_set_bisect(Sh, True)
+                else:
+                    row[f"{name}_f"] = G.gbr_setham_info(Sh)["trie_elements"] / D
+                for fp in (32, 64):
+                    t = timed(lambda: G.gbr_setham_hv(Sh, xs[fp], ys[fp], check=0), reps)
+                    row[f"{name}_fp{fp}_ns"] = t * 1e9 / D / M
+                Sh.close()
+            for fp in (32, 64):
+                row[f"bisection_over_trie_R8_fp{fp}"] = row[f"bisection_fp{fp}_ns"] / row[f"trie_R8_fp{fp}_ns"]
+                row[f"bisection_over_fused_staggered_fp{fp}"] = row[f"bisection_fp{fp}_ns"] / row[f"fused_staggered_fp{fp}_ns"]
+            out[filling].append(row)
+            del xs, ys, states
+            torch.cuda.empty_cache()
+    return out
 
 
 def run_ours(args, rank: int, world: int):
@@ -575,8 +692,12 @@ def run_ours(args, rank: int, world: int):
         except Exception as ex:
             line["configs"] = {"error": repr(ex)}
     if rank == 0 and world == 1 and not args.no_cpu:
-        v, desc, dt = oracle_sample(args.cpu_seconds)
-        line["cpu_baseline"] = {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": desc}
+        v1, desc1, _ = oracle_sample(args.cpu_seconds / 3)
+        pool = OraclePool()
+        v, desc = pool.sample(args.cpu_seconds * 2 / 3)
+        pool.close()
+        line["cpu_baseline"] = {"value": v, "unit": UNIT, "cores": pool.workers, "kind": "oracle", "sample": desc,
+                                "single_thread": {"value": v1, "sample": desc1}}
     if rank == 0:
         print(json.dumps(line), flush=True)
 
@@ -662,6 +783,9 @@ def main():
                     help="run the ranking kernels this many times on 2^26 queries and exit (for ncu captures)")
     ap.add_argument("--ranking-sweep", action="store_true",
                     help="print the M=28 ranking sweep (every filling) as JSON and exit")
+    ap.add_argument("--eig-timings", action="store_true",
+                    help="print the per-state H·v times of every ranking strategy on the open chain "
+                         "(half and quarter filling, M = 4..32) as JSON and exit")
     ap.add_argument("--profile-hv", type=int, default=0,
                     help="run this many FP32 H·v calls on the workload sector and exit (for ncu captures)")
     args = ap.parse_args()
@@ -673,6 +797,13 @@ def main():
         return
     if args.profile_lanczos:
         profile_lanczos(args.profile_lanczos)
+        return
+    if args.eig_timings:
+        import torch
+        import __graft_entry__
+        __graft_entry__.build()
+        import paper_2203_04158_gb300 as G
+        print(json.dumps({"eig_timings_open_chain": eig_timings(G, torch)}), flush=True)
         return
     if args.ranking_sweep:
         import torch

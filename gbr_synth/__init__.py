@@ -187,6 +187,55 @@ def trie_query_members(n: int, nset: int, seed: int = SEED_TRIE_QUERIES, offset:
 
 
 # ---------------------------------------------------------------------------
+# State sets (inputs of the trie-ranked and set Hamiltonians and of the
+# ranking benchmarks): every pattern of a fixed popcount, listed in
+# increasing order by splitting the word into a high and a low half.
+# ---------------------------------------------------------------------------
+
+_POP8 = np.array([bin(i).count("1") for i in range(256)], dtype=np.int64)
+
+
+def _popcount(v: np.ndarray) -> np.ndarray:
+    """Set bits of each value below 2**24 (a byte table)."""
+    v = v.astype(np.int64)
+    return _POP8[v & 255] + _POP8[(v >> 8) & 255] + _POP8[(v >> 16) & 255]
+
+
+def popcount_states(M: int, N: int) -> np.ndarray:
+    """All M-bit patterns with N set bits (M <= 64), in increasing order."""
+    if N < 0 or N > M:
+        return np.empty(0, dtype=np.uint64)
+    if M > 44:
+        raise ValueError("popcount_states enumerates words of at most 44 bits")   # halves below 2**24
+    lo = M // 2
+    hi = M - lo
+    low = np.arange(1 << lo, dtype=np.uint64)
+    high = np.arange(1 << hi, dtype=np.uint64)
+    pl = _popcount(low)
+    ph = _popcount(high)
+    by_pop = [low[pl == k] for k in range(lo + 1)]
+    blocks = []
+    for u in high:                       # increasing high half, then increasing low half
+        k = N - int(ph[int(u)])
+        if 0 <= k <= lo and by_pop[k].size:
+            blocks.append((u << np.uint64(lo)) | by_pop[k])
+    return np.concatenate(blocks) if blocks else np.empty(0, dtype=np.uint64)
+
+
+def fixed_N_states(L: int, N: int) -> np.ndarray:
+    """All 2L-bit states with N particles in total (every S_z), sorted."""
+    return popcount_states(2 * L, N)
+
+
+def sector_states(L: int, Nup: int, Ndn: int) -> np.ndarray:
+    """The (N_up, N_dn) sector as 2L-bit patterns (spin down in the low L
+    bits), sorted: spin-up pattern major, spin-down pattern minor."""
+    up = popcount_states(L, Nup)
+    dn = popcount_states(L, Ndn)
+    return ((up[:, None] << np.uint64(L)) | dn[None, :]).ravel()
+
+
+# ---------------------------------------------------------------------------
 # Momentum-basis Hubbard ring (operator-product form of the Hamiltonian).
 # Orbitals: momentum k_m = 2 pi m / L, m = 0..L-1; spin down m -> bit m,
 # spin up m -> bit L + m.  Operator code = 2 * orbital + 1 for a creator,

@@ -259,6 +259,12 @@ int gbr_setham_create(int L, const double *h, const double *U, const uint64_t *h
                       gbr_setham **out);
 void gbr_setham_destroy(gbr_setham *S);
 
+/* bisect = 1: rank hop targets by bisection in the sorted member list (the
+ * established method of Sec. II, the comparison point of Fig. eig-timings;
+ * targets are always checked); 0 (default): by the trie.
+ * Errors: GBR_EINVAL for a NULL handle. */
+int gbr_setham_set_bisect(gbr_setham *S, int bisect);
+
 /* dim = n; elements = n plus every hop of every member (the matrix elements
  * one H·v visits when the set is closed under H); trie_elements = packed
  * trie size without padding. */

@@ -12,6 +12,7 @@
 
 struct gbr_setham {
     int L = 0, R = 0;
+    int bisect = 0;             // 1: rank by bisection in the member list instead of the trie
     int64_t n = 0;
     int64_t elements = 0;
     gbr::HamK k{};
@@ -31,7 +32,7 @@ struct SetTrieK {
     int64_t padded, smem_entries, n;
 };
 
-template <typename T, typename E>
+template <typename T, typename E, bool BISECT>
 __global__ void __launch_bounds__(256) k_set_hv(const SetTrieK tk, const E *__restrict__ t,
                                                 const uint64_t *__restrict__ states, const HamK hk,
                                                 const T *__restrict__ hc, const T *__restrict__ hd,
@@ -80,14 +81,26 @@ __global__ void __launch_bounds__(256) k_set_hv(const SetTrieK tk, const E *__re
                     const int q = __ffs(emp) - 1;
                     emp &= emp - 1u;
                     const uint64_t b = a ^ ((uint64_t)((1u << p) | (1u << q)) << off);
-                    // Fig. trielookup on the full pattern, indices clamped into the table
-                    E k = 0;
-                    for (int lvl = 0; lvl < tk.H; ++lvl) {
-                        E idx = k + (E)((uint32_t)(b >> tk.shift[lvl]) & ((1u << tk.width[lvl]) - 1u));
-                        idx = idx > last ? last : idx;
-                        k = idx < sm_end ? ts[idx] : __ldg(t + idx);
+                    uint64_t k = 0;
+                    if (BISECT) {
+                        // the established baseline: lower bound in the sorted member list
+                        int64_t lo = 0, len = tk.n;
+                        while (len > 0) {
+                            const int64_t half = len >> 1;
+                            if (__ldg(states + lo + half) < b) { lo += half + 1; len -= half + 1; } else { len = half; }
+                        }
+                        k = (uint64_t)lo;
+                    } else {
+                        // Fig. trielookup on the full pattern, indices clamped into the table
+                        E kk = 0;
+                        for (int lvl = 0; lvl < tk.H; ++lvl) {
+                            E idx = kk + (E)((uint32_t)(b >> tk.shift[lvl]) & ((1u << tk.width[lvl]) - 1u));
+                            idx = idx > last ? last : idx;
+                            kk = idx < sm_end ? ts[idx] : __ldg(t + idx);
+                        }
+                        k = (uint64_t)kk;
                     }
-                    if (check && !((uint64_t)k < (uint64_t)tk.n && __ldg(states + (uint64_t)k) == b)) continue;
+                    if ((check || BISECT) && !(k < (uint64_t)tk.n && __ldg(states + k) == b)) continue;
                     const int lo = min(p, q), hi = max(p, q);
                     const uint32_t between = ((hi >= 32) ? 0xFFFFFFFFu : ((1u << hi) - 1u)) & ~((1u << (lo + 1)) - 1u);
                     const T c = hcs[p * L + q];
@@ -117,7 +130,7 @@ static int launch_set_hv(const gbr_setham *S, const T *x, T *y, int check, cudaS
     const size_t smem = ((tr->smem_entries * sizeof(E) + 15) & ~(size_t)15) + (size_t)(S->L * S->L + S->L) * sizeof(T);
     int64_t blocks = (S->n + 255) / 256;
     blocks = std::max<int64_t>(1, std::min<int64_t>(blocks, (int64_t)sm_count() * 8));
-    auto kern = k_set_hv<T, E>;
+    auto kern = S->bisect ? k_set_hv<T, E, true> : k_set_hv<T, E, false>;
     if (smem > 48 * 1024) GBR_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     kern<<<(int)blocks, 256, smem, st>>>(tk, tr->t.as<E>(), tr->members.as<uint64_t>(), S->k, hc, hd, uv, check, x, y);
     GBR_LAUNCH_CHECK();
@@ -182,6 +195,13 @@ extern "C" int gbr_setham_create(int L, const double *h, const double *U, const 
 }
 
 extern "C" void gbr_setham_destroy(gbr_setham *S) { delete S; }
+
+extern "C" int gbr_setham_set_bisect(gbr_setham *S, int bisect) {
+    clear_error();
+    if (!S) return set_error(GBR_EINVAL, "NULL handle");
+    S->bisect = bisect ? 1 : 0;
+    return GBR_OK;
+}
 
 extern "C" int gbr_setham_info(const gbr_setham *S, int64_t *dim, int64_t *elements, int64_t *trie_elements) {
     clear_error();

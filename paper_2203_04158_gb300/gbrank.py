@@ -101,6 +101,7 @@ def lib():
                 "gbr_setham_create": (i32, [i32, vp, vp, vp, i64, i32, vp]),
                 "gbr_setham_destroy": (None, [vp]),
                 "gbr_setham_info": (i32, [vp, vp, vp, vp]),
+                "gbr_setham_set_bisect": (i32, [vp, i32]),
                 "gbr_setham_hv": (i32, [vp, vp, vp, i32, i32, vp]),
                 "gbr_batch_layout": (i32, [i32, vp, vp, vp]),
                 "gbr_batch_solve": (i32, [i32, vp, vp, i32, vp, vp, vp, vp]),
@@ -374,6 +375,10 @@ def gbr_setham_info(S: SetHam):
     d, e, t = C.c_int64(), C.c_int64(), C.c_int64()
     _check(lib().gbr_setham_info(S, C.byref(d), C.byref(e), C.byref(t)))
     return dict(dim=d.value, elements=e.value, trie_elements=t.value)
+
+
+def gbr_setham_set_bisect(S: SetHam, bisect: bool):
+    _check(lib().gbr_setham_set_bisect(S, int(bool(bisect))))
 
 
 def gbr_setham_hv(S: SetHam, x, y, check: int = 1, stream=None):

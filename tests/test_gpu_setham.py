@@ -76,3 +76,27 @@ def test_large_fixed_N_set_sampled(G):
     y_ref, drop = oracle.hv_set(L, h, U, st, x)
     assert drop == 0 and rel_inf(y, y_ref) <= TOL64
     assert info["trie_elements"] >= st.size
+
+
+@pytest.mark.parametrize("fp", [64, 32])
+def test_bisection_ranking_gives_the_same_bits(G, fp):
+    """Bisection in the member list (the baseline of Fig. eig-timings) and
+    the trie walk rank every target identically, so the products agree bit
+    for bit; on an open subset both drop the same targets."""
+    import torch
+    L = 7
+    h, U = S.chain(L, pbc=False), S.uniform_U(L, 4.0)
+    full = oracle.sector_states(L, 3, 3)
+    rng = np.random.default_rng(5)
+    for st in (full, np.sort(full[rng.choice(full.size, size=700, replace=False)])):
+        Sh = G.gbr_setham_create(L, h, U, st, 8)
+        x = torch.from_numpy(S.start_vector(st.size, 3)).cuda()
+        if fp == 32:
+            x = x.float()
+        ya, yb = torch.full_like(x, float("nan")), torch.full_like(x, float("nan"))
+        G.gbr_setham_hv(Sh, x, ya, check=1)
+        G.gbr_setham_set_bisect(Sh, True)
+        G.gbr_setham_hv(Sh, x, yb, check=0)
+        assert torch.equal(ya, yb)
+        y_ref, _ = oracle.hv_set(L, h, U, st, x.double().cpu().numpy())
+        assert rel_inf(yb.double().cpu().numpy(), y_ref) <= (TOL64 if fp == 64 else TOL32)
