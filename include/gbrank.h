@@ -350,6 +350,12 @@ typedef struct {
     double tol;       /* > 0: every 8 steps, stop once the lowest Ritz pair of T
                          has residual estimate beta_{k+1} |s_k| <= tol * max_j(|alpha_j|,
                          beta_j); 0 = run all iters steps */
+    double ritz_tail; /* > 0 (refine only): the Ritz vector x = sum_j s_j v_j keeps the
+                         leading terms and drops the trailing ones whose coefficients
+                         have norm <= ritz_tail |s|; the Rayleigh quotient then moves by
+                         about ritz_tail^2 times the spectral spread (it stays an upper
+                         bound of the lowest eigenvalue), and the second run of the
+                         recurrence (store_basis 0) stops early.  0 = every term */
 } gbr_lanczos_opts;
 
 typedef struct {
@@ -367,6 +373,7 @@ typedef struct {
                                 is counted in the last slot) */
     int stage_launches[4];   /* profile: launches of each stage */
     int converged;           /* 1 if the tol test stopped the recurrence */
+    int ritz_terms;          /* Lanczos vectors summed into the Ritz vector (refine) */
 } gbr_lanczos_result;
 
 /* Runs Lanczos from the start vector d_v0 (dim doubles on the device, not

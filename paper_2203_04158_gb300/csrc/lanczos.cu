@@ -608,8 +608,25 @@ static int lz_run(Lz &z, const double *d_v0, gbr_lanczos_result *res, const gbr_
         if ((rc = grow(x, (size_t)n * 8))) return rc;
         if ((rc = grow(hx, (size_t)n * 8))) return rc;
         double *sv = z.svec.as<double>();
+        // terms of the Ritz sum: drop the trailing coefficients whose norm is
+        // at most ritz_tail (s is normalised by the tridiagonal solver)
+        int nterm = kdone;
+        if (o->ritz_tail > 0.0 && kdone > 1) {
+            std::vector<double> hs((size_t)kdone);
+            GBR_CUDA_TRY(cudaMemcpyAsync(hs.data(), sv, sizeof(double) * (size_t)kdone, cudaMemcpyDeviceToHost, s));
+            GBR_CUDA_TRY(cudaStreamSynchronize(s));
+            double s2 = 0.0;
+            for (double v : hs) s2 += v * v;
+            const double lim = o->ritz_tail * o->ritz_tail * s2;
+            double tail = 0.0;
+            while (nterm > 1 && tail + hs[(size_t)(nterm - 1)] * hs[(size_t)(nterm - 1)] <= lim) {
+                tail += hs[(size_t)(nterm - 1)] * hs[(size_t)(nterm - 1)];
+                --nterm;
+            }
+        }
+        res->ritz_terms = nterm;
         if (z.store) {
-            k_ritz_from_basis<T><<<z.grid, kRedThreads, 0, s>>>(z.basis.as<T>(), sv, z.scal.as<double>(), kdone, n,
+            k_ritz_from_basis<T><<<z.grid, kRedThreads, 0, s>>>(z.basis.as<T>(), sv, z.scal.as<double>(), nterm, n,
                                                                 x.as<double>());
             count_launches(1);
         } else {
@@ -622,11 +639,11 @@ static int lz_run(Lz &z, const double *d_v0, gbr_lanczos_result *res, const gbr_
             k_scale_start<T><<<z.grid, kRedThreads, 0, s>>>(B0, z.tri.as<double>() + 1, n);
             count_launches(4);
             int ph = 0;
-            for (int j = 0; j < kdone; ++j) {
+            for (int j = 0; j < nterm; ++j) {
                 T *v = z.buf[ph].as<T>();
                 k_ritz_accum<T><<<z.grid, kRedThreads, 0, s>>>(v, sv, z.scal.as<double>(), j, n, x.as<double>());
                 count_launches(1);
-                if (j + 1 < kdone) {
+                if (j + 1 < nterm) {
                     rc = lz_step<T>(z, ph, true, nullptr, false);
                     if (rc) return rc;
                 }
@@ -691,6 +708,7 @@ extern "C" int gbr_lanczos(const gbr_ham *H, const gbr_lanczos_opts *o, const do
     if (!H || !o || !res || !d_v0) return set_error(GBR_EINVAL, "NULL argument");
     if (o->iters < 1 || o->iters > 65535) return set_error(GBR_EINVAL, "iters=%d out of range 1..65535", o->iters);
     if (o->prec != GBR_PREC_FP64 && o->prec != GBR_PREC_MIXED) return set_error(GBR_EINVAL, "unknown prec %d", o->prec);
+    if (!(o->ritz_tail >= 0.0 && o->ritz_tail < 1.0)) return set_error(GBR_EINVAL, "ritz_tail must be in [0, 1)");
     if ((uintptr_t)d_v0 & 7u) return set_error(GBR_EINVAL, "v0 must be 8-byte aligned");
     memset(res, 0, sizeof(*res));
     Lz z(const_cast<gbr_ham *>(H));

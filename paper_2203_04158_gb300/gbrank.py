@@ -36,14 +36,15 @@ class GbrError(RuntimeError):
 
 class LanczosOpts(C.Structure):
     _fields_ = [("iters", C.c_int), ("reorth", C.c_int), ("prec", C.c_int), ("refine", C.c_int),
-                ("store_basis", C.c_int), ("use_graph", C.c_int), ("profile", C.c_int), ("tol", C.c_double)]
+                ("store_basis", C.c_int), ("use_graph", C.c_int), ("profile", C.c_int), ("tol", C.c_double),
+                ("ritz_tail", C.c_double)]
 
 
 class LanczosResult(C.Structure):
     _fields_ = [("E0", C.c_double), ("E_ritz", C.c_double), ("residual", C.c_double), ("iters_done", C.c_int),
                 ("breakdown", C.c_int), ("stored_basis", C.c_int), ("seconds", C.c_double),
                 ("hv_seconds", C.c_double), ("stage_seconds", C.c_double * 4), ("stage_launches", C.c_int * 4),
-                ("converged", C.c_int)]
+                ("converged", C.c_int), ("ritz_terms", C.c_int)]
 
 
 class Term(C.Structure):
@@ -342,10 +343,10 @@ def gbr_launch_count() -> int:
 
 def gbr_lanczos(H: Ham, v0, iters: int, reorth: bool = False, prec: int = GBR_PREC_MIXED, refine: bool = True,
                 store_basis: int = -1, use_graph: bool = False, want_ritz: bool = False, profile: bool = False,
-                tol: float = 0.0, stream=None) -> dict:
+                tol: float = 0.0, ritz_tail: float = 0.0, stream=None) -> dict:
     import torch
     o = LanczosOpts(iters, int(bool(reorth)), prec, int(bool(refine)), store_basis, int(bool(use_graph)),
-                    int(bool(profile)), float(tol))
+                    int(bool(profile)), float(tol), float(ritz_tail))
     r = LanczosResult()
     a = np.zeros(iters, dtype=np.float64)
     b = np.zeros(max(iters, 1), dtype=np.float64)
@@ -356,7 +357,7 @@ def gbr_lanczos(H: Ham, v0, iters: int, reorth: bool = False, prec: int = GBR_PR
     return dict(E0=r.E0, E_ritz=r.E_ritz, residual=r.residual, iters=k, breakdown=bool(r.breakdown),
                 stored_basis=bool(r.stored_basis), seconds=r.seconds, hv_seconds=r.hv_seconds,
                 stage_seconds=list(r.stage_seconds), stage_launches=list(r.stage_launches),
-                converged=bool(r.converged),
+                converged=bool(r.converged), ritz_terms=r.ritz_terms,
                 alpha=a[:k].copy(), beta=b[:max(k - 1, 0)].copy(), ritz=None if rz is None else rz[:k].copy())
 
 
