@@ -221,14 +221,19 @@ __global__ void __launch_bounds__(kBatchThreads) k_batch(const SectorDesc *__res
         const int K = min(iters, D);
         // Restarted Lanczos: each cycle stops as soon as the lowest Ritz pair
         // of T has converged to FP32 level (residual estimate
-        // beta_{k+1} |s_k| <= 1e-6 max(|alpha|, beta), tested every 4 steps and
-        // at the last step of the cycle), which keeps the FP32
+        // beta_{k+1} |s_k| <= 1e-6 max(|alpha|, beta), tested after 4 steps and
+        // then at half the distance the decrease so far predicts (4 to 16
+        // steps), with a warm-started eigenvalue search and the last
+        // eigenvector component alone, and at the last step of the cycle), which keeps the FP32
         // recurrence from running on after convergence and spoiling the Ritz
         // vector; a cycle that ends unconverged restarts from its Ritz vector
         // (at most three cycles).  Each cycle runs the recurrence twice: once
         // for the scalars, once more (bit identical) to accumulate the Ritz
         // vector x in FP64.
         __shared__ int conv_s;
+        __shared__ double lam_hint, gap_hint;   // warm start of the convergence test's eigenvalue search
+        __shared__ int next_check, k_last;       // step of the next test; step and residual of the last one
+        __shared__ double r_last;
         int kdone = 0;
         for (int cyc = 0; cyc < 3; ++cyc) {
             if (cyc > 0) {
@@ -244,7 +249,14 @@ __global__ void __launch_bounds__(kBatchThreads) k_batch(const SectorDesc *__res
             const double n0 = sqrt(bsum((double)fh + (double)fl, red));
             double scale = 0.0;
             kdone = 0;
-            if (threadIdx.x == 0) conv_s = 0;
+            if (threadIdx.x == 0) {
+                conv_s = 0;
+                lam_hint = 0.0;
+                gap_hint = 0.0;
+                next_check = 4;
+                k_last = 0;
+                r_last = 0.0;
+            }
             __syncthreads();
             for (int pass = 0; pass < 2; ++pass) {
                 for (int i = threadIdx.x; i < D; i += blockDim.x) {
@@ -296,15 +308,40 @@ __global__ void __launch_bounds__(kBatchThreads) k_batch(const SectorDesc *__res
                             if (threadIdx.x == 0) conv_s = 1;
                         }
                         __syncthreads();
-                        if (conv_s || (kdone & 3) == 0 || k + 1 >= Kc) {
+                        if (!conv_s && kdone == next_check && k + 1 < Kc) {
+                            // residual estimate from the last eigenvector component alone
+                            const double lam = tridiag_lowest_warm(alpha, beta, kdone, &lam_hint, &gap_hint);
+                            if (threadIdx.x == 0) {
+                                const double thr = 1e-6 * scale;
+                                const double r = b * tridiag_last_component(alpha, beta, kdone, lam, work);
+                                if (r <= thr) {
+                                    conv_s = 1;
+                                } else {
+                                    // next test at half the distance the geometric decrease since
+                                    // the last test predicts, 4 to 16 steps ahead
+                                    int gap = 4;
+                                    if (r_last > 0.0 && r < r_last) {
+                                        const double per_step = log(r / r_last) / (double)(kdone - k_last);
+                                        const double steps = log(thr / r) / per_step;
+                                        gap = 4 * max(1, min(4, (int)(0.5 * steps / 4.0)));
+                                    }
+                                    next_check = kdone + gap;
+                                    r_last = r;
+                                    k_last = kdone;
+                                }
+                            }
+                            __syncthreads();
+                        }
+                        if (conv_s || k + 1 >= Kc) {
+                            // the Ritz pair of the final T for the second pass
                             const double lam = tridiag_lowest_block(alpha, beta, kdone);
                             if (threadIdx.x == 0) {
                                 tridiag_vector_thread(alpha, beta, kdone, lam, svec, work);
                                 if (b * fabs(svec[kdone - 1]) <= 1e-6 * scale) conv_s = 1;
                             }
                             __syncthreads();
+                            break;
                         }
-                        if (conv_s || k + 1 >= Kc) break;
                     }
                     __syncthreads();
                     const float inv = (float)(1.0 / beta[k + 1]);

@@ -36,6 +36,8 @@ struct LzState {
     int breakdown;
     int converged;    // 1 once the residual test stopped the recurrence
     double scale;     // max_j(|alpha_j|, beta_j)
+    double lam_hint;  // convergence test: previous lowest Ritz value and its last decrease
+    double gap_hint;
 };
 
 // 16-byte packs of vector elements for the streaming kernels: every vector
@@ -252,15 +254,15 @@ __global__ void __launch_bounds__(kRedThreads) k_tridiag(const LzState *st, cons
 
 // Convergence test every 8 steps (after beta_{k+1} is known): residual
 // estimate of the lowest Ritz pair, beta_{k+1} |s_k|, against tol * scale.
-// One warp does the multisection; thread 0 the eigenvector.
+// One warp does the eigenvalue search (warm-started from the previous test);
+// thread 0 the last eigenvector component.
 __global__ void __launch_bounds__(32) k_conv_check(LzState *st, const double *alpha, const double *beta, double tol,
-                                                   double *s, double *work) {
+                                                   double *work) {
     const int k = st->k + 1;
     if (st->converged || (k % 8) != 0) return;
-    const double lam = tridiag_lowest_block(alpha, beta, k);
+    const double lam = tridiag_lowest_warm(alpha, beta, k, &st->lam_hint, &st->gap_hint);
     if (threadIdx.x == 0) {
-        tridiag_vector_thread(alpha, beta, k, lam, s, work);
-        const double res = beta[k] * fabs(s[k - 1]);
+        const double res = beta[k] * tridiag_last_component(alpha, beta, k, lam, work);
         if (res <= tol * st->scale) {
             st->stop = 1;
             st->converged = 1;
@@ -483,8 +485,7 @@ static int lz_step(Lz &z, int phase, bool pass2, cudaEvent_t *ev4, bool want_rit
         ++nk;
     }
     if (z.tol > 0.0 && !pass2) {
-        k_conv_check<<<1, 32, 0, z.st>>>(st, z.alpha.as<double>(), z.beta.as<double>(), z.tol, z.svec.as<double>(),
-                                         z.work.as<double>());
+        k_conv_check<<<1, 32, 0, z.st>>>(st, z.alpha.as<double>(), z.beta.as<double>(), z.tol, z.work.as<double>());
         ++nk;
     }
     if (want_ritz) {
