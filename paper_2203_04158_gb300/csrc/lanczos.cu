@@ -413,6 +413,7 @@ struct Lz {
     int64_t n;
     int fp;            // 32 or 64
     int iters, reorth, store;
+    int in_basis = 0;  // the stored basis slots are the working vectors (eager launches only)
     int grid;
     double tol = 0.0;
     cudaStream_t st;
@@ -435,12 +436,21 @@ static int grow(DevBuf &b, size_t bytes) {
 }
 
 template <typename T>
-static int lz_step(Lz &z, int phase, bool pass2, cudaEvent_t *ev4, bool want_ritz) {
+static int lz_step(Lz &z, int phase, bool pass2, cudaEvent_t *ev4, bool want_ritz, int kh = -1) {
     // three rotating buffers: u_k in B[phase], u_{k-1} in B[phase + 2],
     // w (then u_{k+1}) in B[phase + 1] (indices mod 3), which held u_{k-2};
-    // the next step uses phase + 1
+    // the next step uses phase + 1.  With in_basis (eager launches, host step
+    // kh), u_{k-1}, u_k and w are the basis slots k-1, k, k+1 instead, which
+    // saves the copy of u_{k+1} into its slot.
     const int64_t n = z.n;
     T *v = z.buf[phase].as<T>(), *vprev = z.buf[(phase + 2) % 3].as<T>(), *w = z.buf[(phase + 1) % 3].as<T>();
+    const bool basis_slots = z.in_basis && !pass2 && kh >= 0;
+    if (basis_slots) {
+        T *bs = z.basis.as<T>();
+        v = bs + (int64_t)kh * n;
+        vprev = kh > 0 ? bs + (int64_t)(kh - 1) * n : v;
+        w = bs + (int64_t)(kh + 1) * n;
+    }
     LzState *st = z.state.as<LzState>();
     double *part = z.part.as<double>();
     int64_t nk = 0;
@@ -462,7 +472,7 @@ static int lz_step(Lz &z, int phase, bool pass2, cudaEvent_t *ev4, bool want_rit
         ++nk;
     }
     // with re-orthogonalisation the basis slot is written after it
-    T *slot_basis = (z.store && !pass2 && !z.reorth) ? z.basis.as<T>() : nullptr;
+    T *slot_basis = (z.store && !pass2 && !z.reorth && !basis_slots) ? z.basis.as<T>() : nullptr;
     k_step2<T><<<z.grid, kRedThreads, 0, z.st>>>(st, z.scal.as<double>(), v, w, slot_basis, n, part,
                                                 (pass2 || z.reorth) ? 0 : 1);
     ++nk;
@@ -528,6 +538,9 @@ static int lz_run(Lz &z, const double *d_v0, gbr_lanczos_result *res, const gbr_
     // graph mode: one graph per buffer phase, captured on a private stream
     // after two eager steps (which also set kernel attributes), replayed on s
     const bool graphs = o->use_graph && !o->profile;
+    // every basis slot starts on a 16-byte boundary (the step kernels load
+    // 16-byte packs) only when a vector is a whole number of packs
+    z.in_basis = (z.store && !z.reorth && !graphs && ((size_t)z.n * sizeof(T)) % 16 == 0) ? 1 : 0;
     cudaGraphExec_t gexec[3] = {nullptr, nullptr, nullptr};
     int64_t gnodes[3] = {0, 0, 0};
     cudaStream_t cap = nullptr;
@@ -567,7 +580,7 @@ static int lz_run(Lz &z, const double *d_v0, gbr_lanczos_result *res, const gbr_
                 }
                 ev4 = z.evs.data() + z.evs.size() - 5;
             }
-            rc = lz_step<T>(z, phase, false, ev4, want_ritz);
+            rc = lz_step<T>(z, phase, false, ev4, want_ritz, k);
             if (rc) break;
         }
         phase = (phase + 1) % 3;
