@@ -86,8 +86,7 @@ struct SpinLists {
     uint32_t *st;      // states
     uint8_t *cnt;      // hops per state
     uint32_t *ent;     // [state][hmax]: target | bond << 16 | sign << 31
-    float *d32;        // one-body diagonal
-    double *d64;
+    float *d32;        // one-body diagonal (the FP64 one is summed on the fly)
 };
 
 // builds the per-spin state list and hop lists of one spin species
@@ -113,19 +112,30 @@ __device__ void build_spin(int L, int N, int D, int hmax, const double *h, const
         }
         s.cnt[r] = (uint8_t)min(k, hmax);
         s.d32[r] = (float)d;
-        s.d64[r] = d;
     }
 }
 
-// y = H x on the sector, one element per thread iteration
+// sum of h_pp over the occupied sites of one spin pattern (ascending p)
+__device__ __forceinline__ double diag64(uint32_t a, const double *h, int L) {
+    double d = 0.0;
+    while (a) {
+        const int p = __ffs(a) - 1;
+        a &= a - 1u;
+        d += h[p * L + p];
+    }
+    return d;
+}
+
+// y = H x on the sector, one element per thread iteration (hs: the L x L
+// one-body matrix, for the FP64 diagonal)
 template <typename T>
 __device__ void hv_small(const SectorDesc &sd, int hmax, const SpinLists &up, const SpinLists &dn, const T *bc,
-                         const T *U, const T *x, T *y) {
+                         const T *U, const double *hs, const T *x, T *y) {
     const int D = sd.Dup * sd.Ddn;
     for (int i = threadIdx.x; i < D; i += blockDim.x) {
         const int ru = i / sd.Ddn, rd = i - ru * sd.Ddn;
         const uint32_t au = up.st[ru], ad = dn.st[rd];
-        T dg = (sizeof(T) == 8) ? (T)(up.d64[ru] + dn.d64[rd]) : (T)(up.d32[ru] + dn.d32[rd]);
+        T dg = (sizeof(T) == 8) ? (T)(diag64(au, hs, sd.L) + diag64(ad, hs, sd.L)) : (T)(up.d32[ru] + dn.d32[rd]);
         const uint32_t both = au & ad;
         for (int p = 0; p < sd.L; ++p)
             if ((both >> p) & 1u) dg += U[p];
@@ -148,12 +158,18 @@ __device__ void hv_small(const SectorDesc &sd, int hmax, const SpinLists &up, co
 
 struct BatchSmem {
     int maxD, maxDs, hmax, iters;
+    int64_t slot;      // doubles of global scratch per CTA: x, Hx (maxD each), solver work 3 (iters + 2)
 };
 
-__global__ void __launch_bounds__(kBatchThreads) k_batch(const SectorDesc *__restrict__ secs, int nsec,
+// xg: per-CTA scratch of lay.slot doubles for the FP64 Ritz vector, its H·v
+// and the tridiagonal solver's work (global memory; each CTA reuses its own
+// slot, which stays in L2), so that the shared memory holds only the FP32
+// recurrence and three CTAs fit on an SM.
+__global__ void __launch_bounds__(kBatchThreads, 3) k_batch(const SectorDesc *__restrict__ secs, int nsec,
                                                          const ModelDev *__restrict__ models,
                                                          const double *__restrict__ start, int iters, BatchSmem lay,
-                                                         int *counter, double *__restrict__ outE, int *__restrict__ outK) {
+                                                         int *counter, double *__restrict__ outE, int *__restrict__ outK,
+                                                         double *__restrict__ xg) {
     extern __shared__ __align__(16) unsigned char smr[];
     // layout
     unsigned char *p = smr;
@@ -162,18 +178,17 @@ __global__ void __launch_bounds__(kBatchThreads) k_batch(const SectorDesc *__res
     float *v = (float *)take((size_t)maxD * 4);
     float *vp = (float *)take((size_t)maxD * 4);
     float *w = (float *)take((size_t)maxD * 4);
-    double *x = (double *)take((size_t)maxD * 8);
-    double *hx = (double *)take((size_t)maxD * 8);
+    double *x = xg + (size_t)blockIdx.x * lay.slot;
+    double *hx = x + maxD;
     SpinLists up, dn;
     up.st = (uint32_t *)take((size_t)maxDs * 4); dn.st = (uint32_t *)take((size_t)maxDs * 4);
     up.cnt = (uint8_t *)take((size_t)maxDs); dn.cnt = (uint8_t *)take((size_t)maxDs);
     up.ent = (uint32_t *)take((size_t)maxDs * hmax * 4); dn.ent = (uint32_t *)take((size_t)maxDs * hmax * 4);
     up.d32 = (float *)take((size_t)maxDs * 4); dn.d32 = (float *)take((size_t)maxDs * 4);
-    up.d64 = (double *)take((size_t)maxDs * 8); dn.d64 = (double *)take((size_t)maxDs * 8);
     double *alpha = (double *)take((size_t)(kmax + 2) * 8);
     double *beta = (double *)take((size_t)(kmax + 2) * 8);
     double *svec = (double *)take((size_t)(kmax + 2) * 8);
-    double *work = (double *)take((size_t)(kmax + 2) * 3 * 8);
+    double *work = xg + (size_t)blockIdx.x * lay.slot + 2 * (size_t)maxD;   // 3 (kmax + 2) doubles
     __shared__ double red[kBatchThreads / 32];
     __shared__ double hs[kBatchMaxL * kBatchMaxL];
     __shared__ double bc64[kBatchMaxL * kBatchMaxL];
@@ -271,7 +286,7 @@ __global__ void __launch_bounds__(kBatchThreads) k_batch(const SectorDesc *__res
                         for (int i = threadIdx.x; i < D; i += blockDim.x) x[i] = fma(svec[k], (double)v[i], k ? x[i] : 0.0);
                         if (k + 1 == ksteps) break;
                     }
-                    hv_small<float>(sd, hmax, up, dn, bc32, U32, v, w);
+                    hv_small<float>(sd, hmax, up, dn, bc32, U32, hs, v, w);
                     __syncthreads();
                     const float bk = k ? (float)beta[k] : 0.f;
                     float ah = 0.f, al = 0.f;
@@ -358,7 +373,7 @@ __global__ void __launch_bounds__(kBatchThreads) k_batch(const SectorDesc *__res
         }
         __syncthreads();
         // FP64 Rayleigh quotient of the Ritz vector
-        hv_small<double>(sd, hmax, up, dn, bc64, U64, x, hx);
+        hv_small<double>(sd, hmax, up, dn, bc64, U64, hs, x, hx);
         __syncthreads();
         double xhx = 0.0, xx = 0.0;
         for (int i = threadIdx.x; i < D; i += blockDim.x) {
@@ -447,11 +462,11 @@ extern "C" int gbr_batch_solve(int n_models, const gbr_model_desc *models, const
     }
     for (const SectorDesc &s : secs) maxD = std::max(maxD, s.Dup * s.Ddn);
     const int K = std::min(iters, maxD);
-    BatchSmem lay{maxD, maxDs, hmax, K};
+    BatchSmem lay{maxD, maxDs, hmax, K, 2 * (int64_t)maxD + 3 * (int64_t)(K + 2)};
     auto r16 = [](size_t b) { return (b + 15) & ~(size_t)15; };
-    size_t smem = 3 * r16((size_t)maxD * 4) + 2 * r16((size_t)maxD * 8) + 2 * r16((size_t)maxDs * 4) +
+    size_t smem = 3 * r16((size_t)maxD * 4) + 2 * r16((size_t)maxDs * 4) +
                   2 * r16((size_t)maxDs) + 2 * r16((size_t)maxDs * hmax * 4) + 2 * r16((size_t)maxDs * 4) +
-                  2 * r16((size_t)maxDs * 8) + 3 * r16((size_t)(K + 2) * 8) + r16((size_t)(K + 2) * 24);
+                  3 * r16((size_t)(K + 2) * 8);
     int dev = 0, optin = 0;
     GBR_CUDA_TRY(cudaGetDevice(&dev));
     GBR_CUDA_TRY(cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev));
@@ -465,7 +480,7 @@ extern "C" int gbr_batch_solve(int n_models, const gbr_model_desc *models, const
         return (int64_t)secs[(size_t)a].Dup * secs[(size_t)a].Ddn > (int64_t)secs[(size_t)b].Dup * secs[(size_t)b].Ddn;
     });
     for (size_t i = 0; i < idx.size(); ++i) order[i] = secs[(size_t)idx[i]];
-    DevBuf dsec, dmod, dE, dK, dctr;
+    DevBuf dsec, dmod, dE, dK, dctr, dx;
     if ((rc = dsec.upload(order.data(), order.size() * sizeof(SectorDesc)))) return rc;
     if ((rc = dmod.upload(md.data(), md.size() * sizeof(ModelDev)))) return rc;
     if ((rc = dE.alloc(order.size() * 8))) return rc;
@@ -477,8 +492,9 @@ extern "C" int gbr_batch_solve(int n_models, const gbr_model_desc *models, const
     int per_sm = 0;
     GBR_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_batch, kBatchThreads, smem));
     const int grid = std::max(1, std::min<int>((int)order.size(), sm_count() * std::max(1, per_sm)));
+    if ((rc = dx.alloc((size_t)grid * (size_t)lay.slot * 8))) return rc;
     k_batch<<<grid, kBatchThreads, smem, st>>>(dsec.as<SectorDesc>(), (int)order.size(), dmod.as<ModelDev>(), d_start,
-                                               K, lay, dctr.as<int>(), dE.as<double>(), dK.as<int>());
+                                               K, lay, dctr.as<int>(), dE.as<double>(), dK.as<int>(), dx.as<double>());
     GBR_LAUNCH_CHECK();
     count_launches(1);
     std::vector<double> E(order.size());
