@@ -321,6 +321,19 @@ def ranking_extras(G, torch):
     torch.cuda.synchronize()
     t = e0.elapsed_time(e1) / 1e3 / reps
     out["trie_40bit_2p24_sorted"] = {"ranks_per_s": n / t, "ms": t * 1e3}
+    # the same set in a trie dispatched from the most significant chunk
+    trm = G.gbr_trie_create(members, 40, 8, msb_first=True)
+    infm = G.gbr_trie_info(trm)
+    for name, qq in (("trie_msb_first_40bit_2p24", q), ("trie_msb_first_40bit_2p24_sorted", qs)):
+        G.gbr_trie_rank(trm, qq, r)
+        e0.record()
+        for _ in range(reps):
+            G.gbr_trie_rank(trm, qq, r)
+        e1.record()
+        torch.cuda.synchronize()
+        tm = e0.elapsed_time(e1) / 1e3 / reps
+        out[name] = {"ranks_per_s": n / tm, "ms": tm * 1e3, "overhead_f": infm["n_elements"] / infm["n_members"]}
+    del trm
     # the bisection baseline the paper compares against, on the same queries
     for name, qq in (("bisection_40bit_2p24", q), ("bisection_40bit_2p24_sorted", qs)):
         G.gbr_trie_rank_bisect(tr, qq, r)
@@ -517,8 +530,9 @@ def eig_timings(G, torch):
     (N = M/2, M = 4..32) and quarter filling (N = M/4, M = 8..32).
     Strategies: the fused per-element kernel with staggered tables and with
     combinadics (Fig. algr), the factored path, and per-element ranking of the
-    full 2L-bit pattern over the sector's state set by the trie (R = 8, 4)
-    and by bisection (the baseline)."""
+    full 2L-bit pattern over the sector's state set by the trie (R = 8, 4,
+    most significant chunk first; R = 8 also in the paper's order) and by
+    bisection (the baseline)."""
     import gbr_synth as S
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
 
@@ -554,8 +568,9 @@ def eig_timings(G, torch):
                     row[f"{name}_fp{fp}_ns"] = t * 1e9 / D / M
                 H.close()
             states = S.sector_states(L, Ns, Ns)
-            for name, R, bis in (("trie_R8", 8, False), ("trie_R4", 4, False), ("bisection", 8, True)):
-                Sh = G.gbr_setham_create(L, h, U, states, R)
+            for name, R, bis, msb in (("trie_R8", 8, False, True), ("trie_R8_paper_order", 8, False, False),
+                                      ("trie_R4", 4, False, True), ("bisection", 8, True, True)):
+                Sh = G.gbr_setham_create(L, h, U, states, R, msb_first=msb)
                 if bis:
                     G.gbr_setham_set_bisect(Sh, True)
                 else:

@@ -119,6 +119,18 @@ typedef struct gbr_trie gbr_trie;
  * Errors: GBR_EINVAL if the input is unsorted, has duplicates or a bit at
  * or above M; GBR_ENOMEM; GBR_ECUDA. */
 int gbr_trie_create(const uint64_t *h_sorted, int64_t n, int M, int R, gbr_trie **out);
+
+/* gbr_trie_create with a choice of dispatch order.  msb_first = 0 is the
+ * paper's order above (Fig. trielookup).  msb_first = 1 dispatches the most
+ * significant chunk first (width M mod R, or R, at the top, then R-bit chunks
+ * down to bit 0); the paper has no counterpart: this is an interface of this
+ * library.  Ranks are the same either way; with the most significant chunk
+ * first, members close in value share their walk down to the last levels,
+ * so queries that arrive in increasing order (the hop targets of consecutive
+ * members of a sorted set) read neighbouring table entries.  The trie sizes
+ * differ for general sets (not for fixed-popcount sectors).
+ * Errors: as gbr_trie_create, and GBR_EINVAL for msb_first outside {0, 1}. */
+int gbr_trie_create_ordered(const uint64_t *h_sorted, int64_t n, int M, int R, int msb_first, gbr_trie **out);
 void gbr_trie_destroy(gbr_trie *t);
 
 /* n_members, n_elements (trie entries without padding; the overhead factor
@@ -132,6 +144,10 @@ int gbr_trie_info(const gbr_trie *t, int64_t *n_members, int64_t *n_elements, in
  * Needs no GPU. */
 int gbr_trie_build_host(const uint64_t *h_sorted, int64_t n, int M, int R, uint64_t *h_t, int64_t cap,
                         int64_t *size_out);
+
+/* gbr_trie_build_host with the dispatch order of gbr_trie_create_ordered. */
+int gbr_trie_build_host_ordered(const uint64_t *h_sorted, int64_t n, int M, int R, int msb_first, uint64_t *h_t,
+                                int64_t cap, int64_t *size_out);
 
 /* Ranks n patterns by the trie walk of Fig. trielookup.  Every table index
  * is clamped into the table, so any input is safe.  check = 1 verifies the
@@ -252,11 +268,17 @@ typedef struct gbr_setham gbr_setham;
 /* L: 1..32 sites; h, U as for gbr_ham_create; h_states: n distinct 2L-bit
  * patterns in increasing order (spin down in the low L bits; host, copied);
  * R: trie radix bits (1..16, 8 recommended).  Builds the packed trie of the
- * set (gbr_trie_create's layout).
+ * set (gbr_trie_create_ordered's layout, most significant chunk first).
  * Errors: GBR_EINVAL (unsorted set, bits at or above 2L, h not symmetric),
  * GBR_ENOMEM, GBR_ECUDA. */
 int gbr_setham_create(int L, const double *h, const double *U, const uint64_t *h_states, int64_t n, int R,
                       gbr_setham **out);
+
+/* gbr_setham_create with the trie's dispatch order (gbr_trie_create_ordered);
+ * gbr_setham_create uses msb_first = 1, whose walks for consecutive members
+ * stay in one subtree of the table. */
+int gbr_setham_create_ordered(int L, const double *h, const double *U, const uint64_t *h_states, int64_t n, int R,
+                              int msb_first, gbr_setham **out);
 void gbr_setham_destroy(gbr_setham *S);
 
 /* bisect = 1: rank hop targets by bisection in the sorted member list (the
@@ -306,7 +328,8 @@ typedef struct gbr_termham gbr_termham;
 
 /* H = sum of nterms tuples on M spin-orbitals (M 1..64), acting on the n
  * sorted, distinct M-bit states h_states (host, copied), ranked by a packed
- * trie of radix 2^R.  Terms must not touch orbitals at or above M.
+ * trie of radix 2^R (most significant chunk first, as gbr_setham_create).
+ * Terms must not touch orbitals at or above M.
  * Errors: GBR_EINVAL, GBR_ENOMEM, GBR_ECUDA. */
 int gbr_termham_create(int M, const gbr_term *h_terms, int nterms, const uint64_t *h_states, int64_t n, int R,
                        gbr_termham **out);

@@ -103,8 +103,13 @@ struct TriePlan {
 };
 
 // Builds the breadth-first packed trie into t (uint64 entries, size + 2^R
-// padding).  Returns GBR_OK or GBR_EINVAL (message set).
-int trie_build(const uint64_t *sorted, int64_t n, int M, int R, TriePlan *plan, std::vector<uint64_t> *t);
+// padding).  msb_first = 0: the paper's order (Fig. trielookup), the least
+// significant chunk (width M mod R, or R) dispatched first; 1: the most
+// significant chunk first (the same width at the top), so that members close
+// in value share their walk down to the last levels.  Returns GBR_OK or
+// GBR_EINVAL (message set).
+int trie_build(const uint64_t *sorted, int64_t n, int M, int R, TriePlan *plan, std::vector<uint64_t> *t,
+               int msb_first = 0);
 
 }  // namespace gbr
 
@@ -119,6 +124,7 @@ struct gbr_comb {
 
 struct gbr_trie {
     int M, R, H;
+    int msb_first;           // dispatch order of the chunks (trie_build)
     int width[gbr::kMaxChunks];
     int shift[gbr::kMaxChunks];
     int64_t n_members, size, padded;

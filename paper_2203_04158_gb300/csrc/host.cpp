@@ -165,7 +165,8 @@ void enumerate_combinations(int L, int N, std::vector<uint64_t> &out) {
 
 // ------------------------------------------------------------------ trie
 
-int trie_build(const uint64_t *sorted, int64_t n, int M, int R, TriePlan *plan, std::vector<uint64_t> *t) {
+int trie_build(const uint64_t *sorted, int64_t n, int M, int R, TriePlan *plan, std::vector<uint64_t> *t,
+               int msb_first) {
     if (M < 1 || M > 64) return set_error(GBR_EINVAL, "trie: M=%d out of range 1..64", M);
     if (R < 1 || R > 16) return set_error(GBR_EINVAL, "trie: R=%d out of range 1..16", R);
     if (n < 1) return set_error(GBR_EINVAL, "trie: empty member set");
@@ -181,7 +182,7 @@ int trie_build(const uint64_t *sorted, int64_t n, int M, int R, TriePlan *plan, 
     P.H = 1 + (M - w0) / R;
     for (int d = 0, sh = 0; d < P.H; ++d) {
         P.width[d] = d ? R : w0;
-        P.shift[d] = sh;
+        P.shift[d] = msb_first ? M - sh - P.width[d] : sh;
         sh += P.width[d];
     }
     // dispatch key: first dispatched (lowest) chunk most significant
@@ -242,12 +243,13 @@ extern "C" int gbr_version(void) { return 1; }
 
 extern "C" int64_t gbr_launch_count(void) { return launch_count(); }
 
-extern "C" int gbr_trie_build_host(const uint64_t *h_sorted, int64_t n, int M, int R, uint64_t *h_t, int64_t cap,
-                                   int64_t *size_out) {
+extern "C" int gbr_trie_build_host_ordered(const uint64_t *h_sorted, int64_t n, int M, int R, int msb_first,
+                                           uint64_t *h_t, int64_t cap, int64_t *size_out) {
     clear_error();
+    if (msb_first != 0 && msb_first != 1) return set_error(GBR_EINVAL, "msb_first=%d must be 0 or 1", msb_first);
     TriePlan plan;
     std::vector<uint64_t> t;
-    int rc = trie_build(h_sorted, n, M, R, &plan, &t);
+    int rc = trie_build(h_sorted, n, M, R, &plan, &t, msb_first);
     if (rc) return rc;
     if (size_out) *size_out = plan.size;
     if (h_t) {
@@ -256,4 +258,9 @@ extern "C" int gbr_trie_build_host(const uint64_t *h_sorted, int64_t n, int M, i
         memcpy(h_t, t.data(), t.size() * sizeof(uint64_t));
     }
     return GBR_OK;
+}
+
+extern "C" int gbr_trie_build_host(const uint64_t *h_sorted, int64_t n, int M, int R, uint64_t *h_t, int64_t cap,
+                                   int64_t *size_out) {
+    return gbr_trie_build_host_ordered(h_sorted, n, M, R, 0, h_t, cap, size_out);
 }

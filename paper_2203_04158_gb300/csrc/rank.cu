@@ -472,17 +472,20 @@ extern "C" int gbr_comb_unrank(const gbr_comb *c, const void *d_rank, int rank_b
     return GBR_OK;
 }
 
-extern "C" int gbr_trie_create(const uint64_t *h_sorted, int64_t n, int M, int R, gbr_trie **out) {
+extern "C" int gbr_trie_create_ordered(const uint64_t *h_sorted, int64_t n, int M, int R, int msb_first,
+                                       gbr_trie **out) {
     clear_error();
     if (!out) return set_error(GBR_EINVAL, "out is NULL");
     *out = nullptr;
+    if (msb_first != 0 && msb_first != 1) return set_error(GBR_EINVAL, "msb_first=%d must be 0 or 1", msb_first);
     TriePlan plan;
     std::vector<uint64_t> t;
-    int rc = trie_build(h_sorted, n, M, R, &plan, &t);
+    int rc = trie_build(h_sorted, n, M, R, &plan, &t, msb_first);
     if (rc) return rc;
     gbr_trie *T = new (std::nothrow) gbr_trie();
     if (!T) return set_error(GBR_ENOMEM, "host allocation failed");
     T->M = M; T->R = R; T->H = plan.H;
+    T->msb_first = msb_first;
     for (int l = 0; l < plan.H; ++l) { T->width[l] = plan.width[l]; T->shift[l] = plan.shift[l]; }
     T->n_members = n;
     T->size = plan.size;
@@ -515,6 +518,10 @@ extern "C" int gbr_trie_create(const uint64_t *h_sorted, int64_t n, int M, int R
     if (rc) { delete T; return rc; }
     *out = T;
     return GBR_OK;
+}
+
+extern "C" int gbr_trie_create(const uint64_t *h_sorted, int64_t n, int M, int R, gbr_trie **out) {
+    return gbr_trie_create_ordered(h_sorted, n, M, R, 0, out);
 }
 
 extern "C" void gbr_trie_destroy(gbr_trie *t) { delete t; }

@@ -142,8 +142,8 @@ static int launch_set_hv(const gbr_setham *S, const T *x, T *y, int check, cudaS
 
 using namespace gbr;
 
-extern "C" int gbr_setham_create(int L, const double *h, const double *U, const uint64_t *h_states, int64_t n, int R,
-                                 gbr_setham **out) {
+extern "C" int gbr_setham_create_ordered(int L, const double *h, const double *U, const uint64_t *h_states,
+                                         int64_t n, int R, int msb_first, gbr_setham **out) {
     clear_error();
     if (!out) return set_error(GBR_EINVAL, "out is NULL");
     *out = nullptr;
@@ -162,7 +162,7 @@ extern "C" int gbr_setham_create(int L, const double *h, const double *U, const 
     S->n = n;
     std::vector<uint16_t> pairs, bidx;
     int rc = build_hamk(L, h, U, GBR_RANK_STAGGERED, &S->k, &pairs, &bidx);
-    if (!rc) rc = gbr_trie_create(h_states, n, 2 * L, R, &S->trie);   // validates order, duplicates and width
+    if (!rc) rc = gbr_trie_create_ordered(h_states, n, 2 * L, R, msb_first, &S->trie);   // validates order, duplicates, width
     if (rc) { delete S; return rc; }
     // elements: the diagonal plus every hop of every member (for a set closed
     // under H, exactly the matrix elements one H·v visits)
@@ -192,6 +192,11 @@ extern "C" int gbr_setham_create(int L, const double *h, const double *U, const 
     if (rc) { delete S; return rc; }
     *out = S;
     return GBR_OK;
+}
+
+extern "C" int gbr_setham_create(int L, const double *h, const double *U, const uint64_t *h_states, int64_t n, int R,
+                                 gbr_setham **out) {
+    return gbr_setham_create_ordered(L, h, U, h_states, n, R, 1, out);
 }
 
 extern "C" void gbr_setham_destroy(gbr_setham *S) { delete S; }

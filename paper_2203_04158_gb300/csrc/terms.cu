@@ -161,7 +161,8 @@ extern "C" int gbr_termham_create(int M, const gbr_term *h_terms, int nterms, co
     T->M = M;
     T->n = n;
     T->nterms = nterms;
-    int rc = gbr_trie_create(h_states, n, M, R, &T->trie);
+    // most significant chunk first: neighbouring members share their walks
+    int rc = gbr_trie_create_ordered(h_states, n, M, R, 1, &T->trie);
     if (!rc) {
         // matrix elements: every (member, term) pair whose left demand holds
         int64_t el = 0;

@@ -75,6 +75,8 @@ def lib():
                 "gbr_comb_rank": (i32, [vp, vp, vp, i32, i64, i32, vp]),
                 "gbr_comb_unrank": (i32, [vp, vp, i32, vp, i64, vp]),
                 "gbr_trie_create": (i32, [vp, i64, i32, i32, vp]),
+                "gbr_trie_create_ordered": (i32, [vp, i64, i32, i32, i32, vp]),
+                "gbr_trie_build_host_ordered": (i32, [vp, i64, i32, i32, i32, vp, i64, vp]),
                 "gbr_trie_destroy": (None, [vp]),
                 "gbr_trie_info": (i32, [vp, vp, vp, vp, vp]),
                 "gbr_trie_build_host": (i32, [vp, i64, i32, i32, vp, i64, vp]),
@@ -100,6 +102,7 @@ def lib():
                 "gbr_termham_hv": (i32, [vp, vp, vp, i32, i32, vp]),
                 "gbr_termham_set_bisect": (i32, [vp, i32]),
                 "gbr_setham_create": (i32, [i32, vp, vp, vp, i64, i32, vp]),
+                "gbr_setham_create_ordered": (i32, [i32, vp, vp, vp, i64, i32, i32, vp]),
                 "gbr_setham_destroy": (None, [vp]),
                 "gbr_setham_info": (i32, [vp, vp, vp, vp]),
                 "gbr_setham_set_bisect": (i32, [vp, i32]),
@@ -231,10 +234,13 @@ def gbr_comb_unrank(c: Comb, rank, out, stream=None):
 
 # ----------------------------------------------------------------------- tries
 
-def gbr_trie_create(sorted_members: np.ndarray, M: int, R: int = 8) -> Trie:
+def gbr_trie_create(sorted_members: np.ndarray, M: int, R: int = 8, msb_first: bool = False) -> Trie:
     a = np.ascontiguousarray(sorted_members, dtype=np.uint64)
     p = C.c_void_p()
-    _check(lib().gbr_trie_create(_hptr(a), a.size, M, R, C.byref(p)))
+    if msb_first:
+        _check(lib().gbr_trie_create_ordered(_hptr(a), a.size, M, R, 1, C.byref(p)))
+    else:
+        _check(lib().gbr_trie_create(_hptr(a), a.size, M, R, C.byref(p)))
     return Trie(p)
 
 
@@ -244,13 +250,14 @@ def gbr_trie_info(t: Trie):
     return dict(n_members=nm.value, n_elements=ne.value, entry_bytes=eb.value, levels=lv.value)
 
 
-def gbr_trie_build_host(sorted_members: np.ndarray, M: int, R: int):
+def gbr_trie_build_host(sorted_members: np.ndarray, M: int, R: int, msb_first: bool = False):
     """(size without padding, table with padding as uint64)."""
     a = np.ascontiguousarray(sorted_members, dtype=np.uint64)
     size = C.c_int64()
-    _check(lib().gbr_trie_build_host(_hptr(a), a.size, M, R, None, 0, C.byref(size)))
+    o = int(bool(msb_first))
+    _check(lib().gbr_trie_build_host_ordered(_hptr(a), a.size, M, R, o, None, 0, C.byref(size)))
     t = np.zeros(size.value + (1 << R), dtype=np.uint64)
-    _check(lib().gbr_trie_build_host(_hptr(a), a.size, M, R, _hptr(t), t.size, C.byref(size)))
+    _check(lib().gbr_trie_build_host_ordered(_hptr(a), a.size, M, R, o, _hptr(t), t.size, C.byref(size)))
     return size.value, t
 
 
@@ -363,12 +370,13 @@ def gbr_lanczos(H: Ham, v0, iters: int, reorth: bool = False, prec: int = GBR_PR
 
 # ------------------------------------------------------ set Hamiltonians
 
-def gbr_setham_create(L: int, h, U, states: np.ndarray, R: int = 8) -> SetHam:
+def gbr_setham_create(L: int, h, U, states: np.ndarray, R: int = 8, msb_first: bool = True) -> SetHam:
     hh = np.ascontiguousarray(h, dtype=np.float64).reshape(L * L)
     uu = None if U is None else np.ascontiguousarray(U, dtype=np.float64).reshape(L)
     st = np.ascontiguousarray(states, dtype=np.uint64)
     p = C.c_void_p()
-    _check(lib().gbr_setham_create(L, _hptr(hh), None if uu is None else _hptr(uu), _hptr(st), st.size, R, C.byref(p)))
+    _check(lib().gbr_setham_create_ordered(L, _hptr(hh), None if uu is None else _hptr(uu), _hptr(st), st.size, R,
+                                           int(bool(msb_first)), C.byref(p)))
     return SetHam(p)
 
 

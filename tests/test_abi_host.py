@@ -69,17 +69,20 @@ def test_host_argument_errors(G):
         G.gbr_ham_create(33, np.zeros((33, 33)), None, 2, 2)
 
 
-def walk(t, M, R, a):
+def walk(t, M, R, a, msb_first=False):
     """Fig. trielookup over the host-built table, with the wrap-around pointer
-    arithmetic of the unsigned entries and clamping into the table."""
+    arithmetic of the unsigned entries and clamping into the table; with
+    msb_first the chunks are taken from the top bits down (the short chunk
+    first, at the top)."""
     w0 = M % R or R
     widths = [w0] + [R] * ((M - w0) // R)
-    k, sh = 0, 0
+    k, done = 0, 0
     for w in widths:
+        sh = M - done - w if msb_first else done
         idx = (k + ((a >> sh) & ((1 << w) - 1))) % (1 << 64)
         idx = min(idx, t.size - 1)
         k = int(t[idx])
-        sh += w
+        done += w
     return k
 
 
@@ -101,6 +104,26 @@ def test_host_trie_random_sets(G, M, R):
     assert size == osize
     for i, a in enumerate(members):
         assert walk(t, M, R, int(a)) == i
+
+
+@pytest.mark.parametrize("M,R", [(7, 3), (10, 4), (12, 5), (16, 8), (20, 8), (11, 12), (40, 8)])
+def test_host_trie_most_significant_first(G, M, R):
+    """The most-significant-first order ranks every member correctly, reads
+    nothing for non-members beyond the table, and on a fixed-popcount sector
+    has the size of the paper's order."""
+    rng = np.random.default_rng(M + 11 * R)
+    if M <= 20:
+        members = np.sort(rng.choice(1 << M, size=min(300, 1 << (M - 1)), replace=False).astype(np.uint64))
+    else:
+        members = np.unique(rng.integers(0, 1 << M, size=3000, dtype=np.uint64))
+    size, t = G.gbr_trie_build_host(members, M, R, msb_first=True)
+    for i, a in enumerate(members):
+        assert walk(t, M, R, int(a), msb_first=True) == i
+    others = np.setdiff1d(rng.integers(0, 1 << min(M, 20), size=200, dtype=np.uint64), members)
+    for a in others:
+        walk(t, M, R, int(a), msb_first=True)          # stays inside the table (clamped)
+    sector = oracle.enumerate_sector(14, 5)
+    assert G.gbr_trie_build_host(sector, 14, 4, msb_first=True)[0] == G.gbr_trie_build_host(sector, 14, 4)[0]
 
 
 @pytest.mark.slow

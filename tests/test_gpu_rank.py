@@ -121,16 +121,22 @@ def test_comb_full_size_2pow28(G):
 
 # ------------------------------------------------------------------- tries
 
+@pytest.mark.parametrize("msb_first", [False, True])
 @pytest.mark.parametrize("M,R", [(7, 3), (10, 4), (12, 5), (16, 8), (20, 8), (24, 8), (13, 16)])
-def test_trie_random_sets(G, M, R):
+def test_trie_random_sets(G, M, R, msb_first):
+    """Both dispatch orders: the paper's (sizes equal to the oracle's) and
+    most significant chunk first; ranks, unranks, non-member flags and the
+    bisection baseline identical."""
     import torch
     rng = np.random.default_rng(100 * M + R)
     k = min(5000, (1 << M) // 3)
     members = np.sort(rng.choice(1 << M, size=k, replace=False).astype(np.uint64))
-    t = G.gbr_trie_create(members, M, R)
+    t = G.gbr_trie_create(members, M, R, msb_first=msb_first)
     info = G.gbr_trie_info(t)
     osize, _ = oracle.trie_build(members, M, R, with_table=False)
-    assert info["n_elements"] == osize and info["n_members"] == k
+    assert info["n_members"] == k
+    if not msb_first:
+        assert info["n_elements"] == osize
     r = torch.empty(k, dtype=torch.int32, device="cuda")
     G.gbr_trie_rank(t, to_dev_u64(members), r, check=1)
     assert np.array_equal(as_u32(r), np.arange(k, dtype=np.uint32))
@@ -166,13 +172,14 @@ def test_trie_paper_sector_M28_N5(G):
     assert np.array_equal(as_u32(r), np.arange(lst.size, dtype=np.uint32))
 
 
-def test_trie_full_size_40bit(G):
+@pytest.mark.parametrize("msb_first", [False, True])
+def test_trie_full_size_40bit(G, msb_first):
     """Trie workload: 2^24 distinct 40-bit patterns, 2^28 member queries."""
     import torch
     import gbr_synth.gpu as SG
     nset, n = 1 << 24, 1 << 28
     members = S.trie_member_set(nset, 40)
-    t = G.gbr_trie_create(members, 40, 8)
+    t = G.gbr_trie_create(members, 40, 8, msb_first=msb_first)
     mdev = to_dev_u64(members)
     j = SG.bounded(S.SEED_TRIE_QUERIES, n, nset)
     pats = mdev[j]
