@@ -248,6 +248,14 @@ int gbr_hv_static(const gbr_ham *H, const void *d_x, void *d_y, int fp, void *st
  * elements) is allocated on first use, so one H·v at a time per handle. */
 int gbr_hv_stage(const gbr_ham *H, const void *d_x, void *d_y, int fp, int stage, void *stream);
 
+/* Self-check of the FP64 reciprocal the tridiagonal eigensolvers use instead
+ * of the division (Newton-Raphson iteration from the single-precision
+ * approximate reciprocal; the paper has no counterpart): *h_max_rel_err
+ * receives the largest relative difference from the IEEE division over n
+ * values from 1e-29 to 1e29 of both signs.  Synchronous; GBR_EINVAL for
+ * n < 1 or a NULL output. */
+int gbr_check_rcp64(int64_t n, double *h_max_rel_err);
+
 /* Kernels this library has launched in the process so far (eager launches
  * plus, for replayed CUDA graphs, the kernels each replay runs). */
 int64_t gbr_launch_count(void);

@@ -349,7 +349,7 @@ __global__ void __launch_bounds__(kBatchThreads, 3) k_batch(const SectorDesc *__
                         }
                         if (conv_s || k + 1 >= Kc) {
                             // the Ritz pair of the final T for the second pass
-                            const double lam = tridiag_lowest_block(alpha, beta, kdone);
+                            const double lam = tridiag_lowest_warm(alpha, beta, kdone, &lam_hint, &gap_hint);
                             if (threadIdx.x == 0) {
                                 tridiag_vector_thread(alpha, beta, kdone, lam, svec, work);
                                 if (b * fabs(svec[kdone - 1]) <= 1e-6 * scale) conv_s = 1;
@@ -359,7 +359,7 @@ __global__ void __launch_bounds__(kBatchThreads, 3) k_batch(const SectorDesc *__
                         }
                     }
                     __syncthreads();
-                    const float inv = (float)(1.0 / beta[k + 1]);
+                    const float inv = 1.0f / (float)beta[k + 1];   // FP32: the FP64 divide is slow here
                     for (int i = threadIdx.x; i < D; i += blockDim.x) {
                         const float vn = w[i] * inv;
                         vp[i] = v[i];

@@ -714,7 +714,57 @@ static int lz_run(Lz &z, const double *d_v0, gbr_lanczos_result *res, const gbr_
 
 }  // namespace gbr
 
+namespace gbr {
+
+// rcp64 against the IEEE division on n values x_i = +-10^e, e spread over
+// [-29, 29] with a splitmix-style integer hash of i for the mantissa and
+// sign; each CTA writes its largest relative error.
+__global__ void __launch_bounds__(kRedThreads) k_check_rcp64(int64_t n, double *part) {
+    double worst = 0.0;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        uint64_t z = (uint64_t)i * 0x9E3779B97F4A7C15ull + 0x2545F4914F6CDD1Dull;
+        z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+        z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+        z ^= z >> 31;
+        const double m = 1.0 + (double)(z >> 12) * 0x1.0p-52;                // [1, 2)
+        const double e = -29.0 + 58.0 * (double)((z >> 4) & 0xFFu) / 255.0;  // [-29, 29]
+        const double x = ((z & 1u) ? -m : m) * exp10(e);
+        const double exact = 1.0 / x;
+        const double err = fabs(rcp64(x) - exact) / fabs(exact);
+        worst = fmax(worst, err);
+    }
+    for (int o = 16; o > 0; o >>= 1) worst = fmax(worst, __shfl_down_sync(0xFFFFFFFFu, worst, o));
+    __shared__ double red[kRedThreads / 32];
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = worst;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double w = 0.0;
+        for (int j = 0; j < (int)(blockDim.x >> 5); ++j) w = fmax(w, red[j]);
+        part[blockIdx.x] = w;
+    }
+}
+
+}  // namespace gbr
+
 using namespace gbr;
+
+extern "C" int gbr_check_rcp64(int64_t n, double *h_max_rel_err) {
+    clear_error();
+    if (n < 1 || !h_max_rel_err) return set_error(GBR_EINVAL, "bad arguments");
+    const int grid = (int)std::max<int64_t>(1, std::min<int64_t>((n + kRedThreads - 1) / kRedThreads, 1024));
+    DevBuf part;
+    int rc = part.alloc(sizeof(double) * (size_t)grid);
+    if (rc) return rc;
+    k_check_rcp64<<<grid, kRedThreads>>>(n, part.as<double>());
+    GBR_LAUNCH_CHECK();
+    count_launches(1);
+    std::vector<double> h((size_t)grid);
+    GBR_CUDA_TRY(cudaMemcpy(h.data(), part.p, sizeof(double) * (size_t)grid, cudaMemcpyDeviceToHost));
+    double w = 0.0;
+    for (double v : h) w = std::max(w, v);
+    *h_max_rel_err = w;
+    return GBR_OK;
+}
 
 extern "C" int gbr_lanczos(const gbr_ham *H, const gbr_lanczos_opts *o, const double *d_v0, gbr_lanczos_result *res,
                            double *h_alpha, double *h_beta, double *h_ritz, void *stream) {

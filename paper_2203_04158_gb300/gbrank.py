@@ -87,6 +87,7 @@ def lib():
                 "gbr_ham_destroy": (None, [vp]),
                 "gbr_ham_info": (i32, [vp, vp, vp]),
                 "gbr_ham_set_path": (i32, [vp, i32]),
+                "gbr_check_rcp64": (i32, [i64, C.POINTER(C.c_double)]),
                 "gbr_ham_get_path": (i32, [vp, C.POINTER(i32)]),
                 "gbr_hv": (i32, [vp, vp, vp, i32, vp]),
                 "gbr_ham_tune": (i32, [vp, i32, vp]),
@@ -300,6 +301,13 @@ def gbr_ham_info(H: Ham):
 
 def gbr_ham_set_path(H: Ham, path: int):
     _check(lib().gbr_ham_set_path(H, path))
+
+
+def gbr_check_rcp64(n: int = 1 << 22) -> float:
+    """Largest relative error of the library's FP64 reciprocal against the division."""
+    e = C.c_double()
+    _check(lib().gbr_check_rcp64(n, C.byref(e)))
+    return e.value
 
 
 def gbr_ham_get_path(H: Ham) -> int:
