@@ -567,9 +567,14 @@ static void gather_shape(const gbr_ham *H, int64_t Drows, int64_t Dcols, bool al
                          int *vec_out, int *tr_out) {
     const int fpi = sizeof(T) == 8 ? 1 : 0;
     const int vmax = sizeof(T) == 4 ? 4 : 2;
+    // widest vector whose column chunk (the rows one wave of CTAs gathers
+    // from) stays within the cap: 128 MB for FP32, 64 MB for FP64 (measured
+    // on the L=18 ring, 48,620 rows: FP32 20.7 ms with 100 MB chunks against
+    // 24.5 ms with 50 MB and 37 ms with 25 MB; FP64 109 ms at 50 MB, 113 ms at 100 MB)
+    const double cap = sizeof(T) == 4 ? 128e6 : 64e6;
     int vec = 1;
     for (int v = vmax; v >= 2; v /= 2)
-        if (aligned16 && Dcols % v == 0 && (double)Drows * 128 * v * sizeof(T) <= 64e6) { vec = v; break; }
+        if (aligned16 && Dcols % v == 0 && (double)Drows * 128 * v * sizeof(T) <= cap) { vec = v; break; }
     const int tuned = lz ? H->tune_lz_rows[fpi] : (combine ? H->tune_up_rows[fpi] : H->tune_dn_rows[fpi]);
     // untuned default: 4 rows for the FP32 combine pass (its registers limit
     // occupancy; the tuner's pick on the 4x4 sector), 8 otherwise
