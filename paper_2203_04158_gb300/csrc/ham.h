@@ -95,8 +95,12 @@ int build_hamk(int L, const double *h, const double *U, int rank_method, HamK *k
 bool hv_is_factored(const gbr_ham *H);
 // factored H·v with the fused Lanczos epilogue; *nparts receives the number
 // of partial sums written (the grid of the spin-up pass)
+// xt_ready: X^T is already in the handle's scratch (written by the previous
+// step's update), so the transpose is skipped
 int hv_launch_lz(const gbr_ham *H, const void *x, void *y, int fp, cudaStream_t st, cudaEvent_t *ev, const LzHook &hook,
-                 int *nparts);
+                 int *nparts, bool xt_ready = false);
+// the handle's X^T scratch for precision fp (allocated if needed; NULL on failure)
+void *hv_xt_scratch(const gbr_ham *H, int fp);
 // upper bound of the partial sums hv_launch_lz writes for precision fp
 int64_t hv_lz_parts(const gbr_ham *H, int fp);
 }

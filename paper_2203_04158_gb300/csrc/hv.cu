@@ -668,12 +668,12 @@ static int stage_up(const gbr_ham *H, const T *x, T *y, cudaStream_t st, const H
 template <typename T>
 static int launch_factored(const gbr_ham *H, const T *x, T *y, cudaStream_t st, const HamDev &hd,
                            cudaEvent_t *ev = nullptr, const Scratch *ws = nullptr, const LzHook *hook = nullptr,
-                           int *nparts = nullptr) {
+                           int *nparts = nullptr, bool xt_ready = false) {
     if (ev) cudaEventRecord(ev[0], st);
     int rc = stage_hop_lists<T>(H, st);
     if (rc) return rc;
     if (ev) cudaEventRecord(ev[1], st);
-    if ((rc = stage_transpose<T>(H, x, st, ws))) return rc;
+    if (!xt_ready && (rc = stage_transpose<T>(H, x, st, ws))) return rc;
     if (ev) cudaEventRecord(ev[2], st);
     if ((rc = stage_dn<T>(H, st, hd, ws))) return rc;
     if (ev) cudaEventRecord(ev[3], st);
@@ -717,12 +717,18 @@ bool hv_is_factored(const gbr_ham *H) {
 }
 
 int hv_launch_lz(const gbr_ham *H, const void *x, void *y, int fp, cudaStream_t st, cudaEvent_t *ev, const LzHook &hook,
-                 int *nparts) {
+                 int *nparts, bool xt_ready) {
     const int fpi = fp == 64 ? 1 : 0;
     gbr_ham_prec *pb = prec_bufs(H, fpi);
     HamDev hd{pb->dup.p, pb->ddn.p, pb->uval.p, pb->bcoef.p, pb->hcoef.p};
-    if (fp == 64) return launch_factored<double>(H, (const double *)x, (double *)y, st, hd, ev, nullptr, &hook, nparts);
-    return launch_factored<float>(H, (const float *)x, (float *)y, st, hd, ev, nullptr, &hook, nparts);
+    if (fp == 64)
+        return launch_factored<double>(H, (const double *)x, (double *)y, st, hd, ev, nullptr, &hook, nparts, xt_ready);
+    return launch_factored<float>(H, (const float *)x, (float *)y, st, hd, ev, nullptr, &hook, nparts, xt_ready);
+}
+
+void *hv_xt_scratch(const gbr_ham *H, int fp) {
+    const size_t bytes = (size_t)H->D * (fp == 64 ? 8 : 4);
+    return ensure_ws(H, bytes) ? nullptr : H->ws_xt.p;
 }
 
 int64_t hv_lz_parts(const gbr_ham *H, int fp) {

@@ -137,6 +137,70 @@ __global__ void __launch_bounds__(kRedThreads) k_step2(const LzState *st, const 
     if (threadIdx.x == 0) part[blockIdx.x] = r;
 }
 
+// k_step2 for the factored H·v: the same update w -= (alpha_k / g_k) u_k and
+// partial <w, w>, over 64 x 64 tiles of the D_up x D_dn matrix, which also
+// writes the transpose of the new vector into xt: the spin-down pass of the
+// next H·v reads X^T, and this saves it the transpose's read of the vector.
+// 16-byte packs; needs rows and cols that are multiples of the pack and
+// 16-byte aligned vectors (edge tiles go element by element).
+template <typename T>
+__global__ void __launch_bounds__(256) k_step2_t(const LzState *st, const double *scal, const T *__restrict__ v,
+                                                 T *__restrict__ w, T *__restrict__ xt, int64_t rows, int64_t cols,
+                                                 double *part, int want_dot) {
+    if (st->stop) return;
+    constexpr int TILE = 64, V = Pack<T>::N, RP = TILE / V;
+    __shared__ T tile[TILE][TILE + 1];
+    const T a = (T)scal[kScal * st->k + 2];
+    const int64_t c0 = (int64_t)blockIdx.x * TILE, r0 = (int64_t)blockIdx.y * TILE;
+    const bool full = r0 + TILE <= rows && c0 + TILE <= cols;
+    DotAcc<T> acc;
+    for (int idx = threadIdx.x; idx < TILE * RP; idx += blockDim.x) {
+        const int i = idx / RP, j = idx % RP;
+        const int64_t r = r0 + i, c = c0 + (int64_t)j * V;
+        if (full) {
+            Pack<T> wp = *reinterpret_cast<const Pack<T> *>(w + r * cols + c);
+            const Pack<T> vv = *reinterpret_cast<const Pack<T> *>(v + r * cols + c);
+#pragma unroll
+            for (int e = 0; e < V; ++e) wp.e[e] -= a * vv.e[e];
+            *reinterpret_cast<Pack<T> *>(w + r * cols + c) = wp;
+#pragma unroll
+            for (int e = 0; e < V; ++e) {
+                tile[i][j * V + e] = wp.e[e];
+                if (want_dot) acc.add(wp.e[e], wp.e[e]);
+            }
+        } else {
+#pragma unroll
+            for (int e = 0; e < V; ++e) {
+                T wi = T(0);
+                if (r < rows && c + e < cols) {
+                    wi = w[r * cols + c + e] - a * v[r * cols + c + e];
+                    w[r * cols + c + e] = wi;
+                    if (want_dot) acc.add(wi, wi);
+                }
+                tile[i][j * V + e] = wi;
+            }
+        }
+    }
+    __syncthreads();
+    for (int idx = threadIdx.x; idx < TILE * RP; idx += blockDim.x) {
+        const int c = idx / RP, j = idx % RP;
+        const int64_t oc = c0 + c, orow = r0 + (int64_t)j * V;
+        Pack<T> o;
+#pragma unroll
+        for (int e = 0; e < V; ++e) o.e[e] = tile[j * V + e][c];
+        if (full) {
+            *reinterpret_cast<Pack<T> *>(xt + oc * rows + orow) = o;
+        } else if (oc < cols) {
+#pragma unroll
+            for (int e = 0; e < V; ++e)
+                if (orow + e < rows) xt[oc * rows + orow + e] = o.e[e];
+        }
+    }
+    if (!want_dot) return;
+    const double r = block_sum(acc.value());
+    if (threadIdx.x == 0) part[(int64_t)blockIdx.y * gridDim.x + blockIdx.x] = r;
+}
+
 // partial <w, w> only (after re-orthogonalisation)
 template <typename T>
 __global__ void __launch_bounds__(kRedThreads) k_norm2(const LzState *st, const T *__restrict__ w, int64_t n, double *part) {
@@ -414,6 +478,8 @@ struct Lz {
     int fp;            // 32 or 64
     int iters, reorth, store;
     int in_basis = 0;  // the stored basis slots are the working vectors (eager launches only)
+    int fuse_t = 0;    // the update writes X^T for the next H·v (k_step2_t)
+    void *xt = nullptr;
     int grid;
     double tol = 0.0;
     cudaStream_t st;
@@ -436,7 +502,7 @@ static int grow(DevBuf &b, size_t bytes) {
 }
 
 template <typename T>
-static int lz_step(Lz &z, int phase, bool pass2, cudaEvent_t *ev4, bool want_ritz, int kh = -1) {
+static int lz_step(Lz &z, int phase, bool pass2, cudaEvent_t *ev4, bool want_ritz, int kh = -1, bool first = false) {
     // three rotating buffers: u_k in B[phase], u_{k-1} in B[phase + 2],
     // w (then u_{k+1}) in B[phase + 1] (indices mod 3), which held u_{k-2};
     // the next step uses phase + 1.  With in_basis (eager launches, host step
@@ -458,7 +524,8 @@ static int lz_step(Lz &z, int phase, bool pass2, cudaEvent_t *ev4, bool want_rit
     if (hv_is_factored(z.H)) {
         // w = H v - beta_k v_{k-1} and the partials of <w, v> in the H·v epilogue
         const LzHook hook{vprev, z.scal.as<double>(), &st->k, pass2 ? nullptr : part};
-        int rc = hv_launch_lz(z.H, v, w, z.fp, z.st, ev4, hook, &nparts);
+        // X^T comes from the previous step's update except in each pass's first step
+        int rc = hv_launch_lz(z.H, v, w, z.fp, z.st, ev4, hook, &nparts, z.fuse_t && !first);
         if (rc) return rc;
     } else {
         int rc = hv_launch(z.H, v, w, z.fp, z.st, ev4);
@@ -473,8 +540,16 @@ static int lz_step(Lz &z, int phase, bool pass2, cudaEvent_t *ev4, bool want_rit
     }
     // with re-orthogonalisation the basis slot is written after it
     T *slot_basis = (z.store && !pass2 && !z.reorth && !basis_slots) ? z.basis.as<T>() : nullptr;
-    k_step2<T><<<z.grid, kRedThreads, 0, z.st>>>(st, z.scal.as<double>(), v, w, slot_basis, n, part,
-                                                (pass2 || z.reorth) ? 0 : 1);
+    int nparts2 = z.grid;
+    if (z.fuse_t) {
+        const int64_t rows = z.H->up.D, cols = z.H->dn.D;
+        const dim3 g((unsigned)((cols + 63) / 64), (unsigned)((rows + 63) / 64));
+        k_step2_t<T><<<g, 256, 0, z.st>>>(st, z.scal.as<double>(), v, w, (T *)z.xt, rows, cols, part, pass2 ? 0 : 1);
+        nparts2 = (int)(g.x * g.y);
+    } else {
+        k_step2<T><<<z.grid, kRedThreads, 0, z.st>>>(st, z.scal.as<double>(), v, w, slot_basis, n, part,
+                                                    (pass2 || z.reorth) ? 0 : 1);
+    }
     ++nk;
     if (z.reorth && !pass2) {
         T *basis = z.basis.as<T>();
@@ -491,7 +566,7 @@ static int lz_step(Lz &z, int phase, bool pass2, cudaEvent_t *ev4, bool want_rit
     }
     if (!pass2) {
         k_finalize<<<1, kFinThreads, 0, z.st>>>(st, z.alpha.as<double>(), z.beta.as<double>(), z.scal.as<double>(), part,
-                                                z.grid, 1, z.iters);
+                                                nparts2, 1, z.iters);
         ++nk;
     }
     if (z.tol > 0.0 && !pass2) {
@@ -541,6 +616,16 @@ static int lz_run(Lz &z, const double *d_v0, gbr_lanczos_result *res, const gbr_
     // every basis slot starts on a 16-byte boundary (the step kernels load
     // 16-byte packs) only when a vector is a whole number of packs
     z.in_basis = (z.store && !z.reorth && !graphs && ((size_t)z.n * sizeof(T)) % 16 == 0) ? 1 : 0;
+    // the tiled update that also writes X^T: factored H·v, no re-orthogonalisation
+    // (which changes w after the update), no separate basis-slot copy, and
+    // dimensions that are whole 16-byte packs
+    {
+        const int64_t V = 16 / (int64_t)sizeof(T);
+        z.fuse_t = (hv_is_factored(z.H) && !z.reorth && (!z.store || z.in_basis) && z.H->up.D % V == 0 &&
+                    z.H->dn.D % V == 0 && (z.H->up.D + 63) / 64 <= 65535) ? 1 : 0;
+        z.xt = z.fuse_t ? hv_xt_scratch(z.H, z.fp) : nullptr;
+        if (z.fuse_t && !z.xt) return set_error(GBR_ENOMEM, "scratch for X^T");
+    }
     cudaGraphExec_t gexec[3] = {nullptr, nullptr, nullptr};
     int64_t gnodes[3] = {0, 0, 0};
     cudaStream_t cap = nullptr;
@@ -580,7 +665,7 @@ static int lz_run(Lz &z, const double *d_v0, gbr_lanczos_result *res, const gbr_
                 }
                 ev4 = z.evs.data() + z.evs.size() - 5;
             }
-            rc = lz_step<T>(z, phase, false, ev4, want_ritz, k);
+            rc = lz_step<T>(z, phase, false, ev4, want_ritz, k, k == 0);
             if (rc) break;
         }
         phase = (phase + 1) % 3;
@@ -658,7 +743,7 @@ static int lz_run(Lz &z, const double *d_v0, gbr_lanczos_result *res, const gbr_
                 k_ritz_accum<T><<<z.grid, kRedThreads, 0, s>>>(v, sv, z.scal.as<double>(), j, n, x.as<double>());
                 count_launches(1);
                 if (j + 1 < nterm) {
-                    rc = lz_step<T>(z, ph, true, nullptr, false);
+                    rc = lz_step<T>(z, ph, true, nullptr, false, -1, j == 0);
                     if (rc) return rc;
                 }
                 ph = (ph + 1) % 3;
