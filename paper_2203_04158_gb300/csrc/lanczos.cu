@@ -416,13 +416,24 @@ __global__ void __launch_bounds__(kRedThreads) k_ritz_from_basis(const T *__rest
     }
 }
 
-// x += (s_j / g_j) u_j (second pass, one step at a time); FP32 values enter exactly
+// x += sum_{t < cnt} (s_{j0+t} / g_{j0+t}) u_t for up to three consecutive
+// Lanczos vectors (second pass), x = 0 before the first; FP32 values enter
+// exactly
 template <typename T>
-__global__ void __launch_bounds__(kRedThreads) k_ritz_accum(const T *__restrict__ v, const double *s, const double *scal,
-                                                            int j, int64_t n, double *__restrict__ x) {
-    const double sj = s[j] * scal[kScal * j];
-    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
-        x[i] = fma(sj, (double)v[i], j ? x[i] : 0.0);
+__global__ void __launch_bounds__(kRedThreads) k_ritz_accum3(const T *__restrict__ u0, const T *__restrict__ u1,
+                                                             const T *__restrict__ u2, int cnt, const double *s,
+                                                             const double *scal, int j0, int64_t n,
+                                                             double *__restrict__ x) {
+    const double c0 = s[j0] * scal[kScal * j0];
+    const double c1 = cnt > 1 ? s[j0 + 1] * scal[kScal * (j0 + 1)] : 0.0;
+    const double c2 = cnt > 2 ? s[j0 + 2] * scal[kScal * (j0 + 2)] : 0.0;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        double acc = j0 ? x[i] : 0.0;
+        acc = fma(c0, (double)u0[i], acc);
+        if (cnt > 1) acc = fma(c1, (double)u1[i], acc);
+        if (cnt > 2) acc = fma(c2, (double)u2[i], acc);
+        x[i] = acc;
+    }
 }
 
 // FP64 dots <a,b> partials (refinement)
@@ -737,11 +748,20 @@ static int lz_run(Lz &z, const double *d_v0, gbr_lanczos_result *res, const gbr_
             k_sum<<<1, kRedThreads, 0, s>>>(z.part.as<double>(), z.grid, z.tri.as<double>() + 1);
             k_scale_start<T><<<z.grid, kRedThreads, 0, s>>>(B0, z.tri.as<double>() + 1, n);
             count_launches(4);
-            int ph = 0;
+            // u_j sits in buffer j mod 3 until step j + 2 overwrites it, so the
+            // sum takes the vectors three at a time (one pass over x per three)
+            int ph = 0, j0 = 0;
             for (int j = 0; j < nterm; ++j) {
-                T *v = z.buf[ph].as<T>();
-                k_ritz_accum<T><<<z.grid, kRedThreads, 0, s>>>(v, sv, z.scal.as<double>(), j, n, x.as<double>());
-                count_launches(1);
+                if (j % 3 == 2 || j + 1 == nterm) {
+                    const int cnt = j - j0 + 1;
+                    const T *u0 = z.buf[j0 % 3].as<T>();
+                    const T *u1 = cnt > 1 ? z.buf[(j0 + 1) % 3].as<T>() : u0;
+                    const T *u2 = cnt > 2 ? z.buf[(j0 + 2) % 3].as<T>() : u0;
+                    k_ritz_accum3<T><<<z.grid, kRedThreads, 0, s>>>(u0, u1, u2, cnt, sv, z.scal.as<double>(), j0, n,
+                                                                  x.as<double>());
+                    count_launches(1);
+                    j0 = j + 1;
+                }
                 if (j + 1 < nterm) {
                     rc = lz_step<T>(z, ph, true, nullptr, false, -1, j == 0);
                     if (rc) return rc;
