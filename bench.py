@@ -402,9 +402,12 @@ def config_extras(G, torch):
     st = SG.uniform(S.SEED_START, nst)
     G.gbr_batch_solve(models[:4], st[:G.gbr_batch_layout(models[:4])[1]], 150)
     torch.cuda.synchronize()
-    t0 = time.perf_counter()
-    b = G.gbr_batch_solve(models, st, 150)
-    dt = time.perf_counter() - t0
+    dts = []
+    for _ in range(3):             # best of three whole calls (host set-up included)
+        t0 = time.perf_counter()
+        b = G.gbr_batch_solve(models, st, 150)
+        dts.append(time.perf_counter() - t0)
+    dt = min(dts)
     checks = []
     for m, best in ref["siam_lowest_E0"].items():
         checks.append(abs(b["E0"][int(m)] - best) / max(1.0, abs(best)))
@@ -709,6 +712,7 @@ def run_ours(args, rank: int, world: int):
         except Exception as ex:  # report rather than hide
             line["ranking"] = {"error": repr(ex)}
         H.close()
+        G.gbr_release_cache()          # the 4x4 basis; the L = 18 ring needs the memory
         torch.cuda.empty_cache()
         try:
             line["configs"] = config_extras(G, torch)

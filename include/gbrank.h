@@ -248,6 +248,15 @@ int gbr_hv_static(const gbr_ham *H, const void *d_x, void *d_y, int fp, void *st
  * elements) is allocated on first use, so one H·v at a time per handle. */
 int gbr_hv_stage(const gbr_ham *H, const void *d_x, void *d_y, int fp, int stage, void *stream);
 
+/* A call with a stored basis (store_basis) leaves the basis buffer, its one
+ * large allocation, in a process-wide cache rather than in the handle; the
+ * next call on the same device reuses it when it is large enough, so
+ * repeated solves neither allocate nor free it (the paper has no
+ * counterpart: this is an interface of this library).  The cache keeps at
+ * most one buffer, the largest, until gbr_release_cache frees it.  Always
+ * returns GBR_OK; call it with no solve running. */
+int gbr_release_cache(void);
+
 /* Self-check of the FP64 reciprocal the tridiagonal eigensolvers use instead
  * of the division (Newton-Raphson iteration from the single-precision
  * approximate reciprocal; the paper has no counterpart): *h_max_rel_err

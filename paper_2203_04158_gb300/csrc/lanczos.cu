@@ -23,6 +23,7 @@
 #include <algorithm>
 #include <cmath>
 #include <cstring>
+#include <mutex>
 
 #include "ham.h"
 #include "dot.cuh"
@@ -853,6 +854,81 @@ __global__ void __launch_bounds__(kRedThreads) k_check_rcp64(int64_t n, double *
 
 using namespace gbr;
 
+// The stored basis is a solve's one large allocation (105 GB for 200 FP32
+// steps on the 4x4 sector).  A finished call leaves it in a process-wide
+// cache instead of in the handle; the next call on the same device takes it
+// when it is large enough, so repeated solves, also on new handles, neither
+// allocate nor free it.  gbr_release_cache frees it.
+namespace gbr {
+static std::mutex g_cache_mu;
+static void *g_cache_p = nullptr;
+static size_t g_cache_bytes = 0;
+static int g_cache_dev = -1;
+
+static int current_device() {
+    int d = -1;
+    if (cudaGetDevice(&d) != cudaSuccess) return -1;
+    return d;
+}
+
+static void free_on(void *p, int dev) {
+    const int cur = current_device();
+    if (dev >= 0 && dev != cur) cudaSetDevice(dev);
+    cudaFree(p);
+    if (dev >= 0 && dev != cur && cur >= 0) cudaSetDevice(cur);
+}
+
+// cached bytes usable on the current device
+static size_t cache_bytes_here() {
+    std::lock_guard<std::mutex> g(g_cache_mu);
+    return (g_cache_p && g_cache_dev == current_device()) ? g_cache_bytes : 0;
+}
+
+// moves the cached basis into b when b is smaller than need and the cache is
+// not; a cached buffer on this device too small for need is freed (the
+// free-memory test counted it as available for the new allocation)
+static void cache_take(DevBuf &b, size_t need) {
+    std::lock_guard<std::mutex> g(g_cache_mu);
+    if (!g_cache_p || g_cache_dev != current_device() || (b.p && b.bytes >= need)) return;
+    if (g_cache_bytes < need) {
+        free_on(g_cache_p, g_cache_dev);
+        g_cache_p = nullptr;
+        g_cache_bytes = 0;
+        g_cache_dev = -1;
+        return;
+    }
+    b.release();
+    b.p = g_cache_p;
+    b.bytes = g_cache_bytes;
+    g_cache_p = nullptr;
+    g_cache_bytes = 0;
+    g_cache_dev = -1;
+}
+
+// moves b into the cache unless the cache holds a larger buffer
+static void cache_put(DevBuf &b) {
+    if (!b.p) return;
+    std::lock_guard<std::mutex> g(g_cache_mu);
+    if (g_cache_p && g_cache_bytes >= b.bytes) return;
+    if (g_cache_p) free_on(g_cache_p, g_cache_dev);
+    g_cache_p = b.p;
+    g_cache_bytes = b.bytes;
+    g_cache_dev = current_device();
+    b.p = nullptr;
+    b.bytes = 0;
+}
+}  // namespace gbr
+
+extern "C" int gbr_release_cache(void) {
+    clear_error();
+    std::lock_guard<std::mutex> g(g_cache_mu);
+    if (g_cache_p) free_on(g_cache_p, g_cache_dev);
+    g_cache_p = nullptr;
+    g_cache_bytes = 0;
+    g_cache_dev = -1;
+    return GBR_OK;
+}
+
 extern "C" int gbr_check_rcp64(int64_t n, double *h_max_rel_err) {
     clear_error();
     if (n < 1 || !h_max_rel_err) return set_error(GBR_EINVAL, "bad arguments");
@@ -899,7 +975,8 @@ extern "C" int gbr_lanczos(const gbr_ham *H, const gbr_lanczos_opts *o, const do
         if (store < 0) {
             size_t fr = 0, tot = 0;
             GBR_CUDA_TRY(cudaMemGetInfo(&fr, &tot));
-            fr += z.basis.bytes;   // the cached basis is released before a larger one is taken
+            // the handle's and the process cache's bases are reused or released before a larger one is taken
+            fr += z.basis.bytes + cache_bytes_here();
             const size_t need = basis_bytes + (size_t)z.n * (3 * es + 16) + ((size_t)2 << 30);
             store = need < fr ? 1 : 0;
         }
@@ -922,7 +999,12 @@ extern "C" int gbr_lanczos(const gbr_ham *H, const gbr_lanczos_opts *o, const do
     if ((rc = grow(z.ritz_tmp, sizeof(double) * (size_t)(z.iters + 2)))) return rc;
     for (int i = 0; i < 3; ++i)
         if ((rc = grow(z.buf[i], (size_t)z.n * es))) return rc;
-    if (z.store && (rc = grow(z.basis, basis_bytes))) return rc;
-    if (z.fp == 64) return lz_run<double>(z, d_v0, res, o, h_alpha, h_beta, h_ritz);
-    return lz_run<float>(z, d_v0, res, o, h_alpha, h_beta, h_ritz);
+    if (z.store) {
+        cache_take(z.basis, basis_bytes);
+        if ((rc = grow(z.basis, basis_bytes))) return rc;
+    }
+    rc = z.fp == 64 ? lz_run<double>(z, d_v0, res, o, h_alpha, h_beta, h_ritz)
+                    : lz_run<float>(z, d_v0, res, o, h_alpha, h_beta, h_ritz);
+    if (z.store) cache_put(z.basis);
+    return rc;
 }

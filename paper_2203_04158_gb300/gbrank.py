@@ -88,6 +88,7 @@ def lib():
                 "gbr_ham_info": (i32, [vp, vp, vp]),
                 "gbr_ham_set_path": (i32, [vp, i32]),
                 "gbr_check_rcp64": (i32, [i64, C.POINTER(C.c_double)]),
+                "gbr_release_cache": (i32, []),
                 "gbr_ham_get_path": (i32, [vp, C.POINTER(i32)]),
                 "gbr_hv": (i32, [vp, vp, vp, i32, vp]),
                 "gbr_ham_tune": (i32, [vp, i32, vp]),
@@ -301,6 +302,11 @@ def gbr_ham_info(H: Ham):
 
 def gbr_ham_set_path(H: Ham, path: int):
     _check(lib().gbr_ham_set_path(H, path))
+
+
+def gbr_release_cache():
+    """Frees the stored-basis buffer the library keeps between Lanczos calls."""
+    _check(lib().gbr_release_cache())
 
 
 def gbr_check_rcp64(n: int = 1 << 22) -> float:

@@ -44,6 +44,7 @@ def test_library_exports_every_declared_symbol(G):
 
 def test_null_handles_are_rejected_on_the_host(G):
     lib = C.CDLL(G.gbrank.LIB_PATH)
+    assert lib.gbr_release_cache() == G.GBR_OK          # nothing cached: no device call
     path = C.c_int(-1)
     assert lib.gbr_ham_get_path(None, C.byref(path)) == G.GBR_EINVAL and path.value == -1
     assert lib.gbr_ham_set_path(None, 0) == G.GBR_EINVAL

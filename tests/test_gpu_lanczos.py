@@ -176,3 +176,20 @@ def test_newton_reciprocal_of_the_eigensolvers_is_within_two_ulp(G):
     seeded in single precision; against the IEEE division it stays within
     two units in the last place over 1e-29..1e29."""
     assert G.gbr_check_rcp64(1 << 22) <= 2 * 2.0 ** -52
+
+
+def test_basis_cache_is_reused_and_released(G):
+    """A stored-basis solve leaves its basis in the library's cache; a second
+    solve on a new handle reuses it with the same result, and after
+    gbr_release_cache a third still solves (allocating afresh)."""
+    L, h, U, Nu, Nd = ring8()
+    E = []
+    for _ in range(2):
+        H = G.gbr_ham_create(L, h, U, Nu, Nd)
+        E.append(G.gbr_lanczos(H, v0(4900), 80, prec=G.GBR_PREC_MIXED, refine=True, store_basis=1)["E0"])
+        H.close()
+    G.gbr_release_cache()
+    H = G.gbr_ham_create(L, h, U, Nu, Nd)
+    E.append(G.gbr_lanczos(H, v0(4900), 80, prec=G.GBR_PREC_MIXED, refine=True, store_basis=1)["E0"])
+    G.gbr_release_cache()
+    assert E[0] == E[1] == E[2]
