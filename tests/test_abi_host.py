@@ -51,6 +51,21 @@ def test_null_handles_are_rejected_on_the_host(G):
     assert lib.gbr_ham_info(None, None, None) == G.GBR_EINVAL
 
 
+def test_new_entry_points_validate_on_the_host(G):
+    lib = C.CDLL(G.gbrank.LIB_PATH)
+    members = np.array([1, 5, 9], dtype=np.uint64)
+    pm = members.ctypes.data_as(C.c_void_p)
+    out = C.c_void_p()
+    size = C.c_int64()
+    assert lib.gbr_trie_create_ordered(pm, C.c_int64(3), 8, 4, 2, C.byref(out)) == G.GBR_EINVAL
+    assert lib.gbr_trie_build_host_ordered(pm, C.c_int64(3), 8, 4, -1, None, C.c_int64(0), C.byref(size)) == G.GBR_EINVAL
+    assert lib.gbr_trie_build_host_ordered(pm, C.c_int64(3), 8, 4, 1, None, C.c_int64(0), C.byref(size)) == G.GBR_OK
+    assert size.value > 0
+    err = C.c_double()
+    assert lib.gbr_check_rcp64(C.c_int64(0), C.byref(err)) == G.GBR_EINVAL
+    assert lib.gbr_setham_set_bisect(None, 1) == G.GBR_EINVAL
+
+
 def test_host_argument_errors(G):
     with pytest.raises(G.GbrError) as e:
         G.gbr_comb_create(65, 3, 8)
