@@ -328,9 +328,12 @@ __global__ void __launch_bounds__(128, ((MODE >= 1 && sizeof(T) == 4) ? 10 : 1))
     // row stride of the staged Z tile: 16 bytes of padding put the TR rows of
     // one column in different banks when the tile is written column by column
     constexpr int ZS = 128 * VEC + 16 / (int)sizeof(T);
+    // hop-list row stride, a multiple of 4 so that four targets (and four
+    // coefficients) are read with one 16-byte broadcast load
+    const int hs = (hmax + 3) & ~3;
     extern __shared__ __align__(16) unsigned char smr[];
     uint32_t *st = reinterpret_cast<uint32_t *>(smr);
-    T *sc = reinterpret_cast<T *>(smr + (((size_t)TR * hmax * 4 + 15) & ~(size_t)15));
+    T *sc = reinterpret_cast<T *>(smr + (size_t)TR * hs * 4);
     __shared__ int scnt[64];
     // U class values (combine), in shared memory to keep registers for occupancy
     __shared__ T suv[kMaxUClasses];
@@ -346,8 +349,8 @@ __global__ void __launch_bounds__(128, ((MODE >= 1 && sizeof(T) == 4) ? 10 : 1))
             const int64_t g = (int64_t)k * Drows + r0 + i;
             const uint32_t w = tgt[g];
             const T c = uniform ? hu : bcoef[bond[g]];
-            st[i * hmax + k] = w & 0x7FFFFFFFu;
-            sc[i * hmax + k] = (w >> 31) ? -c : c;
+            st[i * hs + k] = w & 0x7FFFFFFFu;
+            sc[i * hs + k] = (w >> 31) ? -c : c;
         }
     }
     __syncthreads();
@@ -355,8 +358,7 @@ __global__ void __launch_bounds__(128, ((MODE >= 1 && sizeof(T) == 4) ? 10 : 1))
     // combine epilogue: the block Z[r0..r0+TR, chunk] = (Z^T)[chunk, r0..r0+TR]
     // is read from Z^T once, column by column (TR consecutive values each),
     // into shared memory as [row][column]
-    T *zs = reinterpret_cast<T *>(smr + (((size_t)TR * hmax * 4 + 15) & ~(size_t)15) +
-                                  (((size_t)TR * hmax * sizeof(T) + 15) & ~(size_t)15));
+    T *zs = reinterpret_cast<T *>(smr + (size_t)TR * hs * (4 + sizeof(T)));
     if (COMBINE) {
         const T *zt = (const T *)ca.zt;
         const int64_t cbase = cc * (int64_t)(128 * VEC);
@@ -392,17 +394,34 @@ __global__ void __launch_bounds__(128, ((MODE >= 1 && sizeof(T) == 4) ? 10 : 1))
         const int64_t r = r0 + i;
         if (r >= Drows) break;
         const int n = scnt[i];
-        const uint32_t *ti = st + i * hmax;
-        const T *ci = sc + i * hmax;
+        const uint32_t *ti = st + i * hs;
+        const T *ci = sc + i * hs;
         T acc[VEC];
 #pragma unroll
         for (int v = 0; v < VEC; ++v) acc[v] = 0;
         if (VEC == 4 && sizeof(T) == 4) {
+            // the gathered rows move through the L1 data pipe at 4 wavefronts
+            // a row; the hop list costs half a wavefront a row, read four at
+            // a time (summed in hop order, as one at a time)
             float4 a4 = make_float4(0.f, 0.f, 0.f, 0.f);
-#pragma unroll 4
-            for (int k = 0; k < n; ++k) {
+            const float *cf = reinterpret_cast<const float *>(ci);
+            int k = 0;
+#pragma unroll 2
+            for (; k + 4 <= n; k += 4) {
+                const uint4 t4 = *reinterpret_cast<const uint4 *>(ti + k);
+                const float4 c4 = *reinterpret_cast<const float4 *>(cf + k);
+                const float4 v0 = __ldcg(reinterpret_cast<const float4 *>(x + (int64_t)t4.x * Dcols + c0));
+                const float4 v1 = __ldcg(reinterpret_cast<const float4 *>(x + (int64_t)t4.y * Dcols + c0));
+                const float4 v2 = __ldcg(reinterpret_cast<const float4 *>(x + (int64_t)t4.z * Dcols + c0));
+                const float4 v3 = __ldcg(reinterpret_cast<const float4 *>(x + (int64_t)t4.w * Dcols + c0));
+                a4.x += c4.x * v0.x; a4.y += c4.x * v0.y; a4.z += c4.x * v0.z; a4.w += c4.x * v0.w;
+                a4.x += c4.y * v1.x; a4.y += c4.y * v1.y; a4.z += c4.y * v1.z; a4.w += c4.y * v1.w;
+                a4.x += c4.z * v2.x; a4.y += c4.z * v2.y; a4.z += c4.z * v2.z; a4.w += c4.z * v2.w;
+                a4.x += c4.w * v3.x; a4.y += c4.w * v3.y; a4.z += c4.w * v3.z; a4.w += c4.w * v3.w;
+            }
+            for (; k < n; ++k) {
                 const float4 v = __ldcg(reinterpret_cast<const float4 *>(x + (int64_t)ti[k] * Dcols + c0));
-                const float c = (float)ci[k];
+                const float c = cf[k];
                 a4.x += c * v.x; a4.y += c * v.y; a4.z += c * v.z; a4.w += c * v.w;
             }
             acc[0] = a4.x; acc[1] = a4.y; acc[2] = a4.z; acc[3 % VEC] = a4.w;
@@ -595,8 +614,8 @@ static int launch_gather(const gbr_ham *H, const SpinSector &lists, int64_t Drow
     const int64_t nrb = (Drows + TR - 1) / TR;
     const int64_t ncc = (Dcols + 128 * vec - 1) / (128 * vec);
     const int hmax = std::max(1, lists.hmax);
-    const size_t smem = (((size_t)TR * hmax * 4 + 15) & ~(size_t)15) + (((size_t)TR * hmax * sizeof(T) + 15) & ~(size_t)15) +
-                        (COMBINE ? (size_t)TR * (128 * vec * sizeof(T) + 16) : 0);
+    const int hs = (hmax + 3) & ~3;   // the kernel's padded hop-list stride
+    const size_t smem = (size_t)TR * hs * (4 + sizeof(T)) + (COMBINE ? (size_t)TR * (128 * vec * sizeof(T) + 16) : 0);
     const int64_t blocks = nrb * ncc;
     if (blocks > 0x7FFFFFFF) return set_error(GBR_EINVAL, "sector too large for the gather grid");
 #define GBR_G(V, R)                                                                                          \
