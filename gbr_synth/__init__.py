@@ -260,6 +260,60 @@ def momentum_ring_terms(L: int, t: float = 1.0, U: float = 4.0):
     return terms
 
 
+def two_orbital_impurity_terms(n_bath: int = 4, U: float = 4.0, J: float = 0.6, seed: int = SEED_MODELS,
+                               model: int = 0):
+    """Operator-product term list of a two-orbital Anderson impurity with the
+    Kanamori interaction (a multi-orbital model whose U_ijkl goes beyond
+    density-density terms), as (coefficient, [operator codes]) with code
+    2 * orbital + 1 for a creator and 2 * orbital for an annihilator.
+
+    Sites 0 and 1 are the impurity orbitals a, b; sites 2 .. 1 + n_bath the
+    bath; spin-orbital p is (site p, down), L + p is (site p, up), L = 2 + n_bath.
+    One-body: eps_a = -U/2 - 0.1, eps_b = -U/2 + 0.1 on the orbitals, bath
+    energies eps_k ~ U[-2, 2), hybridisations V_mk ~ U[0, 1) between each
+    orbital and each bath site (draw indices model*64 + 1 + k for eps_k,
+    model*64 + 16 + m*8 + k for V_mk).  Interaction (U' = U - 2J):
+        U sum_m n_m,up n_m,dn + U' sum_{s,s'} n_a,s n_b,s' - J sum_s n_a,s n_b,s
+        - J (c+_a,up c_a,dn c+_b,dn c_b,up + h.c.)      (spin flip)
+        + J (c+_a,up c+_a,dn c_b,dn c_b,up + h.c.)      (pair hopping).
+    Every term comes with its adjoint, so the operator is symmetric; it
+    conserves N_up and N_dn."""
+    L = 2 + n_bath
+    base = model * 64
+    k = np.arange(n_bath, dtype=np.uint64)
+    eps = uniform(seed, base + 1 + k, -2.0, 2.0)
+    terms = []
+
+    def cr(site, spin):
+        return 2 * (site + (L if spin else 0)) + 1
+
+    def an(site, spin):
+        return 2 * (site + (L if spin else 0))
+
+    for spin in (0, 1):
+        terms.append((-U / 2 - 0.1, [cr(0, spin), an(0, spin)]))
+        terms.append((-U / 2 + 0.1, [cr(1, spin), an(1, spin)]))
+        for j in range(n_bath):
+            terms.append((float(eps[j]), [cr(2 + j, spin), an(2 + j, spin)]))
+    for m in (0, 1):
+        V = uniform(seed, base + 16 + m * 8 + k, 0.0, 1.0)
+        for j in range(n_bath):
+            for spin in (0, 1):
+                terms.append((float(V[j]), [cr(m, spin), an(2 + j, spin)]))
+                terms.append((float(V[j]), [cr(2 + j, spin), an(m, spin)]))
+    Up = U - 2 * J
+    for m in (0, 1):
+        terms.append((U, [cr(m, 1), an(m, 1), cr(m, 0), an(m, 0)]))
+    for s in (0, 1):
+        for sp in (0, 1):
+            terms.append((Up - (J if s == sp else 0.0), [cr(0, s), an(0, s), cr(1, sp), an(1, sp)]))
+    terms.append((-J, [cr(0, 1), an(0, 0), cr(1, 0), an(1, 1)]))
+    terms.append((-J, [cr(1, 1), an(1, 0), cr(0, 0), an(0, 1)]))
+    terms.append((J, [cr(0, 1), cr(0, 0), an(1, 0), an(1, 1)]))
+    terms.append((J, [cr(1, 1), cr(1, 0), an(0, 0), an(0, 1)]))
+    return L, terms
+
+
 def momentum_sector_states(L: int, Nup: int, Ndn: int, K: int) -> np.ndarray:
     """Sorted 2L-bit states with N_up, N_dn particles and total momentum
     sum of m over occupied orbitals = K (mod L)."""

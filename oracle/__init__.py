@@ -294,3 +294,79 @@ def lanczos(L, h, U, Nup, Ndn, s0, iters: int, reorth: bool):
         raise RuntimeError(f"ora_lanczos failed: {rc}")
     kk = k.value
     return dict(E0=E0.value, alpha=a[:kk].copy(), beta=b[:max(kk - 1, 0)].copy(), k=kk, ritz=e[:kk].copy())
+
+
+def bethe_ansatz_E0(L: int, Nup: int, Ndn: int, U: float, t: float = 1.0, shift: int = 0, tol: float = 1e-14):
+    """Ground-state energy of the periodic Hubbard ring, H = -t sum (c+_{i+1} c_i + h.c.) + U sum n_up n_dn,
+    from the Lieb-Wu Bethe-ansatz equations (textbook; not in the paper), for U > 0.
+
+    With N = Nup + Ndn electrons, M = min(Nup, Ndn) rapidities Lambda and
+    theta(x) = 2 arctan(x), the logarithmic equations are
+        L k_j = 2 pi I_j - sum_b theta((sin k_j - Lambda_b) / (U / 4t)),
+        sum_j theta((Lambda_a - sin k_j) / (U / 4t)) = 2 pi J_a + sum_b theta((Lambda_a - Lambda_b) / (U / 2t)),
+    and E = -2t sum_j cos k_j.  Taking logarithms of the product form fixes
+    the quantum numbers' parity: I_j is an integer for even M and half an odd
+    integer for odd M; J_a is an integer for odd N - M and half an odd
+    integer for even N - M.  The ground state takes consecutive I_j and J_a
+    centred on zero; when the parity forbids exact centring (the open-shell
+    fillings) the I_j are centred on +1/2 (shift = 0) or -1/2 (shift = 1).
+    (These consecutive quantum numbers give the ground state at the fillings
+    the tests compare with dense diagonalisation; not at every filling.)
+    Solved by Newton's method (finite-difference Jacobian), first at U = 4t
+    from the U = 0 momenta, then continued in small steps of U when U is
+    elsewhere.  Returns (E0, k, Lambda).
+    """
+    N, M = Nup + Ndn, min(Nup, Ndn)
+    if U <= 0 or M < 0 or N > 2 * L:
+        raise ValueError("needs U > 0 and a valid filling")
+    i_half = 0.5 if M % 2 else 0.0
+    j_half = 0.0 if (N - M) % 2 else 0.5
+
+    def centred(n, half, s):
+        base = np.arange(n) - (n - 1) / 2.0
+        if n and abs((base[0] - half) - round(base[0] - half)) > 1e-9:   # parity forbids centring
+            base = base + (0.5 if s == 0 else -0.5)
+        return base
+
+    I = centred(N, i_half, shift)
+    J = centred(M, j_half, 0)
+    th = lambda x: 2.0 * np.arctan(x)
+
+    def resid(z, c):
+        kk, ll = z[:N], z[N:]
+        sk = np.sin(kk)
+        r1 = L * kk - 2.0 * np.pi * I + th((sk[:, None] - ll[None, :]) / c).sum(axis=1)
+        r2 = (th((ll[:, None] - sk[None, :]) / c).sum(axis=1) - 2.0 * np.pi * J
+              - th((ll[:, None] - ll[None, :]) / (2 * c)).sum(axis=1))
+        return np.concatenate([r1, r2])
+
+    def solve(z, c):
+        for _ in range(100):
+            r = resid(z, c)
+            if np.max(np.abs(r)) < tol:
+                break
+            h = 1e-7
+            Jm = np.empty((z.size, z.size))
+            for q in range(z.size):
+                dz = np.zeros(z.size)
+                dz[q] = h
+                Jm[:, q] = (resid(z + dz, c) - resid(z - dz, c)) / (2 * h)
+            step = np.linalg.solve(Jm, -r)
+            lamb = 1.0
+            while lamb > 1e-4 and np.max(np.abs(resid(z + lamb * step, c))) > np.max(np.abs(r)):
+                lamb *= 0.5
+            z = z + lamb * step
+        return z, float(np.max(np.abs(resid(z, c))))
+
+    z = np.concatenate([2.0 * np.pi * I / L, np.linspace(-0.5, 0.5, M)])
+    z, res = solve(z, 1.0)                        # U = 4t
+    Us = [4.0 * t]
+    if U != 4.0 * t:
+        n = max(1, int(np.ceil(abs(np.log(U / (4.0 * t))) / 0.05)))
+        Us = list(4.0 * t * (U / (4.0 * t)) ** (np.arange(1, n + 1) / n))
+    for Ui in Us:
+        z, res = solve(z, Ui / (4.0 * t))
+    if res > 1e-10:
+        raise RuntimeError(f"Bethe-ansatz equations did not converge (residual {res:.2e})")
+    kk = z[:N]
+    return float(-2.0 * t * np.cos(kk).sum()), kk, z[N:]

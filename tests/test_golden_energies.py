@@ -28,6 +28,16 @@ def test_reference_energies_are_the_oracles():
     assert abs(g["square4x4_tp_U0_N7_7_free_E0"] - (-26.4)) <= 1e-12
     mk = _maker()
     assert abs(g["siam_lowest_E0"]["0"] - mk.siam_E0(0)) <= 1e-12
+    # the 18-site ring at U = 4: the Bethe-ansatz energy (recomputed, seconds)
+    E_ba = oracle.bethe_ansatz_E0(18, 9, 9, 4.0)[0]
+    assert abs(g["chain18_U4_N9_9_bethe_E0"] - E_ba) <= 1e-12 * abs(E_ba)
+    # the reduced 4x4 sector (minutes to recompute): converged, and below the
+    # U = 0 closed form shifted by the Hartree energy U N_up N_dn / L (the
+    # variational bound of the uniform free state)
+    E_sq = g["square4x4_tp_U8_N3_3_lanczos_E0"]
+    assert g["square4x4_tp_U8_N3_3_lanczos_change_last_50_steps"] <= 1e-12 * abs(E_sq)
+    E_free = oracle.free_E0(S.square(4, 4, 1.0, -0.3), 3, 3)
+    assert E_free < E_sq < E_free + 8.0 * 9 / 16
     assert set(g["siam_lowest_E0"]) == {str(m) for m in mk.SIAM_MODELS}
 
 

@@ -352,3 +352,58 @@ def test_operator_products_match_the_one_body_form():
     x = S.start_vector(st.size)
     y, drop = oracle.hv_ops(terms, st, x)
     assert drop == 0 and np.allclose(y, oracle.hv(L, h, U, 2, 3, x), rtol=0, atol=1e-13)
+
+
+@pytest.mark.parametrize("L,N,U", [(4, 2, 4.0), (6, 1, 4.0), (6, 3, 2.0), (6, 3, 4.0), (6, 3, 8.0), (8, 3, 4.0),
+                                   (8, 4, 4.0), (8, 4, 1.0)])
+def test_bethe_ansatz_matches_dense_diagonalisation(L, N, U):
+    """The Lieb-Wu energy of the periodic ring (the independent reference for
+    the 18-site ring at U = 4) equals dense diagonalisation of the oracle's
+    sector matrix, at closed-shell (N = 4n + 2 electrons) and open-shell
+    (N = 4n, both shifts of the quantum numbers) fillings."""
+    E_dense = oracle.dense_E0(L, S.chain(L), S.uniform_U(L, U), N, N)
+    for shift in (0, 1):
+        E_ba = oracle.bethe_ansatz_E0(L, N, N, U, shift=shift)[0]
+        assert abs(E_ba - E_dense) <= 1e-12 * abs(E_dense), (shift, E_ba, E_dense)
+
+
+@pytest.mark.slow
+def test_bethe_ansatz_matches_lanczos_ring10():
+    """L = 10, N_up = N_dn = 5 (63,504 states, beyond dense): Bethe ansatz
+    against the oracle's FP64 Lanczos."""
+    L, N, U = 10, 5, 4.0
+    D = oracle.sector_dim(L, N, N)
+    o = oracle.lanczos(L, S.chain(L), S.uniform_U(L, U), N, N, S.start_vector(D), 120, False)
+    E_ba = oracle.bethe_ansatz_E0(L, N, N, U)[0]
+    assert abs(E_ba - o["E0"]) <= 1e-12 * abs(E_ba)
+
+
+def test_bethe_ansatz_weak_coupling_approaches_free_fermions():
+    """As U -> 0 the Bethe-ansatz energy of the 18-site ring tends to the
+    U = 0 closed form plus the first-order (Hartree) shift U N_up N_dn / L of
+    the uniform free ground state; what remains is second order in U (the
+    remainder quarters when U halves).  A wrong first-order term would leave
+    a remainder linear in U (ratio 2)."""
+    L, N = 18, 9
+    E_free = oracle.free_E0(S.chain(L), N, N)
+    d = {U: oracle.bethe_ansatz_E0(L, N, N, U)[0] - (E_free + U * N * N / L) for U in (0.025, 0.05)}
+    assert abs(d[0.025]) < 1e-3
+    assert 3.9 <= d[0.05] / d[0.025] <= 4.1
+
+
+def test_two_orbital_kanamori_terms_are_spin_rotation_invariant():
+    """The Kanamori interaction with U' = U - 2J is SU(2) symmetric: every
+    level of the (N_up, N_dn) = (2, 4) sector (S >= 1) reappears in the
+    (3, 3) sector.  A wrong sign of the spin-flip or pair-hop terms breaks
+    it.  The term list is symmetric and conserves N_up and N_dn."""
+    L, terms = S.two_orbital_impurity_terms(3)
+    ev = {}
+    for nu, nd in ((3, 3), (2, 4)):
+        st = oracle.sector_states(L, nu, nd)
+        Hm = oracle.dense_ops(terms, st)
+        assert np.array_equal(Hm, Hm.T)
+        _, drop = oracle.hv_ops(terms, st, np.ones(st.size))
+        assert drop == 0
+        ev[(nu, nd)] = np.linalg.eigvalsh(Hm)
+    for e in ev[(2, 4)]:
+        assert np.min(np.abs(ev[(3, 3)] - e)) <= 1e-10
