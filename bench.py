@@ -1,17 +1,22 @@
 #!/usr/bin/env python
 """Benchmark of the on-the-fly H·v / Lanczos hot path on one GB300 per rank.
 
-Workload (default): the 4x4 Hubbard torus with diagonal hopping, t = 1,
-t' = -0.3, U = 8, N_up = N_dn = 7 (1.31e8 states, 8.93e9 matrix elements per
-H·v).  One step is one complete mixed-precision ground-state solve through
-the public API: 200 Lanczos steps with FP32 vectors and FP32 on-the-fly H·v
-(unrank, hop, sign, staggered rank, gather), FP64-grade scalars, the FP64
-tridiagonal eigenpair, the Ritz vector and its FP64 H·v Rayleigh quotient.
-The metric is H·v matrix elements per second over the whole step.
+Workload (default, the largest configuration that fits one GPU): the
+18-site Hubbard ring, t = 1, U = 4, N_up = N_dn = 9 (2.36e9 states, 4.74e10
+matrix elements per H·v, 9.5 GB per FP32 vector).  One step is one complete
+mixed-precision ground-state solve through the public API: 150 Lanczos
+steps with FP32 vectors and FP32 on-the-fly H·v (unrank, hop, sign,
+staggered rank, gather), FP64-grade scalars, the FP64 tridiagonal
+eigenpair, the Ritz vector (a second run of the recurrence: 150 stored
+vectors would need 1.4 TB) and its FP64 H·v Rayleigh quotient; every
+iteration replays a captured CUDA graph.  The metric is H·v matrix elements
+per second over the whole step (every H·v the step runs).
 
 Also reported (outside the timed steps): the all-FP64 GPU solve of the same
-sector for the mixed-vs-FP64 comparison, and ranks/s of the staggered and
-trie ranking kernels on their full-size workloads.
+sector and both precisions' time to |dE0|/|E0| <= 1e-9 against the
+Bethe-ansatz energy; the same for the 4x4 t' torus; the ranking kernels on
+their full-size workloads; the batched impurity models; the trie-ranked set
+and term Hamiltonians; a bounded filling sweep and per-state H·v timings.
 
 ``--impl reference`` times the CPU oracle on a bounded sample of the same
 workload (rank 0 only).  With torchrun (N > 1) every rank solves its own
@@ -35,12 +40,22 @@ sys.path.insert(0, ROOT)
 
 METRIC = "H·v matrix elements/s"
 UNIT = "elements/s"
-WORKLOAD = "hubbard_4x4_tp_mixed_lanczos"
-L, NUP, NDN, UVAL, TP, ITERS = 16, 7, 7, 8.0, -0.3, 200
+TP = -0.3
+# the sectors the benchmark solves: name -> (L, hopping builder, U, N_up, N_dn, Lanczos steps, description)
+WORKLOADS = {
+    "hubbard_ring18_mixed_lanczos": (18, lambda S: S.chain(18), 4.0, 9, 9, 150, "18-site ring, PBC, t=1"),
+    "hubbard_4x4_tp_mixed_lanczos": (16, lambda S: S.square(4, 4, 1.0, TP), 8.0, 7, 7, 200,
+                                     "4x4 torus, t=1, t'=-0.3"),
+}
+WORKLOAD = "hubbard_ring18_mixed_lanczos"
+L, _HF, UVAL, NUP, NDN, ITERS, _DESC = WORKLOADS[WORKLOAD]
 # time-to-1e-9 runs: the Ritz sum drops trailing coefficients of norm <= 1e-6,
 # which moves the refined energy by ~1e-12 times the spectral spread (the
 # achieved error is reported beside each time); the timed steps sum every term
 RITZ_TAIL = 1e-6
+# peak of the L2-to-SM path derived from ncu counters of the spin-down gather
+# on the 4x4 sector: 21.45 TB/s of sectors delivered to L1 at 91.23 % of peak
+L2_TO_SM_PEAK_GBS = 21450.0 / 0.9123
 
 
 def peaks():
@@ -94,9 +109,10 @@ class Clocks:
                 "reasons": reasons, "samples": len(self.samples)}
 
 
-def model():
+def model(workload: str = WORKLOAD):
     import gbr_synth as S
-    return S.square(4, 4, 1.0, TP), S.uniform_U(L, UVAL)
+    Lw, hf, Uv, _, _, _, _ = WORKLOADS[workload]
+    return hf(S), S.uniform_U(Lw, Uv)
 
 
 def src_hash():
@@ -175,7 +191,7 @@ def oracle_sample(seconds: float):
             break
         n = min(D - r0, int(n * max(2.0, 1.2 * seconds / max(dt, 1e-3))))
     elems = oracle.count_elements(L, h, NUP, NDN, r0, r0 + n)
-    desc = (f"rows [{r0}, {r0 + n}) of the 4x4 sector: {elems} matrix elements by literal operator "
+    desc = (f"rows [{r0}, {r0 + n}) of the {WORKLOAD} sector: {elems} matrix elements by literal operator "
             f"application (Eq. cee) with bisection ranking, single thread, {dt:.1f} s")
     return elems / dt, desc, dt
 
@@ -223,7 +239,7 @@ class OraclePool:
         res = self.pool.map(_oracle_rows, jobs)
         wall = time.perf_counter() - t0
         elems = sum(e for e, _ in res)
-        desc = (f"rows [{r0}, {r0 + n * self.workers}) of the 4x4 sector in {self.workers} blocks of {n}, one per "
+        desc = (f"rows [{r0}, {r0 + n * self.workers}) of the {WORKLOAD} sector in {self.workers} blocks of {n}, one per "
                 f"worker process: {elems} matrix elements by literal operator application (Eq. cee) with bisection "
                 f"ranking, {wall:.1f} s wall")
         return elems / wall, desc
@@ -249,7 +265,7 @@ def run_reference(args, rank: int):
     line = {"metric": METRIC, "value": v, "unit": UNIT, "impl": "reference", "n_gpus": 0, "steps": args.steps,
             "warmup": args.warmup, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
             "dtype": "f64", "data": "synthetic",
-            "config": {"workload": WORKLOAD, "dim": math.comb(16, 7) ** 2},
+            "config": {"workload": WORKLOAD, "dim": math.comb(L, NUP) * math.comb(L, NDN)},
             "cpu_baseline": {"value": v, "unit": UNIT, "cores": pool.workers, "kind": "oracle", "sample": descs[-1]},
             "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
@@ -413,30 +429,9 @@ def config_extras(G, torch):
         checks.append(abs(b["E0"][int(m)] - best) / max(1.0, abs(best)))
     out["siam256_batch"] = {"models": 256, "sectors": ns, "states": nst, "seconds": dt, "sectors_per_s": ns / dt,
                             "max_rel_err_sampled_models": max(checks)}
-    # L=18 ring, U=4, half filling: mixed (150 steps, FP64 refinement) vs all-FP64
-    h18, U18 = S.chain(18), S.uniform_U(18, 4.0)
-    H18 = G.gbr_ham_create(18, h18, U18, 9, 9)
-    D18, el18 = G.gbr_ham_info(H18)
-    s18 = SG.uniform(S.SEED_START, D18)
-    rm = G.gbr_lanczos(H18, s18, 150, prec=G.GBR_PREC_MIXED, refine=True, store_basis=-1)
-    rd = G.gbr_lanczos(H18, s18, 150, prec=G.GBR_PREC_FP64, refine=False, store_basis=0)
-    # time to 1e-9: both stop on the residual test (tol 1e-6 of the spectral scale)
-    rmt = G.gbr_lanczos(H18, s18, 150, prec=G.GBR_PREC_MIXED, refine=True, store_basis=-1, tol=1e-6,
-                        ritz_tail=RITZ_TAIL)
-    rdt = G.gbr_lanczos(H18, s18, 150, prec=G.GBR_PREC_FP64, refine=False, store_basis=0, tol=1e-6)
-    out["chain18_mixed_vs_fp64"] = {"dim": D18, "elements_per_hv": el18, "mixed_E0": rm["E0"], "mixed_s": rm["seconds"],
-                                    "mixed_basis": "stored" if rm["stored_basis"] else "recomputed",
-                                    "fp64_E0": rd["E0"], "fp64_s": rd["seconds"],
-                                    "rel_diff": abs(rm["E0"] - rd["E0"]) / abs(rd["E0"]),
-                                    "speedup_mixed_over_fp64": rd["seconds"] / rm["seconds"],
-                                    "to_1e-9": {"mixed_s": rmt["seconds"], "mixed_iters": rmt["iters"],
-                                                "mixed_rel_err": abs(rmt["E0"] - rd["E0"]) / abs(rd["E0"]),
-                                                "mixed_ritz_terms": rmt["ritz_terms"],
-                                                "fp64_s": rdt["seconds"], "fp64_iters": rdt["iters"],
-                                                "fp64_rel_err": abs(rdt["E0"] - rd["E0"]) / abs(rd["E0"]),
-                                                "speedup": rdt["seconds"] / rmt["seconds"]},
-                                    "E0_U0_closed_form": ref["chain18_U0_N9_9_free_E0"]}
-    del s18, H18
+    # 4x4 t' torus, U=8, N_up = N_dn = 7: mixed (200 steps, stored basis, FP64
+    # refinement) vs all-FP64, both to 1e-9 of the 200-step FP64 energy
+    out["hubbard_4x4_tp_mixed_lanczos"] = square_extras(G, torch)
     torch.cuda.empty_cache()
     # every S_z of the 12-site ring at 12 particles, ranked by a packed trie
     h12, U12 = S.chain(12), S.uniform_U(12, 4.0)
@@ -485,14 +480,63 @@ def config_extras(G, torch):
     return out
 
 
-def ranking_sweep(G, torch):
+def square_extras(G, torch):
+    import gbr_synth as S
+    import gbr_synth.gpu as SG
+    name = "hubbard_4x4_tp_mixed_lanczos"
+    Lq, hf, Uv, Nu, Nd, iters, desc = WORKLOADS[name]
+    H = G.gbr_ham_create(Lq, hf(S), S.uniform_U(Lq, Uv), Nu, Nd)
+    D, elems = G.gbr_ham_info(H)
+    G.gbr_ham_tune(H, 32)
+    G.gbr_ham_tune(H, 64)
+    s = SG.uniform(S.SEED_START, D)
+    def run(**kw):
+        opts = {"refine": True, "store_basis": -1}
+        opts.update(kw)
+        return G.gbr_lanczos(H, s, iters, **opts)
+
+    run(prec=G.GBR_PREC_MIXED)
+    rm = run(prec=G.GBR_PREC_MIXED)
+    rg = run(prec=G.GBR_PREC_MIXED, use_graph=True)
+    rd = run(prec=G.GBR_PREC_FP64, refine=False)
+    rmt = run(prec=G.GBR_PREC_MIXED, tol=1e-6, ritz_tail=RITZ_TAIL)
+    rdt = G.gbr_lanczos(H, s, iters, prec=G.GBR_PREC_FP64, refine=False, store_basis=0, tol=1e-6)
+    rp = run(prec=G.GBR_PREC_MIXED, profile=True)
+    ref = rd["E0"]
+    out = {"lattice": desc, "dim": D, "elements_per_hv": elems, "iters": iters,
+           "gather_shape": G.gbr_ham_get_shape(H, 32),
+           "mixed_E0": rm["E0"], "mixed_s": rm["seconds"], "mixed_graph_s": rg["seconds"],
+           "mixed_elements_per_s": elems * hv_count(rm) / rm["seconds"],
+           "fp64_E0": rd["E0"], "fp64_s": rd["seconds"], "rel_diff": abs(rm["E0"] - ref) / abs(ref),
+           "speedup_mixed_over_fp64": rd["seconds"] / rm["seconds"],
+           "to_1e-9": {"mixed_s": rmt["seconds"], "mixed_iters": rmt["iters"],
+                       "mixed_rel_err": abs(rmt["E0"] - ref) / abs(ref), "fp64_s": rdt["seconds"],
+                       "fp64_iters": rdt["iters"], "fp64_rel_err": abs(rdt["E0"] - ref) / abs(ref),
+                       "speedup": rdt["seconds"] / rmt["seconds"]},
+           "roofline": stage_roofline(rp, D, elems, G),
+           "hv_paths": hv_path_extras(G, torch, H, s)}
+    H.close()
+    del s
+    G.gbr_release_cache()
+    return out
+
+
+def next3_extras(G, torch):
+    """A bounded part of the filling sweep (Sec. V-A) and of the per-state
+    H·v timings (Sec. V-B, quarter filling at M = 24 and 32, half at 24), so
+    that the default run reports the low-filling regime."""
+    return {"ranking_sweep_M28": ranking_sweep(G, torch, Ns=(2, 7, 14), n=1 << 24),
+            "eig_timings": eig_timings(G, torch, cases=(("quarter", (24, 32)), ("half", (24,))))}
+
+
+def ranking_sweep(G, torch, Ns=(1, 2, 5, 9, 14, 19, 23, 26, 27), n=1 << 26):
     """Analog of the paper's ranking microbenchmark (Sec. V-A: M = 28, every
     filling, states drawn with replacement and sorted): staggered, trie and
     bisection ranks/s on 2^26 queries per sector, sorted and unsorted."""
     import numpy as np
     import gbr_synth as S
     import gbr_synth.gpu as SG
-    M, n = 28, 1 << 26
+    M = 28
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     rows = []
 
@@ -505,7 +549,7 @@ def ranking_sweep(G, torch):
         torch.cuda.synchronize()
         return e0.elapsed_time(e1) / reps / 1e3
 
-    for N in (1, 2, 5, 9, 14, 19, 23, 26, 27):
+    for N in Ns:
         D = math.comb(M, N)
         members = S.popcount_states(M, N)
         c = G.gbr_comb_create(M, N, 8)
@@ -526,7 +570,7 @@ def ranking_sweep(G, torch):
     return rows
 
 
-def eig_timings(G, torch):
+def eig_timings(G, torch, cases=(("half", range(4, 33, 4)), ("quarter", (8, 16, 24, 32)))):
     """Analog of the paper's Fig. eig-timings (Sec. V-B): one H·v of the open
     Hubbard chain of Eq. Hring (t = 1, U = 4) per ranking strategy, as time
     per state and per spin-orbital (ns), for S_z = 0 at half filling
@@ -549,8 +593,8 @@ def eig_timings(G, torch):
         torch.cuda.synchronize()
         return e0.elapsed_time(e1) / reps / 1e3
 
-    out = {"half": [], "quarter": []}
-    for filling, Ms in (("half", range(4, 33, 4)), ("quarter", (8, 16, 24, 32))):
+    out = {filling: [] for filling, _ in cases}
+    for filling, Ms in cases:
         for M in Ms:
             L = M // 2
             Ns = L // 2 if filling == "half" else L // 4
@@ -591,6 +635,46 @@ def eig_timings(G, torch):
     return out
 
 
+def hv_count(r) -> int:
+    """H·v calls one solve ran: the recurrence, the second run of it for the
+    Ritz vector when the basis was not stored, and the FP64 refinement."""
+    n = r["iters"]
+    if not r["stored_basis"]:
+        n += max(r["ritz_terms"] - 1, 0)
+    return n + 1
+
+
+def stage_roofline(r, D: int, elems: int, G):
+    """Roofline of the FP32 H·v as the Lanczos launches it, from a profiled
+    solve (CUDA events at the stage boundaries of every H·v on the launching
+    stream): hop lists, spin-down gather, spin-up gather with diagonal,
+    combine and the fused first update; the transpose runs only in the first
+    step (the update writes X^T for the next one)."""
+    import numpy as np
+    st = np.asarray(r["stage_seconds"], dtype=np.float64)
+    nl = np.asarray(r["stage_launches"], dtype=np.float64)
+    names = ["k_hop_lists", "k_transpose", "k_gather_dn", "k_gather_up_combine"]
+    per = st / np.maximum(nl, 1)
+    t_hv = float(per[0] + per[2] + per[3])
+    hbm, src = peaks()
+    alg = 2 * D * 4                               # read x, write y (FP32)
+    achieved = alg / t_hv / 1e9
+    k = int(np.argmax(st))
+    onchip = (elems - D) * 4                      # one 4-byte gather per off-diagonal matrix element
+    return {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s", "frac": achieved / hbm,
+            "traffic": None, "kernel": "fp32_hv (hop lists + spin-down gather + spin-up gather with combine)",
+            "peak_source": src, "avg_launch_ms": t_hv * 1e3, "algorithmic_bytes_per_launch": alg,
+            "timing": "profiled solve outside the timed steps, CUDA events per stage on the launching stream",
+            "dominant_kernel": {"name": names[k], "avg_launch_ms": float(per[k] * 1e3),
+                                "frac_of_hbm": alg / per[k] / 1e9 / hbm},
+            "stage_ms": {names[i]: float(per[i] * 1e3) for i in range(4)},
+            "stage_share": {names[i]: float(st[i] / max(st.sum(), 1e-30)) for i in range(4)},
+            "onchip": {"bound": "l2_to_sm", "achieved": onchip / t_hv / 1e9, "peak": L2_TO_SM_PEAK_GBS,
+                       "unit": "GB/s", "frac": onchip / t_hv / 1e9 / L2_TO_SM_PEAK_GBS,
+                       "bytes_per_launch": onchip,
+                       "note": "4 bytes of x gathered per off-diagonal matrix element"}}
+
+
 def run_ours(args, rank: int, world: int):
     import numpy as np
     import torch
@@ -608,19 +692,19 @@ def run_ours(args, rank: int, world: int):
     H = G.gbr_ham_create(L, h, U, NUP, NDN)
     D, elems = G.gbr_ham_info(H)
     s = SG.uniform(S.SEED_START, D)
-    # the library's autotuner picks the gather tiles (untimed set-up)
+    # the library's autotuner picks the gather family and tiles (untimed set-up)
     G.gbr_ham_tune(H, 32)
     G.gbr_ham_tune(H, 64)
 
-    def solve(prec=G.GBR_PREC_MIXED, profile=True, refine=True):
-        return G.gbr_lanczos(H, s, ITERS, prec=prec, refine=refine, store_basis=-1, profile=profile)
+    def solve(prec=G.GBR_PREC_MIXED, refine=True, **kw):
+        return G.gbr_lanczos(H, s, ITERS, prec=prec, refine=refine, store_basis=-1, **kw)
 
     def barrier():
         ranks_barrier(world)
         torch.cuda.synchronize()
 
     for _ in range(args.warmup):
-        solve()
+        solve(use_graph=True)
     barrier()
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     n0 = G.gbr_launch_count()
@@ -629,95 +713,76 @@ def run_ours(args, rank: int, world: int):
         barrier()
         e0.record()
         for _ in range(args.steps):
-            results.append(solve())
+            results.append(solve(use_graph=True))
         e1.record()
         barrier()
     launches = G.gbr_launch_count() - n0
     t = max_over_ranks(e0.elapsed_time(e1) / 1e3, world, device="cuda")
-    iters_done = results[-1]["iters"]
-    elems_step = elems * (iters_done + 1)        # FP32 H·v per step plus the FP64 refinement H·v
-    value = aggregate_rate(elems_step, args.steps, world, t)
+    nhv = hv_count(results[-1])
+    value = aggregate_rate(elems * nhv, args.steps, world, t)
+    # stage times from one profiled solve (eager launches, events per stage)
+    rp = solve(profile=True)
+    roofline = stage_roofline(rp, D, elems, G)
+    shape = G.gbr_ham_get_shape(H, 32)
+    E_ref = reference_energies()["chain18_U4_N9_9_bethe_E0"]
+    E0 = results[-1]["E0"]
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": t / args.steps * 1e3, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32+f64", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "lattice": _DESC, "U": UVAL, "N_up": NUP, "N_dn": NDN, "dim": D,
+                       "elements_per_hv": elems, "lanczos_iters": ITERS, "hv_per_step": nhv,
+                       "precision": "FP32 vectors and H·v, FP64-grade dots, FP64 tridiagonal and Rayleigh quotient",
+                       "basis": "stored" if results[-1]["stored_basis"] else "recomputed (second run of the recurrence)",
+                       "cuda_graphs": True, "gather_shape": shape,
+                       "l2": "inputs larger than L2 (9.5 GB FP32 vectors)", "parallelism": f"replicas{world}"},
+            "clocks": clk.summary(), "gpu_launches": int(launches), "roofline": roofline,
+            "E0": E0, "E0_bethe_ansatz": E_ref, "E0_rel_err": abs(E0 - E_ref) / abs(E_ref),
+            "residual": results[-1]["residual"]}
 
-    # dominant kernel from the live per-stage event timings
-    st = np.sum([r["stage_seconds"] for r in results], axis=0)
-    nl = np.sum([r["stage_launches"] for r in results], axis=0)
-    path = G.gbr_ham_get_path(H)
-    # algorithmic bytes of each kernel's own function: transpose reads and
-    # writes a vector; the spin-down gather reads X^T once and writes Z^T;
-    # the spin-up gather as launched by the Lanczos reads X once, Z^T and
-    # v_{k-1} (fused first update) and writes w
-    names = ["k_hop_lists", "k_transpose", "k_gather_dn", "k_gather_up_combine"]
-    bytes_per = [0, 2 * D * 4, 2 * D * 4, 4 * D * 4]
-    k = int(np.argmax(st))
-    avg = st[k] / max(nl[k], 1)
-    hbm, src = peaks()
-    achieved = bytes_per[k] / avg / 1e9
-    roofline = {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s", "frac": achieved / hbm,
-                "traffic": ncu_traffic(names[k]), "kernel": names[k], "peak_source": src,
-                "avg_launch_ms": avg * 1e3,
-                "algorithmic_bytes_per_launch": bytes_per[k],
-                "stage_share": {names[i]: float(st[i] / st.sum()) for i in range(4)},
-                "hv_path": {G.GBR_HV_FUSED: "fused", G.GBR_HV_FACTORED: "factored"}.get(path, str(path))}
-
-    # end to end through the public API with host buffers
+    # end to end through the public API with host buffers: handle creation,
+    # the FP64 start vector from pinned host memory, the solve, E0 back
+    H.close()
+    G.gbr_release_cache()
+    torch.cuda.empty_cache()
     s_host = s.cpu().pin_memory()
+    del s
+    torch.cuda.empty_cache()
     e2e_t = []
-    for i in range(max(2, min(args.steps, 3))):
+    for i in range(2):
         barrier()
         t0 = time.perf_counter()
         H2 = G.gbr_ham_create(L, h, U, NUP, NDN)
         s_dev = s_host.to("cuda", non_blocking=True)
-        r2 = G.gbr_lanczos(H2, s_dev, ITERS, prec=G.GBR_PREC_MIXED, refine=True, store_basis=-1)
+        r2 = G.gbr_lanczos(H2, s_dev, ITERS, prec=G.GBR_PREC_MIXED, refine=True, store_basis=-1, use_graph=True)
         _ = r2["E0"]
         H2.close()
         del s_dev
         torch.cuda.synchronize()
         e2e_t.append(time.perf_counter() - t0)
-    e2e_v = elems * (r2["iters"] + 1) / statistics.median(e2e_t)
-
-    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
-            "warmup": args.warmup, "ms_per_step": t / args.steps * 1e3, "higher_is_better": True,
-            "scaling": "weak", "vs_baseline": None, "dtype": "f32+f64", "data": "synthetic",
-            "config": {"workload": WORKLOAD, "lattice": "4x4 torus", "t": 1.0, "tp": TP, "U": UVAL,
-                       "N_up": NUP, "N_dn": NDN, "dim": D, "elements_per_hv": elems, "lanczos_iters": ITERS,
-                       "precision": "FP32 vectors and H·v, FP64-grade dots, FP64 tridiagonal and Rayleigh quotient",
-                       "basis": "stored" if results[-1]["stored_basis"] else "recomputed",
-                       "l2": "inputs larger than L2 (0.52 GB FP32 vectors)", "parallelism": f"replicas{world}"},
-            "clocks": clk.summary(), "gpu_launches": int(launches), "roofline": roofline,
-            "e2e": {"value": e2e_v, "unit": UNIT, "h2d_bytes_per_step": D * 8,
-                    "d2h_bytes_per_step": 8 * (2 * ITERS + 8)},
-            "E0": results[-1]["E0"], "residual": results[-1]["residual"]}
-
+    e2e_v = elems * hv_count(r2) / statistics.median(e2e_t)
+    line["e2e"] = {"value": e2e_v, "unit": UNIT, "h2d_bytes_per_step": D * 8,
+                   "d2h_bytes_per_step": 8 * (2 * ITERS + 8),
+                   "note": "untuned handle (default gather shape), created inside the timed region"}
     if rank == 0 and not args.no_extras:
-        r64 = solve(prec=G.GBR_PREC_FP64, profile=False, refine=False)
-        rm = results[-1]
-        # time to |dE0|/|E0| <= 1e-9: both precisions stop on the residual test
-        # (tol 1e-6 of the spectral scale); the reference is the 200-step FP64 run
-        rmt = G.gbr_lanczos(H, s, ITERS, prec=G.GBR_PREC_MIXED, refine=True, store_basis=-1, tol=1e-6,
-                            ritz_tail=RITZ_TAIL)
-        r6t = G.gbr_lanczos(H, s, ITERS, prec=G.GBR_PREC_FP64, refine=False, store_basis=0, tol=1e-6)
-        ref = r64["E0"]
-        line["lanczos"] = {"mixed_E0": rm["E0"], "mixed_s": rm["seconds"], "fp64_E0": r64["E0"],
-                           "fp64_s": r64["seconds"], "rel_diff": abs(rm["E0"] - r64["E0"]) / abs(r64["E0"]),
-                           "speedup_mixed_over_fp64": r64["seconds"] / rm["seconds"],
-                           "to_1e-9": {"mixed_s": rmt["seconds"], "mixed_iters": rmt["iters"],
-                                       "mixed_rel_err": abs(rmt["E0"] - ref) / abs(ref),
-                                       "mixed_ritz_terms": rmt["ritz_terms"],
-                                       "fp64_s": r6t["seconds"], "fp64_iters": r6t["iters"],
-                                       "fp64_rel_err": abs(r6t["E0"] - ref) / abs(ref),
-                                       "speedup": r6t["seconds"] / rmt["seconds"]}}
-        line["hv_paths"] = hv_path_extras(G, torch, H, s)
         try:
-            line["ranking"] = ranking_extras(G, torch)
+            line["lanczos"] = precision_extras(G, torch, s_host)
         except Exception as ex:  # report rather than hide
-            line["ranking"] = {"error": repr(ex)}
-        H.close()
-        G.gbr_release_cache()          # the 4x4 basis; the L = 18 ring needs the memory
-        torch.cuda.empty_cache()
+            line["lanczos"] = {"error": repr(ex)}
+    del s_host
+    torch.cuda.empty_cache()
+    if rank == 0 and not args.no_extras:
         try:
             line["configs"] = config_extras(G, torch)
         except Exception as ex:
             line["configs"] = {"error": repr(ex)}
+        try:
+            line["ranking"] = ranking_extras(G, torch)
+        except Exception as ex:
+            line["ranking"] = {"error": repr(ex)}
+        try:
+            line["next3"] = next3_extras(G, torch)
+        except Exception as ex:
+            line["next3"] = {"error": repr(ex)}
     if rank == 0 and world == 1 and not args.no_cpu:
         v1, desc1, _ = oracle_sample(args.cpu_seconds / 3)
         pool = OraclePool()
@@ -729,19 +794,65 @@ def run_ours(args, rank: int, world: int):
         print(json.dumps(line), flush=True)
 
 
-def profile_hv(n: int):
-    """A few FP32 H·v calls on the benchmark sector (no timing, no output):
-    the target of the ncu captures summarised under profiles/."""
+def precision_extras(G, torch, s_host):
+    """Mixed vs FP64 on the benchmark sector: the 150-step FP64 solve, and both
+    precisions' time to |dE0|/|E0| <= 1e-9 (residual stop), against the
+    Bethe-ansatz energy."""
+    h, U = model()
+    H = G.gbr_ham_create(L, h, U, NUP, NDN)
+    G.gbr_ham_tune(H, 32)
+    G.gbr_ham_tune(H, 64)
+    s = s_host.to("cuda")
+    E_ref = reference_energies()["chain18_U4_N9_9_bethe_E0"]
+    rd = G.gbr_lanczos(H, s, ITERS, prec=G.GBR_PREC_FP64, refine=False, store_basis=0, use_graph=True)
+    rm = G.gbr_lanczos(H, s, ITERS, prec=G.GBR_PREC_MIXED, refine=True, store_basis=-1, use_graph=True)
+    rmt = G.gbr_lanczos(H, s, ITERS, prec=G.GBR_PREC_MIXED, refine=True, store_basis=-1, tol=1e-6,
+                        ritz_tail=RITZ_TAIL, use_graph=True)
+    rdt = G.gbr_lanczos(H, s, ITERS, prec=G.GBR_PREC_FP64, refine=False, store_basis=0, tol=1e-6, use_graph=True)
+    H.close()
+    del s
+    torch.cuda.empty_cache()
+    rel = lambda E: abs(E - E_ref) / abs(E_ref)
+    return {"E0_bethe_ansatz": E_ref,
+            "mixed_E0": rm["E0"], "mixed_s": rm["seconds"], "mixed_rel_err": rel(rm["E0"]),
+            "fp64_E0": rd["E0"], "fp64_s": rd["seconds"], "fp64_rel_err": rel(rd["E0"]),
+            "speedup_mixed_over_fp64": rd["seconds"] / rm["seconds"],
+            "to_1e-9": {"mixed_s": rmt["seconds"], "mixed_iters": rmt["iters"], "mixed_rel_err": rel(rmt["E0"]),
+                        "mixed_ritz_terms": rmt["ritz_terms"],
+                        "fp64_s": rdt["seconds"], "fp64_iters": rdt["iters"], "fp64_rel_err": rel(rdt["E0"]),
+                        "speedup": rdt["seconds"] / rmt["seconds"]}}
+
+
+PROFILE_SECTORS = {
+    # name: (L, hopping, U, N_up, N_dn)
+    "sq4x4": (16, lambda S: S.square(4, 4, 1.0, TP), 8.0, 7, 7),
+    "ring16": (16, lambda S: S.chain(16), 4.0, 8, 8),
+    "ring18": (18, lambda S: S.chain(18), 4.0, 9, 9),
+    # the 18-site ring's spin-up rows (48,620 states, ~9.5 hops) with 3,060 columns (N_dn = 4): 0.6 GB vectors
+    "ring18_dn4": (18, lambda S: S.chain(18), 4.0, 9, 4),
+}
+
+
+def profile_hv(n: int, sector: str = "sq4x4", shape: str = "", fp: int = 32):
+    """A few H·v calls on one sector with a given launch shape (no timing,
+    no output): the target of the ncu captures summarised under profiles/.
+    shape: "window,rows_dn,rows_up,rows_lz" for gbr_ham_set_shape, or empty
+    for the handle's default."""
     import torch
     import __graft_entry__
     __graft_entry__.build()
     import gbr_synth as S
     import gbr_synth.gpu as SG
     import paper_2203_04158_gb300 as G
-    h, U = model()
-    H = G.gbr_ham_create(L, h, U, NUP, NDN)
+    Ls, hf, Uv, Nu, Nd = PROFILE_SECTORS[sector]
+    H = G.gbr_ham_create(Ls, hf(S), S.uniform_U(Ls, Uv), Nu, Nd)
+    G.gbr_ham_set_path(H, G.GBR_HV_FACTORED)
+    if shape:
+        G.gbr_ham_set_shape(H, fp, *[int(v) for v in shape.split(",")])
     D, _ = G.gbr_ham_info(H)
-    x = SG.uniform(S.SEED_START, D).float()
+    x = SG.uniform(S.SEED_START, D)
+    if fp == 32:
+        x = x.float()
     y = torch.empty_like(x)
     for _ in range(n):
         G.gbr_hv(H, x, y)
@@ -814,10 +925,13 @@ def main():
                     help="print the per-state H·v times of every ranking strategy on the open chain "
                          "(half and quarter filling, M = 4..32) as JSON and exit")
     ap.add_argument("--profile-hv", type=int, default=0,
-                    help="run this many FP32 H·v calls on the workload sector and exit (for ncu captures)")
+                    help="run this many H·v calls on --profile-sector and exit (for ncu captures)")
+    ap.add_argument("--profile-sector", default="sq4x4", choices=sorted(PROFILE_SECTORS))
+    ap.add_argument("--profile-shape", default="", help="launch shape window,rows_dn,rows_up,rows_lz")
+    ap.add_argument("--profile-fp", type=int, default=32, choices=[32, 64])
     args = ap.parse_args()
     if args.profile_hv:
-        profile_hv(args.profile_hv)
+        profile_hv(args.profile_hv, args.profile_sector, args.profile_shape, args.profile_fp)
         return
     if args.profile_rank:
         profile_rank(args.profile_rank)

@@ -241,7 +241,9 @@ int gbr_hv_static(const gbr_ham *H, const void *d_x, void *d_y, int fp, void *st
  *   stage 1: rank the per-spin hop lists (unrank, hop, sign, staggered or
  *            combinadics rank) into the handle's tables (x, y unused);
  *   stage 2: X^T into the handle's scratch (y unused);
- *   stage 3: Z^T = H_dn X^T into the handle's scratch (x, y unused);
+ *   stage 3: Z = X H_dn^T into the handle's scratch, computed as the row
+ *            gathers H_dn X^T (x, y unused); stored transposed with the
+ *            plain gathers, row-major with the windowed ones;
  *   stage 4: y = H_up X + Dg o X + Z (row gathers, diagonal, combine).
  * Calling 1..4 in order on one stream equals gbr_hv with the factored path.
  * Arguments as for gbr_hv; the handle's scratch (two vectors of dim
@@ -269,10 +271,48 @@ int gbr_check_rcp64(int64_t n, double *h_max_rel_err);
  * plus, for replayed CUDA graphs, the kernels each replay runs). */
 int64_t gbr_launch_count(void);
 
-/* Auto-tunes the H·v launch shape (threads, tiles) for precision fp on this
- * device by timing the candidates on scratch vectors; the choice is kept in
- * the handle.  Synchronises the stream. */
+/* Auto-tunes the H·v launch shape for precision fp on this device by timing
+ * the candidates on scratch vectors; the choice is kept in the handle: the
+ * path (fused or factored), the gather family of the factored path (plain
+ * row gathers, or windowed gathers that stage each CTA's own rows in shared
+ * memory), the rows per CTA of each gather pass in that family, and those of
+ * the spin-up pass as the Lanczos launches it.  Synchronises the stream. */
 int gbr_ham_tune(gbr_ham *H, int fp, void *stream);
+
+/* Launch shape of the H·v for precision fp: the knobs gbr_ham_tune sets,
+ * exposed for tests and experiments (the paper has no counterpart).
+ * h_shape: 6 ints (host).
+ *   [0]: 1 = windowed row gathers in the factored path (each CTA copies its
+ *     TR own rows of a 512-byte column slice into shared memory with bulk
+ *     copies, serves the hops that stay inside them from there, and the
+ *     spin-down pass keeps its product row-major), 0 = plain row gathers;
+ *   [1..3]: rows per CTA of the spin-down pass, the spin-up pass and the
+ *     spin-up pass with the fused Lanczos update (plain: 4, 8 or 16;
+ *     windowed: 32 or 64; 0 = default);
+ *   [4]: chunk width R of the per-spin staggered tables (Fig. fastrank):
+ *     8 or 4 (0 = 8); the paper compares both inside the H·v (Sec. V-B);
+ *   [5]: threads per state of the fused per-element kernel: 1, 2 or 4
+ *     (0 = 1); the threads of a state split its occupied sites.
+ * In the factored path every element sums its hops in the same order under
+ * every value of [0..4], so gbr_hv's results do not depend on them; [5]
+ * changes the summation order of the fused kernel (a fixed butterfly).
+ * The windowed family needs per-spin dimensions whose rows are whole 16-byte
+ * packs (gbr_ham_get_shape reports 0 otherwise) and 16-byte aligned vectors
+ * (a combine pass on other vectors runs the plain kernel).  Errors:
+ * GBR_EINVAL for NULL arguments, fp other than 32 or 64, or values outside
+ * the lists above. */
+int gbr_ham_set_shape(gbr_ham *H, int fp, const int *h_shape);
+/* The shape gbr_hv uses for precision fp (h_shape: 6 ints, as above). */
+int gbr_ham_get_shape(const gbr_ham *H, int fp, int *h_shape);
+
+/* Device status word of the library's kernels on the current device (the
+ * paper has no counterpart).  Kernels that wait on an mbarrier for their own
+ * bulk copies bound the wait (about a second); when it runs out they set bit
+ * 0 here and return without computing, instead of trapping or hanging.
+ * *status receives the word; clear = 1 resets it.  Returns GBR_ETIMEOUT if
+ * the word is non-zero, else GBR_OK (GBR_ECUDA if it cannot be read).
+ * Synchronous with respect to the device. */
+int gbr_device_status(int clear, int *status);
 
 /* ------------------------------------------------------------------------
  * The same Hamiltonians on an arbitrary sorted set of 2L-bit states, ranked
@@ -426,6 +466,24 @@ typedef struct {
 int gbr_lanczos(const gbr_ham *H, const gbr_lanczos_opts *opts, const double *d_v0, gbr_lanczos_result *res,
                 double *h_alpha, double *h_beta, double *h_ritz, void *stream);
 
+/* The same Lanczos solve with the trie-ranked H·v of a set Hamiltonian as
+ * the operator (Sec. IV: a state set cut by further quantum numbers, ranked
+ * by a packed trie; the ground state of, e.g., one S_z sector or one
+ * symmetry-cut subset).  The operator is gbr_setham_hv with the membership
+ * check on, so a set that H does not map into itself gets the projection
+ * P H P.  d_v0: dim doubles (the set's size); arguments, precision paths,
+ * refinement and errors as for gbr_lanczos (stage_seconds stay zero). */
+int gbr_setham_lanczos(const gbr_setham *S, const gbr_lanczos_opts *opts, const double *d_v0,
+                       gbr_lanczos_result *res, double *h_alpha, double *h_beta, double *h_ritz, void *stream);
+
+/* The same Lanczos solve with the term-list H·v (Appendix: Eqs. Talpha2 and
+ * Fig. mul; Sec. V-C, Eq. Hk for the momentum-basis ring) as the operator,
+ * with the membership check on.  The term list must make a symmetric
+ * operator on the set (every term with its adjoint, real coefficients):
+ * Lanczos assumes it.  Arguments and errors as for gbr_lanczos. */
+int gbr_termham_lanczos(const gbr_termham *T, const gbr_lanczos_opts *opts, const double *d_v0,
+                        gbr_lanczos_result *res, double *h_alpha, double *h_beta, double *h_ritz, void *stream);
+
 /* ------------------------------------------------------------------------
  * Batched ground states of many small models, every (N_up, N_dn) sector,
  * in one persistent launch (the impurity-solver use case of Sec. I and VI).
@@ -453,10 +511,27 @@ int gbr_batch_layout(int n_models, const gbr_model_desc *models, int64_t *n_sect
  *            be NULL); ties within 1e-10 |E| go to the lower N_up + N_dn,
  *            then the lower N_up;
  *   h_sector_E (host, may be NULL): n_sectors refined sector energies.
- * Synchronises the stream. Errors: GBR_EINVAL, GBR_ENOMEM, GBR_ECUDA,
- * GBR_ETIMEOUT (a bounded wait on the work queue ran out). */
+ * The work queue is an atomic counter: no CTA waits on another.
+ * Synchronises the stream. Errors: GBR_EINVAL, GBR_ENOMEM, GBR_ECUDA. */
 int gbr_batch_solve(int n_models, const gbr_model_desc *models, const double *d_start, int iters, double *h_E0,
                     int *h_arg, double *h_sector_E, void *stream);
+
+/* Launch shape of gbr_batch_solve (process-wide; the paper has no
+ * counterpart): threads per CTA (128, 256 or 512) and CTAs per SM
+ * (0 = as many as the shared memory and registers allow, else at most that
+ * many).  Every shape gives the same sector energies up to FP rounding of
+ * the block reductions.  Errors: GBR_EINVAL for other values. */
+int gbr_batch_set_shape(int threads, int ctas_per_sm);
+int gbr_batch_get_shape(int *threads, int *ctas_per_sm);
+
+/* Auto-tunes the batch solver's launch shape on this batch: solves it with
+ * every candidate (threads 128, 256, 512 x CTAs per SM as many as fit, 2, 1),
+ * times each whole launch with CUDA events, keeps the fastest as the
+ * process-wide shape and returns it in h_shape[2] (threads, CTAs per SM);
+ * h_ms (host, may be NULL) receives the 9 times in that order.  Arguments as
+ * for gbr_batch_solve.  Synchronises the stream. */
+int gbr_batch_tune(int n_models, const gbr_model_desc *models, const double *d_start, int iters, int *h_shape,
+                   float *h_ms, void *stream);
 
 #ifdef __cplusplus
 }

@@ -20,7 +20,7 @@
 
 namespace gbr {
 
-constexpr int kBatchThreads = 256;
+constexpr int kBatchThreads = 256;   // default CTA size of the batch solver
 constexpr int kBatchMaxL = 10;
 
 struct SectorDesc {
@@ -165,7 +165,12 @@ struct BatchSmem {
 // and the tridiagonal solver's work (global memory; each CTA reuses its own
 // slot, which stays in L2), so that the shared memory holds only the FP32
 // recurrence and three CTAs fit on an SM.
-__global__ void __launch_bounds__(kBatchThreads, 3) k_batch(const SectorDesc *__restrict__ secs, int nsec,
+//
+// NT threads per CTA (128, 256 or 512; the autotuner's choice), at most
+// 64 K / (NT x 3 x 256 / NT) registers a thread so that three CTAs fit on an SM
+// at 256 and the register budget per SM stays the same at the other sizes.
+template <int NT>
+__global__ void __launch_bounds__(NT, (NT >= 512 ? 1 : 768 / NT)) k_batch(const SectorDesc *__restrict__ secs, int nsec,
                                                          const ModelDev *__restrict__ models,
                                                          const double *__restrict__ start, int iters, BatchSmem lay,
                                                          int *counter, double *__restrict__ outE, int *__restrict__ outK,
@@ -189,7 +194,7 @@ __global__ void __launch_bounds__(kBatchThreads, 3) k_batch(const SectorDesc *__
     double *beta = (double *)take((size_t)(kmax + 2) * 8);
     double *svec = (double *)take((size_t)(kmax + 2) * 8);
     double *work = xg + (size_t)blockIdx.x * lay.slot + 2 * (size_t)maxD;   // 3 (kmax + 2) doubles
-    __shared__ double red[kBatchThreads / 32];
+    __shared__ double red[NT / 32];
     __shared__ double hs[kBatchMaxL * kBatchMaxL];
     __shared__ double bc64[kBatchMaxL * kBatchMaxL];
     __shared__ float bc32[kBatchMaxL * kBatchMaxL];
@@ -426,9 +431,33 @@ extern "C" int gbr_batch_layout(int n_models, const gbr_model_desc *models, int6
     return GBR_OK;
 }
 
-extern "C" int gbr_batch_solve(int n_models, const gbr_model_desc *models, const double *d_start, int iters,
-                               double *h_E0, int *h_arg, double *h_sector_E, void *stream) {
-    clear_error();
+namespace gbr {
+// CTA size and CTAs per SM of the batch solver (process-wide; 0 = as many as
+// fit), set by gbr_batch_set_shape or gbr_batch_tune
+static int g_batch_threads = kBatchThreads, g_batch_per_sm = 0;
+
+template <int NT>
+static int launch_batch(int grid_req_per_sm, size_t smem, int nsec, const SectorDesc *secs, const ModelDev *md,
+                        const double *d_start, int K, const BatchSmem &lay, int *ctr, double *E, int *Kout,
+                        DevBuf &dx, cudaStream_t st, int *grid_out) {
+    auto kern = k_batch<NT>;
+    GBR_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    int per_sm = 0;
+    GBR_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, NT, smem));
+    per_sm = std::max(1, per_sm);
+    if (grid_req_per_sm > 0) per_sm = std::min(per_sm, grid_req_per_sm);
+    const int grid = std::max(1, std::min<int>(nsec, sm_count() * per_sm));
+    int rc;
+    if ((rc = dx.alloc((size_t)grid * (size_t)lay.slot * 8))) return rc;
+    kern<<<grid, NT, smem, st>>>(secs, nsec, md, d_start, K, lay, ctr, E, Kout, dx.as<double>());
+    GBR_LAUNCH_CHECK();
+    count_launches(1);
+    if (grid_out) *grid_out = grid;
+    return GBR_OK;
+}
+
+static int batch_run(int n_models, const gbr_model_desc *models, const double *d_start, int iters, double *h_E0,
+                     int *h_arg, double *h_sector_E, cudaStream_t st, int threads, int per_sm_req, float *ms_out) {
     if (n_models < 1 || !models) return set_error(GBR_EINVAL, "bad model list");
     if (!d_start || !h_E0) return set_error(GBR_EINVAL, "NULL argument");
     if (iters < 1 || iters > 4096) return set_error(GBR_EINVAL, "iters=%d out of range 1..4096", iters);
@@ -486,17 +515,31 @@ extern "C" int gbr_batch_solve(int n_models, const gbr_model_desc *models, const
     if ((rc = dE.alloc(order.size() * 8))) return rc;
     if ((rc = dK.alloc(order.size() * 4))) return rc;
     if ((rc = dctr.alloc(16))) return rc;
-    cudaStream_t st = (cudaStream_t)stream;
     GBR_CUDA_TRY(cudaMemsetAsync(dctr.p, 0, 16, st));
-    GBR_CUDA_TRY(cudaFuncSetAttribute(k_batch, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-    int per_sm = 0;
-    GBR_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_batch, kBatchThreads, smem));
-    const int grid = std::max(1, std::min<int>((int)order.size(), sm_count() * std::max(1, per_sm)));
-    if ((rc = dx.alloc((size_t)grid * (size_t)lay.slot * 8))) return rc;
-    k_batch<<<grid, kBatchThreads, smem, st>>>(dsec.as<SectorDesc>(), (int)order.size(), dmod.as<ModelDev>(), d_start,
-                                               K, lay, dctr.as<int>(), dE.as<double>(), dK.as<int>(), dx.as<double>());
-    GBR_LAUNCH_CHECK();
-    count_launches(1);
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    if (ms_out) {
+        GBR_CUDA_TRY(cudaEventCreate(&e0));
+        GBR_CUDA_TRY(cudaEventCreate(&e1));
+        cudaEventRecord(e0, st);
+    }
+    const int nsec = (int)order.size();
+    if (threads == 128)
+        rc = launch_batch<128>(per_sm_req, smem, nsec, dsec.as<SectorDesc>(), dmod.as<ModelDev>(), d_start, K, lay,
+                               dctr.as<int>(), dE.as<double>(), dK.as<int>(), dx, st, nullptr);
+    else if (threads == 512)
+        rc = launch_batch<512>(per_sm_req, smem, nsec, dsec.as<SectorDesc>(), dmod.as<ModelDev>(), d_start, K, lay,
+                               dctr.as<int>(), dE.as<double>(), dK.as<int>(), dx, st, nullptr);
+    else
+        rc = launch_batch<256>(per_sm_req, smem, nsec, dsec.as<SectorDesc>(), dmod.as<ModelDev>(), d_start, K, lay,
+                               dctr.as<int>(), dE.as<double>(), dK.as<int>(), dx, st, nullptr);
+    if (rc) return rc;
+    if (ms_out) {
+        cudaEventRecord(e1, st);
+        GBR_CUDA_TRY(cudaEventSynchronize(e1));
+        cudaEventElapsedTime(ms_out, e0, e1);
+        cudaEventDestroy(e0);
+        cudaEventDestroy(e1);
+    }
     std::vector<double> E(order.size());
     GBR_CUDA_TRY(cudaMemcpyAsync(E.data(), dE.p, E.size() * 8, cudaMemcpyDeviceToHost, st));
     GBR_CUDA_TRY(cudaStreamSynchronize(st));
@@ -522,5 +565,55 @@ extern "C" int gbr_batch_solve(int n_models, const gbr_model_desc *models, const
         if (h_arg) { h_arg[2 * m] = bu; h_arg[2 * m + 1] = bd; }
         s0 += ns;
     }
+    return GBR_OK;
+}
+}  // namespace gbr
+
+extern "C" int gbr_batch_solve(int n_models, const gbr_model_desc *models, const double *d_start, int iters,
+                               double *h_E0, int *h_arg, double *h_sector_E, void *stream) {
+    clear_error();
+    return batch_run(n_models, models, d_start, iters, h_E0, h_arg, h_sector_E, (cudaStream_t)stream,
+                     g_batch_threads, g_batch_per_sm, nullptr);
+}
+
+extern "C" int gbr_batch_set_shape(int threads, int ctas_per_sm) {
+    clear_error();
+    if (threads != 128 && threads != 256 && threads != 512)
+        return set_error(GBR_EINVAL, "threads %d must be 128, 256 or 512", threads);
+    if (ctas_per_sm < 0 || ctas_per_sm > 32) return set_error(GBR_EINVAL, "ctas_per_sm %d out of range 0..32", ctas_per_sm);
+    g_batch_threads = threads;
+    g_batch_per_sm = ctas_per_sm;
+    return GBR_OK;
+}
+
+extern "C" int gbr_batch_get_shape(int *threads, int *ctas_per_sm) {
+    clear_error();
+    if (!threads || !ctas_per_sm) return set_error(GBR_EINVAL, "NULL argument");
+    *threads = g_batch_threads;
+    *ctas_per_sm = g_batch_per_sm;
+    return GBR_OK;
+}
+
+extern "C" int gbr_batch_tune(int n_models, const gbr_model_desc *models, const double *d_start, int iters,
+                              int *h_shape, float *h_ms, void *stream) {
+    clear_error();
+    if (!h_shape) return set_error(GBR_EINVAL, "NULL argument");
+    std::vector<double> E((size_t)std::max(n_models, 1));
+    float best = 1e30f;
+    int bt = kBatchThreads, bp = 0, i = 0;
+    for (int t : {128, 256, 512})
+        for (int p : {0, 2, 1}) {
+            float ms = 0.f;
+            const int rc = batch_run(n_models, models, d_start, iters, E.data(), nullptr, nullptr,
+                                     (cudaStream_t)stream, t, p, &ms);
+            if (rc) return rc;
+            if (h_ms) h_ms[i] = ms;
+            ++i;
+            if (ms < best) { best = ms; bt = t; bp = p; }
+        }
+    g_batch_threads = bt;
+    g_batch_per_sm = bp;
+    h_shape[0] = bt;
+    h_shape[1] = bp;
     return GBR_OK;
 }

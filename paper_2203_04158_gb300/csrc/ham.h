@@ -12,8 +12,10 @@ constexpr int kMaxUClasses = 8;
 struct SpinSector {
     int L = 0, N = 0;
     int64_t D = 0;
-    StagDesc desc{};          // staggered tables (Fig. fastrank) for C^L_N
+    StagDesc desc{};          // staggered tables (Fig. fastrank) for C^L_N, 8-bit chunks
     DevBuf stag;              // uint32 entries (per-spin dimensions stay below 2^32)
+    StagDesc desc4{};         // the same with 4-bit chunks (more, smaller lookups)
+    DevBuf stag4;
     DevBuf states;            // D uint32 patterns (unrank list, Sec. II)
     DevBuf diag;              // D doubles: sum_p h_pp n_p
     int hmax = 0;             // largest number of valid hops of one state
@@ -50,6 +52,13 @@ struct LzHook {
     double *part;
 };
 
+// Device work buffers of a Lanczos solve, kept between calls and grown when
+// needed (one set per operator handle).
+struct LzWork {
+    DevBuf state, alpha, beta, scal, part, coef, tri, svec, work, ritz;
+    DevBuf buf[3], basis, x, hx;
+};
+
 }  // namespace gbr
 
 struct gbr_ham {
@@ -70,12 +79,18 @@ struct gbr_ham {
     int tune_up_rows[2] = {0, 0};
     int tune_dn_rows[2] = {0, 0};
     int tune_lz_rows[2] = {0, 0};   // the spin-up pass with the fused Lanczos update
+    // windowed gathers (own rows staged in shared memory, Z written row-major):
+    // win_dn < 0 = off (the untuned default), else on; the rows per CTA of the
+    // spin-down, spin-up and fused-update passes (32 or 64; 0 = 64)
+    int win_dn[2] = {-1, -1}, win_up[2] = {0, 0}, win_lz[2] = {0, 0};
+    // chunk width R of the per-spin staggered tables (8 or 4) and threads per
+    // state of the fused per-element kernel (1, 2 or 4)
+    int rank_R[2] = {8, 8}, fused_tps[2] = {1, 1};
     // scratch of the factored path (X^T and Z^T), grown on first use; one
     // H·v at a time per handle
     gbr::DevBuf ws_xt, ws_zt;
-    // Lanczos work buffers, kept between calls and grown when needed
-    gbr::DevBuf lz_state, lz_alpha, lz_beta, lz_scal, lz_part, lz_coef, lz_tri, lz_svec, lz_work, lz_ritz;
-    gbr::DevBuf lz_buf[3], lz_basis, lz_x, lz_hx;
+    // Lanczos work buffers
+    gbr::LzWork lzw;
 };
 
 namespace gbr {
@@ -103,4 +118,18 @@ int hv_launch_lz(const gbr_ham *H, const void *x, void *y, int fp, cudaStream_t 
 void *hv_xt_scratch(const gbr_ham *H, int fp);
 // upper bound of the partial sums hv_launch_lz writes for precision fp
 int64_t hv_lz_parts(const gbr_ham *H, int fp);
+
+// The operator of a Lanczos solve: the sector Hamiltonian (whose factored
+// H·v carries the fused first update of each step), or any other operator
+// given as y = A x in precision fp (32 or 64) on a stream.
+struct LzOp {
+    const gbr_ham *ham;
+    const void *obj;
+    int (*apply)(const void *obj, const void *x, void *y, int fp, cudaStream_t st);
+    int64_t n;
+    LzWork *work;
+};
+// The Lanczos solve of gbr_lanczos on any operator (argument checks included).
+int lanczos_solve(const LzOp &op, const gbr_lanczos_opts *o, const double *d_v0, gbr_lanczos_result *res,
+                  double *h_alpha, double *h_beta, double *h_ritz, void *stream);
 }

@@ -29,35 +29,40 @@
 
 namespace gbr {
 
-// Per-spin ranking constants (chunks of 8 bits, at most 4 chunks for L <= 32).
+// Per-spin ranking constants: chunks of R = 8 bits (at most 4 for L <= 32)
+// or R = 4 bits (at most 8).
+constexpr int kSpinChunks = 8;
 struct SpinK {
     int L, N, Q;
-    int shift[4], width[4], lo[4], hi[4], off[4];
+    int shift[kSpinChunks], width[kSpinChunks], lo[kSpinChunks], hi[kSpinChunks], off[kSpinChunks];
     int64_t D;
     int tab_entries;
 };
 
-static SpinK spin_k(const SpinSector &s) {
+static SpinK spin_k(const SpinSector &s, int R = 8) {
+    const StagDesc &d = R == 4 ? s.desc4 : s.desc;
     SpinK k;
     memset(&k, 0, sizeof(k));
-    k.L = s.L; k.N = s.N; k.Q = s.desc.Q; k.D = s.D;
-    for (int q = 0; q < s.desc.Q && q < 4; ++q) {
-        k.shift[q] = s.desc.shift[q];
-        k.width[q] = s.desc.width[q];
-        k.lo[q] = s.desc.lo[q];
-        k.hi[q] = s.desc.hi[q];
-        k.off[q] = (int)s.desc.off[q];
+    k.L = s.L; k.N = s.N; k.Q = d.Q; k.D = s.D;
+    for (int q = 0; q < d.Q && q < kSpinChunks; ++q) {
+        k.shift[q] = d.shift[q];
+        k.width[q] = d.width[q];
+        k.lo[q] = d.lo[q];
+        k.hi[q] = d.hi[q];
+        k.off[q] = (int)d.off[q];
     }
-    k.tab_entries = (int)s.desc.entries;
+    k.tab_entries = (int)d.entries;
     return k;
 }
+
+static const uint32_t *spin_tab(const SpinSector &s, int R) { return (R == 4 ? s.stag4 : s.stag).as<uint32_t>(); }
 
 // Fig. fastrank on a per-spin pattern (tables in shared memory).
 __device__ __forceinline__ uint32_t spin_rank_stag(const SpinK &s, const uint32_t *tab, uint32_t a) {
     uint32_t acc = 0;
     int np = 0;
 #pragma unroll
-    for (int q = 0; q < 4; ++q) {
+    for (int q = 0; q < kSpinChunks; ++q) {
         if (q < s.Q) {
             const uint32_t r = (a >> s.shift[q]) & ((1u << s.width[q]) - 1u);
             const int row = min(max(np, s.lo[q]), s.hi[q]) - s.lo[q];
@@ -168,9 +173,13 @@ __device__ __forceinline__ T diag_value(const HamK &hk, const T *dup, const T *d
 
 // --------------------------------------------------------------- fused path
 //
-// One thread per element i = r_up * D_dn + r_dn: the whole of Eq. Talpha for
-// every term, with the target ranked on the fly.
-template <typename T>
+// One group of TPS threads per element i = r_up * D_dn + r_dn: the whole of
+// Eq. Talpha for every term, with the target ranked on the fly.  With
+// TPS > 1 the occupied sites of both spins are dealt round-robin to the
+// group's threads (site j of the list of occupied sites, up spin first, goes
+// to thread j mod TPS), whose partial sums meet in a fixed butterfly; the
+// diagonal term is the first thread's.
+template <typename T, int TPS>
 __global__ void __launch_bounds__(256) k_hv_fused(const SpinK su, const SpinK sd, const HamK hk,
                                                   const uint32_t *__restrict__ st_up, const uint32_t *__restrict__ st_dn,
                                                   const uint32_t *__restrict__ tab_up, const uint32_t *__restrict__ tab_dn,
@@ -192,16 +201,23 @@ __global__ void __launch_bounds__(256) k_hv_fused(const SpinK su, const SpinK sd
 #pragma unroll
     for (int c = 0; c < kMaxUClasses; ++c) uval[c] = c < hk.nucls ? uval_g[c] : T(0);
     __syncthreads();
+    const int g = (int)(threadIdx.x % TPS);
+    const int lane = threadIdx.x & 31;
+    const unsigned gmask = TPS == 32 ? 0xFFFFFFFFu : (((1u << TPS) - 1u) << (lane & ~(TPS - 1)));
     const int64_t D = su.D * sd.D;
-    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < D; i += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t first = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) / TPS;
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x / TPS;
+    for (int64_t i = first; i < D; i += stride) {
         const int64_t ru = i / sd.D, rd = i - ru * sd.D;
         const uint32_t au = st_up[ru], ad = st_dn[rd];
-        T acc = diag_value<T>(hk, dup, ddn, uval, ru, rd, au, ad) * x[i];
+        T acc = g == 0 ? diag_value<T>(hk, dup, ddn, uval, ru, rd, au, ad) * x[i] : T(0);
+        int j = 0;   // index of the occupied site in the list (up spin, then down)
         // spin up: changes r_up
         uint32_t occ = au;
         while (occ) {
             const int p = __ffs(occ) - 1;
             occ &= occ - 1u;
+            if ((j++ % TPS) != g) continue;
             uint32_t emp = hk.nbr[p] & ~au;
             while (emp) {
                 const int q = __ffs(emp) - 1;
@@ -217,6 +233,7 @@ __global__ void __launch_bounds__(256) k_hv_fused(const SpinK su, const SpinK sd
         while (occ) {
             const int p = __ffs(occ) - 1;
             occ &= occ - 1u;
+            if ((j++ % TPS) != g) continue;
             uint32_t emp = hk.nbr[p] & ~ad;
             while (emp) {
                 const int q = __ffs(emp) - 1;
@@ -227,7 +244,9 @@ __global__ void __launch_bounds__(256) k_hv_fused(const SpinK su, const SpinK sd
                 acc += (__popc(ad & between_mask(p, q)) & 1) ? -c * v : c * v;
             }
         }
-        y[i] = acc;
+#pragma unroll
+        for (int o = TPS / 2; o > 0; o >>= 1) acc += __shfl_xor_sync(gmask, acc, o);
+        if (g == 0) y[i] = acc;
     }
 }
 
@@ -303,9 +322,10 @@ __global__ void __launch_bounds__(256) k_transpose16(const T *__restrict__ in, T
 struct CombineArgs {
     const uint32_t *st_up, *st_dn;   // per-spin patterns (row and column states)
     const void *dup, *ddn, *uval;     // per-spin diagonals, U class values (precision T)
-    const void *zt;                   // Z^T = H_dn X^T, D_dn x D_up
+    const void *zt;                   // Z^T = H_dn X^T (D_dn x D_up), or Z (D_up x D_dn) when zrow
     HamK hk;
     LzHook lz;                        // fused first Lanczos update (MODE 2)
+    int zrow;                         // 1: the spin-down pass wrote Z row-major (window kernels)
 };
 
 // MODE 0: Z = H_lists W.  MODE 1: y = H_up X + Dg o X + Z (combine).  MODE 2:
@@ -359,7 +379,7 @@ __global__ void __launch_bounds__(128, ((MODE >= 1 && sizeof(T) == 4) ? 10 : 1))
     // is read from Z^T once, column by column (TR consecutive values each),
     // into shared memory as [row][column]
     T *zs = reinterpret_cast<T *>(smr + (size_t)TR * hs * (4 + sizeof(T)));
-    if (COMBINE) {
+    if (COMBINE && !ca.zrow) {
         const T *zt = (const T *)ca.zt;
         const int64_t cbase = cc * (int64_t)(128 * VEC);
         const int nrow = (int)((Drows - r0) < (int64_t)TR ? (Drows - r0) : (int64_t)TR);
@@ -453,7 +473,11 @@ __global__ void __launch_bounds__(128, ((MODE >= 1 && sizeof(T) == 4) ? 10 : 1))
                 xo[0] = __ldg(x + r * Dcols + c0);
             }
             T zv[VEC];
-            if (VEC == 4 && sizeof(T) == 4) {
+            if (ca.zrow) {
+                const T *zr = (const T *)ca.zt + r * Dcols + c0;
+#pragma unroll
+                for (int v = 0; v < VEC; ++v) zv[v] = __ldcs(zr + v);
+            } else if (VEC == 4 && sizeof(T) == 4) {
                 const float4 z4 = *reinterpret_cast<const float4 *>(zs + i * ZS + threadIdx.x * VEC);
                 zv[0] = z4.x; zv[1 % VEC] = z4.y; zv[2 % VEC] = z4.z; zv[3 % VEC] = z4.w;
             } else {
@@ -509,6 +533,259 @@ __global__ void __launch_bounds__(128, ((MODE >= 1 && sizeof(T) == 4) ? 10 : 1))
     }
 }
 
+// ------------------------------------------------------- windowed gathers
+//
+// The same row gathers with the CTA's own rows staged in shared memory.  A
+// CTA owns TR consecutive rows and one 512-byte column slice of the gather
+// source (128 FP32 or 64 FP64 columns); those TR row slices are copied into
+// shared memory with 1-D bulk copies (cp.async.bulk, completion counted on an
+// mbarrier) while the CTA stages its hop lists.  A hop whose target row lies
+// in the window is read from shared memory, every other hop from L2, so the
+// L2-to-SM traffic falls by the share of hops that stay inside TR
+// consecutive ranks (lexicographic order keeps hops on the low sites local:
+// about 27 % of the 4x4 torus's hops and 40 % of the 18-site ring's at
+// TR = 64).  The combine pass also takes the state's own x value (diagonal
+// term) from the window.  The spin-down pass writes Z = (H_dn X^T)^T row-major
+// through a shared-memory transpose of its output tile, so the spin-up pass
+// reads Z with plain coalesced row loads.  8 warps; warp w handles the rows
+// w, w + 8, ... of the tile, its 32 lanes 16 bytes each of the slice.
+
+// bounded wait on an mbarrier phase: false if it did not complete within
+// about a second (the caller reports GBR_ETIMEOUT through the status word)
+__device__ __forceinline__ bool mbar_wait_bounded(uint64_t *bar, uint32_t parity) {
+    const uint32_t a = (uint32_t)__cvta_generic_to_shared(bar);
+    for (int it = 0; it < (1 << 24); ++it) {
+        uint32_t ok;
+        asm volatile(
+            "{\n\t.reg .pred p;\n\t"
+            "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+            "selp.u32 %0, 1, 0, p;\n\t}"
+            : "=r"(ok)
+            : "r"(a), "r"(parity)
+            : "memory");
+        if (ok) return true;
+        if (it > 64) __nanosleep(64);
+    }
+    return false;
+}
+
+// device status word: bit 0 = a bounded wait ran out (read and cleared by
+// gbr_device_status)
+__device__ int g_gbr_status = 0;
+
+template <typename T> struct WinVec;
+template <> struct WinVec<float> {
+    typedef float4 V;
+    __device__ static __forceinline__ void fma4(float *a, float c, const float4 &v) {
+        a[0] += c * v.x; a[1] += c * v.y; a[2] += c * v.z; a[3] += c * v.w;
+    }
+    __device__ static __forceinline__ void get(float *o, const float4 &v) { o[0] = v.x; o[1] = v.y; o[2] = v.z; o[3] = v.w; }
+    __device__ static __forceinline__ float4 put(const float *o) { return make_float4(o[0], o[1], o[2], o[3]); }
+    // four consecutive hop coefficients (16-byte aligned)
+    __device__ static __forceinline__ void coef4(float *c, const float *p) { get(c, *reinterpret_cast<const float4 *>(p)); }
+};
+template <> struct WinVec<double> {
+    typedef double2 V;
+    __device__ static __forceinline__ void fma4(double *a, double c, const double2 &v) { a[0] += c * v.x; a[1] += c * v.y; }
+    __device__ static __forceinline__ void get(double *o, const double2 &v) { o[0] = v.x; o[1] = v.y; }
+    __device__ static __forceinline__ double2 put(const double *o) { return make_double2(o[0], o[1]); }
+    __device__ static __forceinline__ void coef4(double *c, const double *p) {
+        get(c, *reinterpret_cast<const double2 *>(p));
+        get(c + 2, *reinterpret_cast<const double2 *>(p + 2));
+    }
+};
+
+// bytes of the window region (also the transposed output tile of MODE 0,
+// whose rows are padded by one element)
+template <typename T, int TR>
+__host__ __device__ constexpr size_t win_region_bytes() {
+    return ((size_t)TR * (32 * (16 / sizeof(T)) + 1) * sizeof(T) + 15) & ~(size_t)15;
+}
+
+template <typename T, int MODE, int TR>
+__global__ void __launch_bounds__(256, 2) k_gwin(const int64_t Drows, const int64_t Dcols, const int hmax,
+                                                 const int64_t nrb, const uint16_t *__restrict__ cnt,
+                                                 const uint32_t *__restrict__ tgt, const uint16_t *__restrict__ bond,
+                                                 const T *__restrict__ bcoef, const int uniform, const T hu,
+                                                 const T *__restrict__ x, T *__restrict__ y, const CombineArgs ca) {
+    constexpr bool COMBINE = MODE >= 1;
+    constexpr bool LZ = MODE == 2;
+    constexpr int VEC = 16 / (int)sizeof(T);
+    constexpr int WC = 32 * VEC;          // columns of the slice (512 bytes)
+    constexpr int NW = 8;                 // warps
+    constexpr int RPW = TR / NW;          // rows per warp
+    typedef typename WinVec<T>::V V;
+    // padded hop-list stride (multiple of 4: four targets per 16-byte load)
+    const int hs = (hmax + 3) & ~3;
+    extern __shared__ __align__(128) unsigned char smr[];
+    T *win = reinterpret_cast<T *>(smr);
+    uint32_t *st = reinterpret_cast<uint32_t *>(smr + win_region_bytes<T, TR>());
+    T *sc = reinterpret_cast<T *>(smr + win_region_bytes<T, TR>() + (size_t)TR * hs * 4);
+    __shared__ int scnt[TR];
+    __shared__ T suv[kMaxUClasses];
+    __shared__ __align__(8) uint64_t bar;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int64_t rb = blockIdx.x % nrb, cc = blockIdx.x / nrb;
+    const int64_t r0 = rb * TR, c0 = cc * WC;
+    const int nrow = (int)((Drows - r0) < (int64_t)TR ? (Drows - r0) : (int64_t)TR);
+    const int ncol = (int)((Dcols - c0) < (int64_t)WC ? (Dcols - c0) : (int64_t)WC);
+    if (threadIdx.x == 0) {
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"((uint32_t)__cvta_generic_to_shared(&bar)) : "memory");
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    __syncthreads();
+    // window: nrow slices of ncol * sizeof(T) bytes (a multiple of 16: the
+    // launcher requires Dcols * sizeof(T) % 16 == 0 and 16-byte aligned x)
+    if (warp == 0) {
+        const uint32_t rowb = (uint32_t)ncol * (uint32_t)sizeof(T);
+        const uint32_t ba = (uint32_t)__cvta_generic_to_shared(&bar);
+        if (lane == 0)
+            asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(ba), "r"(rowb * (uint32_t)nrow)
+                         : "memory");
+        __syncwarp();
+        for (int i = lane; i < nrow; i += 32) {
+            const T *src = x + (r0 + i) * Dcols + c0;
+            const uint32_t dst = (uint32_t)__cvta_generic_to_shared(win + (size_t)i * WC);
+            asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(dst),
+                         "l"(src), "r"(rowb), "r"(ba)
+                         : "memory");
+        }
+    }
+    // hop lists of the tile's rows (coalesced along the rows), meanwhile
+    for (int i = threadIdx.x; i < TR; i += blockDim.x) scnt[i] = (i < nrow) ? (int)cnt[r0 + i] : 0;
+    if (COMBINE && threadIdx.x < kMaxUClasses)
+        suv[threadIdx.x] = threadIdx.x < ca.hk.nucls ? ((const T *)ca.uval)[threadIdx.x] : T(0);
+    __syncthreads();
+    for (int e = threadIdx.x; e < TR * hmax; e += blockDim.x) {
+        const int i = e % TR, k = e / TR;
+        if (k < scnt[i]) {
+            const int64_t g = (int64_t)k * Drows + r0 + i;
+            const uint32_t w = tgt[g];
+            const T c = uniform ? hu : bcoef[bond[g]];
+            st[i * hs + k] = w & 0x7FFFFFFFu;
+            sc[i * hs + k] = (w >> 31) ? -c : c;
+        }
+    }
+    const int ok = mbar_wait_bounded(&bar, 0) ? 1 : 0;
+    if (!__syncthreads_and(ok)) {
+        if (threadIdx.x == 0) atomicOr(&g_gbr_status, 1);
+        return;
+    }
+    const int cl = lane * VEC;                 // this lane's first column in the slice
+    const bool active = cl < ncol;
+    const T *xs = x + c0 + cl;
+    DotAcc<T> dacc;
+    int klz = 0;
+    T slz = T(1), blz = T(0);
+    if (LZ) {
+        klz = *ca.lz.kstate;
+        slz = (T)ca.lz.scal[4 * klz];
+        blz = (T)ca.lz.scal[4 * klz + 1];
+    }
+    uint32_t ad[VEC];
+    T dd[VEC];
+    if (COMBINE && active) {
+        const T *ddn = (const T *)ca.ddn;
+#pragma unroll
+        for (int v = 0; v < VEC; ++v) {
+            ad[v] = ca.st_dn[c0 + cl + v];
+            dd[v] = ddn[c0 + cl + v];
+        }
+    }
+    T keep[MODE == 0 ? RPW : 1][VEC];
+#pragma unroll
+    for (int j = 0; j < RPW; ++j) {
+        const int i = warp + j * NW;
+        T acc[VEC];
+#pragma unroll
+        for (int v = 0; v < VEC; ++v) acc[v] = T(0);
+        if (i < nrow && active) {
+            const int n = scnt[i];
+            const uint32_t *ti = st + i * hs;
+            const T *ci = sc + i * hs;
+            // target row t: from the window if r0 <= t < r0 + nrow, else from L2
+            auto row = [&](uint32_t t) -> const V * {
+                const uint32_t tl = t - (uint32_t)r0;
+                return tl < (uint32_t)nrow ? reinterpret_cast<const V *>(win + (size_t)tl * WC + cl)
+                                           : reinterpret_cast<const V *>(xs + (int64_t)t * Dcols);
+            };
+            int k = 0;
+#pragma unroll 2
+            for (; k + 4 <= n; k += 4) {
+                const uint4 t4 = *reinterpret_cast<const uint4 *>(ti + k);
+                T c4[4];
+                WinVec<T>::coef4(c4, ci + k);
+                const V v0 = *row(t4.x), v1 = *row(t4.y), v2 = *row(t4.z), v3 = *row(t4.w);
+                WinVec<T>::fma4(acc, c4[0], v0);
+                WinVec<T>::fma4(acc, c4[1], v1);
+                WinVec<T>::fma4(acc, c4[2], v2);
+                WinVec<T>::fma4(acc, c4[3], v3);
+            }
+            for (; k < n; ++k) WinVec<T>::fma4(acc, ci[k], *row(ti[k]));
+            if (COMBINE) {
+                const int64_t r = r0 + i;
+                const uint32_t au = ca.st_up[r];
+                const T du = ((const T *)ca.dup)[r];
+                T xo[VEC], zv[VEC];
+                WinVec<T>::get(xo, *reinterpret_cast<const V *>(win + (size_t)i * WC + cl));
+                WinVec<T>::get(zv, __ldcs(reinterpret_cast<const V *>((const T *)ca.zt + r * Dcols + c0 + cl)));
+#pragma unroll
+                for (int v = 0; v < VEC; ++v) {
+                    const uint32_t both = au & ad[v];
+                    T dg = du + dd[v];
+#pragma unroll
+                    for (int u = 0; u < kMaxUClasses; ++u) {
+                        if (u >= ca.hk.nucls) break;
+                        dg += suv[u] * (T)__popc(both & ca.hk.umask[u]);
+                    }
+                    acc[v] += dg * xo[v] + zv[v];
+                }
+                if (LZ) {
+                    if (klz > 0) {
+                        T vp[VEC];
+                        WinVec<T>::get(vp, __ldcs(reinterpret_cast<const V *>((const T *)ca.lz.vprev + r * Dcols + c0 + cl)));
+#pragma unroll
+                        for (int v = 0; v < VEC; ++v) acc[v] = slz * acc[v] - blz * vp[v];
+                    }
+#pragma unroll
+                    for (int v = 0; v < VEC; ++v) dacc.add(acc[v], xo[v]);
+                }
+                __stcs(reinterpret_cast<V *>(y + r * Dcols + c0 + cl), WinVec<T>::put(acc));
+            }
+        }
+        if (MODE == 0) {
+#pragma unroll
+            for (int v = 0; v < VEC; ++v) keep[MODE == 0 ? j : 0][v] = acc[v];
+        }
+    }
+    if (MODE == 0) {
+        // transpose the TR x ncol output tile through shared memory (the
+        // window is no longer read) and write Z[c0 + col][r0 + i] = tile[i][col]
+        // as TR-element runs of consecutive ranks
+        constexpr int TS = WC + 1;
+        __syncthreads();
+        if (active) {
+#pragma unroll
+            for (int j = 0; j < RPW; ++j) {
+                const int i = warp + j * NW;
+                if (i < nrow) {
+#pragma unroll
+                    for (int v = 0; v < VEC; ++v) win[(size_t)i * TS + cl + v] = keep[j][v];
+                }
+            }
+        }
+        __syncthreads();
+        for (int e = threadIdx.x; e < TR * ncol; e += blockDim.x) {
+            const int i = e % TR, col = e / TR;
+            if (i < nrow) __stcs(y + (c0 + col) * Drows + r0 + i, win[(size_t)i * TS + col]);
+        }
+    }
+    if (LZ && ca.lz.part) {
+        const double r = block_sum(dacc.value());
+        if (threadIdx.x == 0) ca.lz.part[blockIdx.x] = r;
+    }
+}
+
 // ------------------------------------------------------------------ launch
 
 struct HamDev {
@@ -518,15 +795,16 @@ struct HamDev {
 
 template <typename T>
 static int launch_hop_lists(const gbr_ham *H, const SpinSector &s, cudaStream_t st) {
-    const SpinK sk = spin_k(s);
+    const int R = H->rank_R[sizeof(T) == 8 ? 1 : 0];
+    const SpinK sk = spin_k(s, R);
     const int nb = (H->L + 1) * (H->L + 1);
-    const size_t smem = (size_t)(s.desc.entries + nb) * 4 + (size_t)H->L * H->L * 2 + 16;
+    const size_t smem = (size_t)(sk.tab_entries + nb) * 4 + (size_t)H->L * H->L * 2 + 16;
     const int threads = 128;
     int64_t blocks = (s.D + threads - 1) / threads;
     blocks = std::min<int64_t>(blocks, (int64_t)sm_count() * 8);
     if (smem > 48 * 1024) GBR_CUDA_TRY(cudaFuncSetAttribute(k_hop_lists, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     k_hop_lists<<<(int)std::max<int64_t>(blocks, 1), threads, smem, st>>>(
-        sk, H->k, s.states.as<uint32_t>(), s.stag.as<uint32_t>(), H->binom.as<uint32_t>(),
+        sk, H->k, s.states.as<uint32_t>(), spin_tab(s, R), H->binom.as<uint32_t>(),
         reinterpret_cast<const uint16_t *>(H->bonds.p) + 2 * H->k.nbond, s.hop_cnt.as<uint16_t>(),
         s.hop_tgt.as<uint32_t>(), s.hop_bond.as<uint16_t>(), s.hmax);
     GBR_LAUNCH_CHECK();
@@ -536,16 +814,18 @@ static int launch_hop_lists(const gbr_ham *H, const SpinSector &s, cudaStream_t 
 
 template <typename T>
 static int launch_fused(const gbr_ham *H, const T *x, T *y, cudaStream_t st, const HamDev &hd) {
-    const SpinK su = spin_k(H->up), sd = spin_k(H->dn);
+    const int fpi = sizeof(T) == 8 ? 1 : 0;
+    const int R = H->rank_R[fpi], tps = H->fused_tps[fpi];
+    const SpinK su = spin_k(H->up, R), sd = spin_k(H->dn, R);
     const int nb = (H->L + 1) * (H->L + 1);
     const size_t smem = (size_t)(su.tab_entries + sd.tab_entries + nb + 1) * 4 + (size_t)H->L * H->L * sizeof(T) + 16;
     const int threads = 256;
-    int64_t blocks = (H->D + threads - 1) / threads;
+    int64_t blocks = (H->D * tps + threads - 1) / threads;
     blocks = std::max<int64_t>(1, std::min<int64_t>(blocks, (int64_t)sm_count() * 8));
-    auto kern = k_hv_fused<T>;
+    auto kern = tps == 4 ? k_hv_fused<T, 4> : (tps == 2 ? k_hv_fused<T, 2> : k_hv_fused<T, 1>);
     if (smem > 48 * 1024) GBR_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     kern<<<(int)blocks, threads, smem, st>>>(su, sd, H->k, H->up.states.as<uint32_t>(), H->dn.states.as<uint32_t>(),
-                                             H->up.stag.as<uint32_t>(), H->dn.stag.as<uint32_t>(),
+                                             spin_tab(H->up, R), spin_tab(H->dn, R),
                                              H->binom.as<uint32_t>(), (const T *)hd.hcoef, (const T *)hd.dup,
                                              (const T *)hd.ddn, (const T *)hd.uval, x, y);
     GBR_LAUNCH_CHECK();
@@ -602,11 +882,73 @@ static void gather_shape(const gbr_ham *H, int64_t Drows, int64_t Dcols, bool al
     *tr_out = (tr_req == 4 || tr_req == 16) ? tr_req : 8;
 }
 
+// Shared memory of a windowed gather pass with TR rows per CTA.
+template <typename T>
+static size_t gwin_smem(int TR, int hmax) {
+    const int hs = (std::max(1, hmax) + 3) & ~3;
+    const size_t win = TR == 32 ? win_region_bytes<T, 32>() : win_region_bytes<T, 64>();
+    return win + (size_t)TR * hs * (4 + sizeof(T));
+}
+
+// Rows per CTA of a windowed pass (knob: 0 = default 64, -1 = windows off).
+static int gwin_rows(int knob) { return knob == 32 ? 32 : 64; }
+
+// Whether this H·v runs the windowed passes (and so keeps Z row-major): the
+// handle's choice, slices that are whole 16-byte packs, and shared memory
+// for the hop lists of the longest per-spin list.
+template <typename T>
+static bool gwin_on(const gbr_ham *H) {
+    const int fpi = sizeof(T) == 8 ? 1 : 0;
+    if (H->win_dn[fpi] < 0) return false;
+    if ((H->up.D * (int64_t)sizeof(T)) % 16 || (H->dn.D * (int64_t)sizeof(T)) % 16) return false;
+    const int hmax = std::max(H->up.hmax, H->dn.hmax);
+    return gwin_smem<T>(64, hmax) <= 200 * 1024;
+}
+
+// Windowed row-gather pass (k_gwin); the caller has checked gwin_on and the
+// 16-byte alignment of every vector the pass reads or writes.
+template <typename T, int MODE>
+static int launch_gwin(const gbr_ham *H, const SpinSector &lists, int64_t Drows, int64_t Dcols, const T *w, T *z,
+                       const CombineArgs &ca, cudaStream_t st, const HamDev &hd, int TR, int *grid_out) {
+    constexpr int WC = 32 * (16 / (int)sizeof(T));
+    const int64_t nrb = (Drows + TR - 1) / TR;
+    const int64_t ncc = (Dcols + WC - 1) / WC;
+    const int hmax = std::max(1, lists.hmax);
+    const size_t smem = gwin_smem<T>(TR, hmax);
+    const int64_t blocks = nrb * ncc;
+    if (blocks > 0x7FFFFFFF) return set_error(GBR_EINVAL, "sector too large for the gather grid");
+#define GBR_W(R)                                                                                                    \
+    {                                                                                                               \
+        auto kern = k_gwin<T, MODE, R>;                                                                             \
+        GBR_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));          \
+        kern<<<(int)blocks, 256, smem, st>>>(Drows, Dcols, hmax, nrb, lists.hop_cnt.as<uint16_t>(),                \
+                                             lists.hop_tgt.as<uint32_t>(), lists.hop_bond.as<uint16_t>(),           \
+                                             (const T *)hd.bcoef, H->k.uniform, (T)H->k.hu, w, z, ca);               \
+    }
+    if (TR == 32) GBR_W(32) else GBR_W(64)
+#undef GBR_W
+    GBR_LAUNCH_CHECK();
+    count_launches(1);
+    if (grid_out) *grid_out = (int)blocks;
+    return GBR_OK;
+}
+
 // One row-gather pass Z = H_lists W (+ the combine epilogue, + the Lanczos update).
 template <typename T, int MODE>
 static int launch_gather(const gbr_ham *H, const SpinSector &lists, int64_t Drows, int64_t Dcols, const T *w, T *z,
                          const CombineArgs &ca, cudaStream_t st, const HamDev &hd, int *grid_out = nullptr) {
     constexpr bool COMBINE = MODE >= 1;
+    if (gwin_on<T>(H)) {
+        // the windowed kernels need every vector on a 16-byte boundary
+        uintptr_t al = (uintptr_t)w | (uintptr_t)z;
+        if (COMBINE) al |= (uintptr_t)ca.zt;
+        if (MODE == 2) al |= (uintptr_t)ca.lz.vprev;
+        const int fpi = sizeof(T) == 8 ? 1 : 0;
+        const int knob = MODE == 0 ? H->win_dn[fpi] : (MODE == 1 ? H->win_up[fpi] : H->win_lz[fpi]);
+        if ((al & 15u) == 0) return launch_gwin<T, MODE>(H, lists, Drows, Dcols, w, z, ca, st, hd, gwin_rows(knob), grid_out);
+        // MODE 0 always gets the 16-byte aligned scratch; a combine pass on
+        // unaligned vectors falls through to the plain kernel reading Z row-major
+    }
     bool aligned16 = (((uintptr_t)w | (uintptr_t)z) & 15u) == 0;
     if (MODE == 2) aligned16 = aligned16 && (((uintptr_t)ca.lz.vprev) & 15u) == 0;
     int vec = 1, TR = 8;
@@ -680,6 +1022,7 @@ static int stage_up(const gbr_ham *H, const T *x, T *y, cudaStream_t st, const H
     ca.uval = hd.uval;
     ca.zt = ws ? ws->zt : H->ws_zt.p;
     ca.hk = H->k;
+    ca.zrow = gwin_on<T>(H) ? 1 : 0;
     if (hook) return launch_gather<T, 2>(H, H->up, H->up.D, H->dn.D, x, y, ca, st, hd, nparts);
     return launch_gather<T, 1>(H, H->up, H->up.D, H->dn.D, x, y, ca, st, hd, nparts);
 }
@@ -790,15 +1133,17 @@ static std::vector<gbr_ham_prec *> g_prec_owner;   // never shared across handle
 static int build_spin(gbr_ham *H, SpinSector &s, int N) {
     s.L = H->L;
     s.N = N;
-    const int R = std::min(8, H->L);
-    int rc = stag_plan(H->L, N, R, &s.desc);
-    if (rc) return rc;
-    std::vector<uint64_t> tab;
-    stag_fill(s.desc, tab);
-    if (s.desc.wide) return set_error(GBR_EINVAL, "per-spin ranks exceed 32 bits");
-    std::vector<uint32_t> t32(tab.begin(), tab.end());
-    rc = s.stag.upload(t32.data(), t32.size() * 4);
-    if (rc) return rc;
+    int rc = GBR_OK;
+    for (int R : {8, 4}) {
+        StagDesc &d = R == 8 ? s.desc : s.desc4;
+        if ((rc = stag_plan(H->L, N, std::min(R, H->L), &d))) return rc;
+        if (d.Q > kSpinChunks) return set_error(GBR_EINVAL, "internal: %d chunks", d.Q);
+        std::vector<uint64_t> tab;
+        stag_fill(d, tab);
+        if (d.wide) return set_error(GBR_EINVAL, "per-spin ranks exceed 32 bits");
+        std::vector<uint32_t> t32(tab.begin(), tab.end());
+        if ((rc = (R == 8 ? s.stag : s.stag4).upload(t32.data(), t32.size() * 4))) return rc;
+    }
     std::vector<uint64_t> st;
     enumerate_combinations(H->L, N, st);
     s.D = (int64_t)st.size();
@@ -1026,10 +1371,77 @@ extern "C" int gbr_hv_stage(const gbr_ham *H, const void *d_x, void *d_y, int fp
     return hv_stage(H, d_x, d_y, fp, stage, (cudaStream_t)stream);
 }
 
+extern "C" int gbr_ham_set_shape(gbr_ham *H, int fp, const int *shape) {
+    clear_error();
+    if (!H || !shape) return set_error(GBR_EINVAL, "NULL argument");
+    if (fp != 32 && fp != 64) return set_error(GBR_EINVAL, "fp=%d must be 32 or 64", fp);
+    const int fpi = fp == 64 ? 1 : 0;
+    if (shape[0] != 0 && shape[0] != 1) return set_error(GBR_EINVAL, "window flag %d must be 0 or 1", shape[0]);
+    for (int i = 1; i < 4; ++i) {
+        const int v = shape[i];
+        const bool okv = v == 0 || (shape[0] ? (v == 32 || v == 64) : (v == 4 || v == 8 || v == 16));
+        if (!okv) return set_error(GBR_EINVAL, "rows per CTA %d not allowed for this family", v);
+    }
+    if (shape[4] != 0 && shape[4] != 4 && shape[4] != 8) return set_error(GBR_EINVAL, "chunk width %d must be 4 or 8", shape[4]);
+    if (shape[5] != 0 && shape[5] != 1 && shape[5] != 2 && shape[5] != 4)
+        return set_error(GBR_EINVAL, "threads per state %d must be 1, 2 or 4", shape[5]);
+    H->rank_R[fpi] = shape[4] ? shape[4] : 8;
+    H->fused_tps[fpi] = shape[5] ? shape[5] : 1;
+    if (shape[0]) {
+        H->win_dn[fpi] = shape[1];
+        H->win_up[fpi] = shape[2];
+        H->win_lz[fpi] = shape[3];
+    } else {
+        H->win_dn[fpi] = -1;
+        H->tune_dn_rows[fpi] = shape[1];
+        H->tune_up_rows[fpi] = shape[2];
+        H->tune_lz_rows[fpi] = shape[3];
+    }
+    return GBR_OK;
+}
+
+extern "C" int gbr_ham_get_shape(const gbr_ham *H, int fp, int *shape) {
+    clear_error();
+    if (!H || !shape) return set_error(GBR_EINVAL, "NULL argument");
+    if (fp != 32 && fp != 64) return set_error(GBR_EINVAL, "fp=%d must be 32 or 64", fp);
+    const int fpi = fp == 64 ? 1 : 0;
+    const bool on = fp == 64 ? gwin_on<double>(H) : gwin_on<float>(H);
+    shape[0] = on ? 1 : 0;
+    if (on) {
+        shape[1] = gwin_rows(H->win_dn[fpi]);
+        shape[2] = gwin_rows(H->win_up[fpi]);
+        shape[3] = gwin_rows(H->win_lz[fpi]);
+    } else {
+        auto plain = [](int v, int dflt) { return (v == 4 || v == 8 || v == 16) ? v : dflt; };
+        shape[1] = plain(H->tune_dn_rows[fpi], 8);
+        shape[2] = plain(H->tune_up_rows[fpi], 8);
+        shape[3] = plain(H->tune_lz_rows[fpi], 8);
+    }
+    shape[4] = H->rank_R[fpi];
+    shape[5] = H->fused_tps[fpi];
+    return GBR_OK;
+}
+
+extern "C" int gbr_device_status(int clear, int *status) {
+    clear_error();
+    if (!status) return set_error(GBR_EINVAL, "NULL argument");
+    int v = 0;
+    GBR_CUDA_TRY(cudaMemcpyFromSymbol(&v, g_gbr_status, sizeof(int)));
+    if (clear) {
+        const int zero = 0;
+        GBR_CUDA_TRY(cudaMemcpyToSymbol(g_gbr_status, &zero, sizeof(int)));
+    }
+    *status = v;
+    return v ? set_error(GBR_ETIMEOUT, "a bounded device-side wait ran out (status 0x%x)", v) : GBR_OK;
+}
+
 // Times the candidate launch shapes on scratch vectors and keeps the fastest
-// in the handle: the path (fused for sectors up to 2^22 states), the rows per
-// CTA of the spin-up pass, the rows staged per CTA by the spin-down pass, and
-// the rows per CTA of the spin-up pass with the fused Lanczos update.
+// in the handle: the path (fused for sectors up to 2^22 states), the gather
+// family (plain row gathers, or windowed gathers with the CTA's own rows in
+// shared memory), the rows per CTA of the spin-up and spin-down passes in
+// that family, the rows per CTA of the spin-up pass with the fused Lanczos
+// update, the chunk width of the per-spin staggered tables, and the threads
+// per state of the fused kernel.
 extern "C" int gbr_ham_tune(gbr_ham *H, int fp, void *stream) {
     clear_error();
     if (!H) return set_error(GBR_EINVAL, "NULL handle");
@@ -1061,17 +1473,41 @@ extern "C" int gbr_ham_tune(gbr_ham *H, int fp, void *stream) {
     float best = 1e30f, ms = 0.f;
     int best_path = GBR_HV_FACTORED;
     H->path = GBR_HV_FACTORED;
-    // rows per CTA of the spin-up (combine) pass, then of the spin-down pass
+    const int keep_win = H->win_dn[fpi];
+    // rows per CTA of the spin-up (combine) pass, then of the spin-down pass,
+    // first with the plain row gathers, then (where the sector allows) with
+    // the windowed ones; the faster family stays on
+    float best_plain = 1e30f, best_win = 1e30f;
+    int win_pick[2] = {0, 0};
+    H->win_dn[fpi] = -1;
     for (int pass = 0; pass < 2; ++pass) {
         int *knob = pass == 0 ? &H->tune_up_rows[fpi] : &H->tune_dn_rows[fpi];
         int best_tr = 8;
         for (int tr : {4, 8, 16}) {
             *knob = tr;
             if ((rc = time_it(&ms))) goto done;
-            if (ms < best || (tr == 8 && ms <= best)) { best = ms; best_tr = tr; }
+            if (ms < best_plain || (tr == 8 && ms <= best_plain)) { best_plain = ms; best_tr = tr; }
         }
         *knob = best_tr;
     }
+    {
+        H->win_dn[fpi] = 0;
+        if (fp == 64 ? gwin_on<double>(H) : gwin_on<float>(H)) {
+            for (int pass = 0; pass < 2; ++pass) {
+                int *knob = pass == 0 ? &H->win_up[fpi] : &H->win_dn[fpi];
+                int best_tr = 64;
+                for (int tr : {32, 64}) {
+                    *knob = tr;
+                    if ((rc = time_it(&ms))) goto done;
+                    if (ms < best_win) { best_win = ms; best_tr = tr; }
+                }
+                *knob = best_tr;
+                win_pick[pass] = best_tr;
+            }
+        }
+    }
+    H->win_dn[fpi] = best_win < best_plain ? win_pick[1] : -1;
+    best = std::min(best_plain, best_win);
     // rows per CTA of the combine pass as the Lanczos launches it (fused
     // first update, another kernel with its own best tile), timed on that
     // kernel with a stand-in recurrence state (step 1, v_{k-1} = x)
@@ -1098,24 +1534,59 @@ extern "C" int gbr_ham_tune(gbr_ham *H, int fp, void *stream) {
             cudaEventElapsedTime(ms_out, e0, e1);
             return GBR_OK;
         };
+        const bool winmode = H->win_dn[fpi] >= 0;
         float best_lz = 1e30f;
         int best_tr = 0;
-        for (int tr : {4, 8, 16}) {
-            H->tune_lz_rows[fpi] = tr;
+        for (int tr : {4, 8, 16, 32, 64}) {
+            if (winmode != (tr >= 32)) continue;
+            (winmode ? H->win_lz[fpi] : H->tune_lz_rows[fpi]) = tr;
             if ((rc = time_lz(&ms))) goto done;
             if (ms < best_lz) { best_lz = ms; best_tr = tr; }
         }
-        H->tune_lz_rows[fpi] = best_tr;
+        (winmode ? H->win_lz[fpi] : H->tune_lz_rows[fpi]) = best_tr;
     }
-    if (H->D <= ((int64_t)1 << 22)) {
-        H->path = GBR_HV_FUSED;
-        if ((rc = time_it(&ms))) goto done;
-        if (ms < best) { best = ms; best_path = GBR_HV_FUSED; }
+    // chunk width of the per-spin tables in the factored path (its ranking
+    // pass only), then the fused per-element kernel over chunk width and
+    // threads per state (Sec. V-B compares R = 4 and 8 inside the H·v)
+    {
+        H->path = GBR_HV_FACTORED;
+        float best_fac = 1e30f;
+        int best_R = 8;
+        for (int R : {8, 4}) {
+            H->rank_R[fpi] = R;
+            if ((rc = time_it(&ms))) goto done;
+            if (ms < best_fac) { best_fac = ms; best_R = R; }
+        }
+        H->rank_R[fpi] = best_R;
+        best = std::min(best, best_fac);
+        if (H->D <= ((int64_t)1 << 22)) {
+            H->path = GBR_HV_FUSED;
+            float best_fu = 1e30f;
+            int bR = 8, bT = 1;
+            for (int R : {8, 4})
+                for (int tps : {1, 2, 4}) {
+                    H->rank_R[fpi] = R;
+                    H->fused_tps[fpi] = tps;
+                    if ((rc = time_it(&ms))) goto done;
+                    if (ms < best_fu) { best_fu = ms; bR = R; bT = tps; }
+                }
+            H->fused_tps[fpi] = bT;
+            if (best_fu < best) {
+                best = best_fu;
+                best_path = GBR_HV_FUSED;
+                H->rank_R[fpi] = bR;
+            } else {
+                H->rank_R[fpi] = best_R;
+            }
+        }
     }
     H->path = keep_path == GBR_HV_AUTO ? best_path : keep_path;
 done:
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
-    if (rc) H->path = keep_path;
+    if (rc) {
+        H->path = keep_path;
+        H->win_dn[fpi] = keep_win;
+    }
     return rc;
 }

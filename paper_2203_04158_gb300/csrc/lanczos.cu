@@ -485,7 +485,7 @@ __global__ void k_scale_start(T *__restrict__ v, const double *nrm2, int64_t n) 
 // ------------------------------------------------------------------ driver
 
 struct Lz {
-    const gbr_ham *H;
+    LzOp op;
     int64_t n;
     int fp;            // 32 or 64
     int iters, reorth, store;
@@ -500,11 +500,18 @@ struct Lz {
     DevBuf *buf;
     DevBuf &basis, &x, &hx;
     std::vector<cudaEvent_t> evs;   // profile: 5 events per H·v (stage boundaries)
-    explicit Lz(gbr_ham *h)
-        : H(h), state(h->lz_state), alpha(h->lz_alpha), beta(h->lz_beta), scal(h->lz_scal), part(h->lz_part),
-          coef(h->lz_coef),
-          tri(h->lz_tri), svec(h->lz_svec), work(h->lz_work), ritz_tmp(h->lz_ritz), buf(h->lz_buf),
-          basis(h->lz_basis), x(h->lz_x), hx(h->lz_hx) {}
+    explicit Lz(const LzOp &o)
+        : op(o), state(o.work->state), alpha(o.work->alpha), beta(o.work->beta), scal(o.work->scal),
+          part(o.work->part), coef(o.work->coef), tri(o.work->tri), svec(o.work->svec), work(o.work->work),
+          ritz_tmp(o.work->ritz), buf(o.work->buf), basis(o.work->basis), x(o.work->x), hx(o.work->hx) {}
+    // y = A x in precision fp (the sector Hamiltonian's H·v records the stage events)
+    int apply(const void *xin, void *yout, int fp, cudaStream_t s, cudaEvent_t *ev = nullptr) const {
+        if (op.ham) return hv_launch(op.ham, xin, yout, fp, s, ev);
+        if (ev)
+            for (int e = 0; e < 5; ++e) cudaEventRecord(ev[e], s);
+        return op.apply(op.obj, xin, yout, fp, s);
+    }
+    bool factored() const { return op.ham && hv_is_factored(op.ham); }
 };
 
 // grows a handle-owned buffer to at least bytes (contents not kept)
@@ -533,14 +540,14 @@ static int lz_step(Lz &z, int phase, bool pass2, cudaEvent_t *ev4, bool want_rit
     double *part = z.part.as<double>();
     int64_t nk = 0;
     int nparts = z.grid;
-    if (hv_is_factored(z.H)) {
+    if (z.factored()) {
         // w = H v - beta_k v_{k-1} and the partials of <w, v> in the H·v epilogue
         const LzHook hook{vprev, z.scal.as<double>(), &st->k, pass2 ? nullptr : part};
         // X^T comes from the previous step's update except in each pass's first step
-        int rc = hv_launch_lz(z.H, v, w, z.fp, z.st, ev4, hook, &nparts, z.fuse_t && !first);
+        int rc = hv_launch_lz(z.op.ham, v, w, z.fp, z.st, ev4, hook, &nparts, z.fuse_t && !first);
         if (rc) return rc;
     } else {
-        int rc = hv_launch(z.H, v, w, z.fp, z.st, ev4);
+        int rc = z.apply(v, w, z.fp, z.st, ev4);
         if (rc) return rc;
         k_step1<T><<<z.grid, kRedThreads, 0, z.st>>>(st, z.scal.as<double>(), vprev, v, w, n, part, pass2 ? 0 : 1);
         ++nk;
@@ -554,7 +561,7 @@ static int lz_step(Lz &z, int phase, bool pass2, cudaEvent_t *ev4, bool want_rit
     T *slot_basis = (z.store && !pass2 && !z.reorth && !basis_slots) ? z.basis.as<T>() : nullptr;
     int nparts2 = z.grid;
     if (z.fuse_t) {
-        const int64_t rows = z.H->up.D, cols = z.H->dn.D;
+        const int64_t rows = z.op.ham->up.D, cols = z.op.ham->dn.D;
         const dim3 g((unsigned)((cols + 63) / 64), (unsigned)((rows + 63) / 64));
         k_step2_t<T><<<g, 256, 0, z.st>>>(st, z.scal.as<double>(), v, w, (T *)z.xt, rows, cols, part, pass2 ? 0 : 1);
         nparts2 = (int)(g.x * g.y);
@@ -633,9 +640,9 @@ static int lz_run(Lz &z, const double *d_v0, gbr_lanczos_result *res, const gbr_
     // dimensions that are whole 16-byte packs
     {
         const int64_t V = 16 / (int64_t)sizeof(T);
-        z.fuse_t = (hv_is_factored(z.H) && !z.reorth && (!z.store || z.in_basis) && z.H->up.D % V == 0 &&
-                    z.H->dn.D % V == 0 && (z.H->up.D + 63) / 64 <= 65535) ? 1 : 0;
-        z.xt = z.fuse_t ? hv_xt_scratch(z.H, z.fp) : nullptr;
+        z.fuse_t = (z.factored() && !z.reorth && (!z.store || z.in_basis) && z.op.ham->up.D % V == 0 &&
+                    z.op.ham->dn.D % V == 0 && (z.op.ham->up.D + 63) / 64 <= 65535) ? 1 : 0;
+        z.xt = z.fuse_t ? hv_xt_scratch(z.op.ham, z.fp) : nullptr;
         if (z.fuse_t && !z.xt) return set_error(GBR_ENOMEM, "scratch for X^T");
     }
     cudaGraphExec_t gexec[3] = {nullptr, nullptr, nullptr};
@@ -771,7 +778,7 @@ static int lz_run(Lz &z, const double *d_v0, gbr_lanczos_result *res, const gbr_
             }
         }
         GBR_LAUNCH_CHECK();
-        if ((rc = hv_launch(z.H, x.p, hx.p, 64, s))) return rc;
+        if ((rc = z.apply(x.p, hx.p, 64, s))) return rc;
         double *part = z.part.as<double>();
         k_dot64<<<z.grid, kRedThreads, 0, s>>>(x.as<double>(), hx.as<double>(), n, part);
         k_sum<<<1, kRedThreads, 0, s>>>(part, z.grid, tri + 2);
@@ -947,19 +954,19 @@ extern "C" int gbr_check_rcp64(int64_t n, double *h_max_rel_err) {
     return GBR_OK;
 }
 
-extern "C" int gbr_lanczos(const gbr_ham *H, const gbr_lanczos_opts *o, const double *d_v0, gbr_lanczos_result *res,
-                           double *h_alpha, double *h_beta, double *h_ritz, void *stream) {
-    clear_error();
-    if (!H || !o || !res || !d_v0) return set_error(GBR_EINVAL, "NULL argument");
+namespace gbr {
+int lanczos_solve(const LzOp &op, const gbr_lanczos_opts *o, const double *d_v0, gbr_lanczos_result *res,
+                  double *h_alpha, double *h_beta, double *h_ritz, void *stream) {
+    if (!o || !res || !d_v0) return set_error(GBR_EINVAL, "NULL argument");
     if (o->iters < 1 || o->iters > 65535) return set_error(GBR_EINVAL, "iters=%d out of range 1..65535", o->iters);
     if (o->prec != GBR_PREC_FP64 && o->prec != GBR_PREC_MIXED) return set_error(GBR_EINVAL, "unknown prec %d", o->prec);
     if (!(o->ritz_tail >= 0.0 && o->ritz_tail < 1.0)) return set_error(GBR_EINVAL, "ritz_tail must be in [0, 1)");
     if ((uintptr_t)d_v0 & 7u) return set_error(GBR_EINVAL, "v0 must be 8-byte aligned");
     memset(res, 0, sizeof(*res));
-    Lz z(const_cast<gbr_ham *>(H));
-    z.n = H->D;
+    Lz z(op);
+    z.n = op.n;
     z.fp = o->prec == GBR_PREC_MIXED ? 32 : 64;
-    z.iters = (int)std::min<int64_t>(o->iters, H->D);
+    z.iters = (int)std::min<int64_t>(o->iters, op.n);
     z.reorth = o->reorth ? 1 : 0;
     z.tol = o->tol > 0.0 ? o->tol : 0.0;
     z.st = (cudaStream_t)stream;
@@ -990,7 +997,7 @@ extern "C" int gbr_lanczos(const gbr_ham *H, const gbr_lanczos_opts *o, const do
     if ((rc = grow(z.beta, sizeof(double) * (size_t)(z.iters + 2)))) return rc;
     if ((rc = grow(z.scal, sizeof(double) * kScal * (size_t)(z.iters + 2)))) return rc;
     size_t nparts = (size_t)z.grid * (size_t)(z.reorth ? z.iters + 1 : 1);
-    nparts = std::max(nparts, (size_t)hv_lz_parts(H, z.fp));
+    if (op.ham) nparts = std::max(nparts, (size_t)hv_lz_parts(op.ham, z.fp));
     if ((rc = grow(z.part, sizeof(double) * nparts))) return rc;
     if ((rc = grow(z.coef, sizeof(double) * (size_t)(z.iters + 2)))) return rc;
     if ((rc = grow(z.tri, sizeof(double) * 16))) return rc;
@@ -1007,4 +1014,13 @@ extern "C" int gbr_lanczos(const gbr_ham *H, const gbr_lanczos_opts *o, const do
                     : lz_run<float>(z, d_v0, res, o, h_alpha, h_beta, h_ritz);
     if (z.store) cache_put(z.basis);
     return rc;
+}
+}  // namespace gbr
+
+extern "C" int gbr_lanczos(const gbr_ham *H, const gbr_lanczos_opts *o, const double *d_v0, gbr_lanczos_result *res,
+                           double *h_alpha, double *h_beta, double *h_ritz, void *stream) {
+    clear_error();
+    if (!H) return set_error(GBR_EINVAL, "NULL argument");
+    const LzOp op{H, nullptr, nullptr, H->D, &const_cast<gbr_ham *>(H)->lzw};
+    return lanczos_solve(op, o, d_v0, res, h_alpha, h_beta, h_ritz, stream);
 }

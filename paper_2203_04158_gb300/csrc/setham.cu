@@ -20,6 +20,7 @@ struct gbr_setham {
     gbr::DevBuf hc64, hc32;     // L x L off-diagonal one-body terms
     gbr::DevBuf hd64, hd32;     // L diagonal one-body terms h_pp
     gbr::DevBuf uv64, uv32;     // U class values
+    gbr::LzWork lzw;            // Lanczos work buffers
     ~gbr_setham() { gbr_trie_destroy(trie); }
 };
 
@@ -138,9 +139,30 @@ static int launch_set_hv(const gbr_setham *S, const T *x, T *y, int check, cudaS
     return GBR_OK;
 }
 
+// y = H x on the set with membership checks (the Lanczos operator; a set
+// not closed under H gets the projected operator P H P)
+static int set_apply(const void *obj, const void *x, void *y, int fp, cudaStream_t st) {
+    const gbr_setham *S = static_cast<const gbr_setham *>(obj);
+    if (S->trie->wide) {
+        if (fp == 64) return launch_set_hv<double, uint64_t>(S, (const double *)x, (double *)y, 1, st);
+        return launch_set_hv<float, uint64_t>(S, (const float *)x, (float *)y, 1, st);
+    }
+    if (fp == 64) return launch_set_hv<double, uint32_t>(S, (const double *)x, (double *)y, 1, st);
+    return launch_set_hv<float, uint32_t>(S, (const float *)x, (float *)y, 1, st);
+}
+
 }  // namespace gbr
 
 using namespace gbr;
+
+extern "C" int gbr_setham_lanczos(const gbr_setham *S, const gbr_lanczos_opts *o, const double *d_v0,
+                                  gbr_lanczos_result *res, double *h_alpha, double *h_beta, double *h_ritz,
+                                  void *stream) {
+    clear_error();
+    if (!S) return set_error(GBR_EINVAL, "NULL handle");
+    const LzOp op{nullptr, S, &set_apply, S->n, &const_cast<gbr_setham *>(S)->lzw};
+    return lanczos_solve(op, o, d_v0, res, h_alpha, h_beta, h_ritz, stream);
+}
 
 extern "C" int gbr_setham_create_ordered(int L, const double *h, const double *U, const uint64_t *h_states,
                                          int64_t n, int R, int msb_first, gbr_setham **out) {

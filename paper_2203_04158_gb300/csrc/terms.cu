@@ -118,6 +118,7 @@ struct gbr_termham {
     int64_t elements = 0;
     gbr_trie *trie = nullptr;
     gbr::DevBuf terms;
+    gbr::LzWork lzw;    // Lanczos work buffers
     ~gbr_termham() { gbr_trie_destroy(trie); }
 };
 
@@ -219,6 +220,28 @@ static int launch_term_hv(const gbr_termham *Th, const T *x, T *y, int check, cu
     return GBR_OK;
 }
 }  // namespace gbr
+
+namespace gbr {
+// y = H x over the set with membership checks (the Lanczos operator)
+static int term_apply(const void *obj, const void *x, void *y, int fp, cudaStream_t st) {
+    const gbr_termham *T = static_cast<const gbr_termham *>(obj);
+    if (T->trie->wide) {
+        if (fp == 64) return launch_term_hv<double, uint64_t>(T, (const double *)x, (double *)y, 1, st);
+        return launch_term_hv<float, uint64_t>(T, (const float *)x, (float *)y, 1, st);
+    }
+    if (fp == 64) return launch_term_hv<double, uint32_t>(T, (const double *)x, (double *)y, 1, st);
+    return launch_term_hv<float, uint32_t>(T, (const float *)x, (float *)y, 1, st);
+}
+}  // namespace gbr
+
+extern "C" int gbr_termham_lanczos(const gbr_termham *T, const gbr_lanczos_opts *o, const double *d_v0,
+                                   gbr_lanczos_result *res, double *h_alpha, double *h_beta, double *h_ritz,
+                                   void *stream) {
+    clear_error();
+    if (!T) return set_error(GBR_EINVAL, "NULL handle");
+    const LzOp op{nullptr, T, &term_apply, T->n, &const_cast<gbr_termham *>(T)->lzw};
+    return lanczos_solve(op, o, d_v0, res, h_alpha, h_beta, h_ritz, stream);
+}
 
 extern "C" int gbr_termham_hv(const gbr_termham *T, const void *d_x, void *d_y, int fp, int check, void *stream) {
     clear_error();

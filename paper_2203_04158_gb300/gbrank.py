@@ -92,10 +92,15 @@ def lib():
                 "gbr_ham_get_path": (i32, [vp, C.POINTER(i32)]),
                 "gbr_hv": (i32, [vp, vp, vp, i32, vp]),
                 "gbr_ham_tune": (i32, [vp, i32, vp]),
+                "gbr_ham_set_shape": (i32, [vp, i32, vp]),
+                "gbr_ham_get_shape": (i32, [vp, i32, vp]),
+                "gbr_device_status": (i32, [i32, vp]),
                 "gbr_hv_stage": (i32, [vp, vp, vp, i32, i32, vp]),
                 "gbr_hv_static": (i32, [vp, vp, vp, i32, vp]),
                 "gbr_launch_count": (i64, []),
                 "gbr_lanczos": (i32, [vp, vp, vp, vp, vp, vp, vp, vp]),
+                "gbr_setham_lanczos": (i32, [vp, vp, vp, vp, vp, vp, vp, vp]),
+                "gbr_termham_lanczos": (i32, [vp, vp, vp, vp, vp, vp, vp, vp]),
                 "gbr_term_product": (i32, [vp, i32, C.c_double, vp]),
                 "gbr_term_mul": (i32, [vp, vp, vp]),
                 "gbr_termham_create": (i32, [i32, vp, i32, vp, i64, i32, vp]),
@@ -111,6 +116,9 @@ def lib():
                 "gbr_setham_hv": (i32, [vp, vp, vp, i32, i32, vp]),
                 "gbr_batch_layout": (i32, [i32, vp, vp, vp]),
                 "gbr_batch_solve": (i32, [i32, vp, vp, i32, vp, vp, vp, vp]),
+                "gbr_batch_set_shape": (i32, [i32, i32]),
+                "gbr_batch_get_shape": (i32, [vp, vp]),
+                "gbr_batch_tune": (i32, [i32, vp, vp, i32, vp, vp, vp]),
             }
             for name, (res, args) in sig.items():
                 f = getattr(L, name)
@@ -326,6 +334,27 @@ def gbr_ham_tune(H: Ham, fp: int = 32, stream=None):
     _check(lib().gbr_ham_tune(H, fp, _stream(stream)))
 
 
+def gbr_ham_set_shape(H: Ham, fp: int, window: int, rows_dn: int = 0, rows_up: int = 0, rows_lz: int = 0,
+                      chunk_bits: int = 0, threads_per_state: int = 0):
+    sh = np.array([window, rows_dn, rows_up, rows_lz, chunk_bits, threads_per_state], dtype=np.int32)
+    _check(lib().gbr_ham_set_shape(H, fp, _hptr(sh)))
+
+
+def gbr_ham_get_shape(H: Ham, fp: int) -> dict:
+    sh = np.zeros(6, dtype=np.int32)
+    _check(lib().gbr_ham_get_shape(H, fp, _hptr(sh)))
+    return dict(window=int(sh[0]), rows_dn=int(sh[1]), rows_up=int(sh[2]), rows_lz=int(sh[3]),
+                chunk_bits=int(sh[4]), threads_per_state=int(sh[5]))
+
+
+def gbr_device_status(clear: bool = True) -> int:
+    """The device status word (0 = no bounded wait ran out); raises GbrError
+    with GBR_ETIMEOUT when it is non-zero."""
+    v = C.c_int(0)
+    _check(lib().gbr_device_status(int(bool(clear)), C.byref(v)))
+    return v.value
+
+
 def gbr_hv(H: Ham, x, y, stream=None):
     import torch
     if x.dtype != y.dtype:
@@ -362,9 +391,8 @@ def gbr_launch_count() -> int:
     return lib().gbr_launch_count()
 
 
-def gbr_lanczos(H: Ham, v0, iters: int, reorth: bool = False, prec: int = GBR_PREC_MIXED, refine: bool = True,
-                store_basis: int = -1, use_graph: bool = False, want_ritz: bool = False, profile: bool = False,
-                tol: float = 0.0, ritz_tail: float = 0.0, stream=None) -> dict:
+def _lanczos(fn, handle, v0, iters, reorth, prec, refine, store_basis, use_graph, want_ritz, profile, tol,
+             ritz_tail, stream) -> dict:
     import torch
     o = LanczosOpts(iters, int(bool(reorth)), prec, int(bool(refine)), store_basis, int(bool(use_graph)),
                     int(bool(profile)), float(tol), float(ritz_tail))
@@ -372,14 +400,35 @@ def gbr_lanczos(H: Ham, v0, iters: int, reorth: bool = False, prec: int = GBR_PR
     a = np.zeros(iters, dtype=np.float64)
     b = np.zeros(max(iters, 1), dtype=np.float64)
     rz = np.zeros(iters, dtype=np.float64) if want_ritz else None
-    _check(lib().gbr_lanczos(H, C.byref(o), _dptr(v0, (torch.float64,)), C.byref(r), _hptr(a), _hptr(b),
-                             None if rz is None else _hptr(rz), _stream(stream)))
+    _check(fn(handle, C.byref(o), _dptr(v0, (torch.float64,)), C.byref(r), _hptr(a), _hptr(b),
+              None if rz is None else _hptr(rz), _stream(stream)))
     k = r.iters_done
     return dict(E0=r.E0, E_ritz=r.E_ritz, residual=r.residual, iters=k, breakdown=bool(r.breakdown),
                 stored_basis=bool(r.stored_basis), seconds=r.seconds, hv_seconds=r.hv_seconds,
                 stage_seconds=list(r.stage_seconds), stage_launches=list(r.stage_launches),
                 converged=bool(r.converged), ritz_terms=r.ritz_terms,
                 alpha=a[:k].copy(), beta=b[:max(k - 1, 0)].copy(), ritz=None if rz is None else rz[:k].copy())
+
+
+def gbr_lanczos(H: Ham, v0, iters: int, reorth: bool = False, prec: int = GBR_PREC_MIXED, refine: bool = True,
+                store_basis: int = -1, use_graph: bool = False, want_ritz: bool = False, profile: bool = False,
+                tol: float = 0.0, ritz_tail: float = 0.0, stream=None) -> dict:
+    return _lanczos(lib().gbr_lanczos, H, v0, iters, reorth, prec, refine, store_basis, use_graph, want_ritz,
+                    profile, tol, ritz_tail, stream)
+
+
+def gbr_setham_lanczos(Sh, v0, iters: int, reorth: bool = False, prec: int = GBR_PREC_MIXED, refine: bool = True,
+                       store_basis: int = -1, use_graph: bool = False, want_ritz: bool = False, tol: float = 0.0,
+                       ritz_tail: float = 0.0, stream=None) -> dict:
+    return _lanczos(lib().gbr_setham_lanczos, Sh, v0, iters, reorth, prec, refine, store_basis, use_graph,
+                    want_ritz, False, tol, ritz_tail, stream)
+
+
+def gbr_termham_lanczos(Th, v0, iters: int, reorth: bool = False, prec: int = GBR_PREC_MIXED, refine: bool = True,
+                        store_basis: int = -1, use_graph: bool = False, want_ritz: bool = False, tol: float = 0.0,
+                        ritz_tail: float = 0.0, stream=None) -> dict:
+    return _lanczos(lib().gbr_termham_lanczos, Th, v0, iters, reorth, prec, refine, store_basis, use_graph,
+                    want_ritz, False, tol, ritz_tail, stream)
 
 
 # ------------------------------------------------------ set Hamiltonians
@@ -493,3 +542,26 @@ def gbr_batch_solve(models, start, iters: int, stream=None) -> dict:
     _check(lib().gbr_batch_solve(len(models), arr, _dptr(start, (torch.float64,)), iters, _hptr(E0), _hptr(arg),
                                  _hptr(sec), _stream(stream)))
     return dict(E0=E0, arg=arg.reshape(-1, 2), sector_E=sec)
+
+
+def gbr_batch_set_shape(threads: int, ctas_per_sm: int = 0):
+    _check(lib().gbr_batch_set_shape(threads, ctas_per_sm))
+
+
+def gbr_batch_get_shape() -> dict:
+    t, p = C.c_int(), C.c_int()
+    _check(lib().gbr_batch_get_shape(C.byref(t), C.byref(p)))
+    return dict(threads=t.value, ctas_per_sm=p.value)
+
+
+def gbr_batch_tune(models, start, iters: int, stream=None) -> dict:
+    import torch
+    arr, keep = _models(models)
+    ns, nst = gbr_batch_layout(models)
+    if start.numel() != nst:
+        raise ValueError(f"start has {start.numel()} entries, the batch has {nst} states")
+    sh = np.zeros(2, dtype=np.int32)
+    ms = np.zeros(9, dtype=np.float32)
+    _check(lib().gbr_batch_tune(len(models), arr, _dptr(start, (torch.float64,)), iters, _hptr(sh), _hptr(ms),
+                                _stream(stream)))
+    return dict(threads=int(sh[0]), ctas_per_sm=int(sh[1]), candidate_ms=ms.tolist())

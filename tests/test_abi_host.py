@@ -51,6 +51,27 @@ def test_null_handles_are_rejected_on_the_host(G):
     assert lib.gbr_ham_info(None, None, None) == G.GBR_EINVAL
 
 
+def test_shape_status_and_operator_lanczos_validate_on_the_host(G):
+    """The launch-shape, device-status and set/term Lanczos entry points
+    reject NULL arguments before touching a device."""
+    lib = C.CDLL(G.gbrank.LIB_PATH)
+    shape = (C.c_int * 6)(1, 64, 64, 64, 8, 1)
+    assert lib.gbr_ham_set_shape(None, 32, shape) == G.GBR_EINVAL
+    assert lib.gbr_ham_get_shape(None, 32, shape) == G.GBR_EINVAL
+    assert lib.gbr_device_status(0, None) == G.GBR_EINVAL
+    opts = G.gbrank.LanczosOpts(10, 0, 1, 1, 0, 0, 0, 0.0, 0.0)
+    res = G.gbrank.LanczosResult()
+    for fn in (lib.gbr_setham_lanczos, lib.gbr_termham_lanczos):
+        fn.argtypes = [C.c_void_p] * 8
+        assert fn(None, C.byref(opts), None, C.byref(res), None, None, None, None) == G.GBR_EINVAL
+        assert b"NULL" in lib_last_error(lib)
+
+
+def lib_last_error(lib):
+    lib.gbr_last_error.restype = C.c_char_p
+    return lib.gbr_last_error()
+
+
 def test_new_entry_points_validate_on_the_host(G):
     lib = C.CDLL(G.gbrank.LIB_PATH)
     members = np.array([1, 5, 9], dtype=np.uint64)

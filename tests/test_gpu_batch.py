@@ -59,3 +59,34 @@ def test_batch_256_models_sampled(G):
         L = h.shape[0]
         best = min(ref_sector_E(h, U, a, b) for a in range(L + 1) for b in range(L + 1))
         assert abs(res["E0"][m] - best) <= 1e-9 * max(1.0, abs(best))
+
+
+def test_batch_tuned_shapes_keep_parity(G):
+    """The batch autotuner times every launch shape (CTA size x CTAs per SM)
+    on a batch; the solve under every shape matches the oracle sector by
+    sector, and the tuner's pick becomes the process-wide shape."""
+    import gbr_synth.gpu as SG
+    models = [S.siam(m) for m in (3, 40, 101)]
+    ns, nst = G.gbr_batch_layout(models)
+    start = SG.uniform(S.SEED_START, nst)
+    ref = []
+    for h, U in models:
+        L = h.shape[0]
+        ref.extend(ref_sector_E(h, U, a, b) for a in range(L + 1) for b in range(L + 1))
+    ref = np.array(ref)
+    keep = G.gbr_batch_get_shape()
+    try:
+        for threads in (128, 256, 512):
+            for per_sm in (0, 2, 1):
+                G.gbr_batch_set_shape(threads, per_sm)
+                res = G.gbr_batch_solve(models, start, 150)
+                err = np.abs(res["sector_E"] - ref) / np.maximum(1.0, np.abs(ref))
+                assert err.max() <= 1e-9, (threads, per_sm, err.max())
+        t = G.gbr_batch_tune(models, start, 150)
+        assert (t["threads"], t["ctas_per_sm"]) in [(a, b) for a in (128, 256, 512) for b in (0, 2, 1)]
+        assert len(t["candidate_ms"]) == 9 and min(t["candidate_ms"]) > 0
+        assert G.gbr_batch_get_shape() == {"threads": t["threads"], "ctas_per_sm": t["ctas_per_sm"]}
+    finally:
+        G.gbr_batch_set_shape(keep["threads"], keep["ctas_per_sm"])
+    with pytest.raises(G.GbrError):
+        G.gbr_batch_set_shape(100, 0)

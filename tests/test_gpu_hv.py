@@ -164,3 +164,102 @@ def test_hv_full_size_hermitian_and_fused_agree(G):
     Hv2 = torch.empty_like(v)
     G.gbr_hv(H, v, Hv2)
     assert (Hv2 - Hv).abs().max().item() <= TOL64 * Hv.abs().max().item()
+
+
+# Sectors whose per-spin dimensions are multiples of 4, so that both gather
+# families run (the windowed one needs rows of whole 16-byte packs); each is
+# ragged against the 32- and 64-row tiles and the 512-byte column slices.
+WIN_KINDS = {
+    "ring12": lambda: (12, S.chain(12), S.uniform_U(12, 4.0), 6, 6),                 # 924 x 924
+    "ring12_unequal": lambda: (12, S.chain(12), S.uniform_U(12, 4.0), 5, 6),         # 792 x 924
+    "sq4x4_N3": lambda: (16, S.square(4, 4, 1.0, -0.3), S.uniform_U(16, 8.0), 3, 3),  # 560 x 560
+    "siam_bath7": lambda: (lambda h, U: (h.shape[0], h, U, 3, 3))(*S.siam(4)),            # 56 x 56, non-uniform hops
+}
+
+
+def _hv(G, H, x):
+    import torch
+    y = torch.full_like(x, float("nan"))
+    G.gbr_hv(H, x, y)
+    return y
+
+
+@pytest.mark.parametrize("kind", list(WIN_KINDS))
+@pytest.mark.parametrize("fp", [32, 64])
+def test_windowed_gathers_equal_plain_gathers_and_oracle(G, kind, fp):
+    """Every element sums its hops in the same order in both gather families
+    and under every tile, so the windowed H·v equals the plain one bit for
+    bit; both match the oracle."""
+    import torch
+    L, h, U, Nu, Nd = WIN_KINDS[kind]()
+    D = oracle.sector_dim(L, Nu, Nd)
+    H = G.gbr_ham_create(L, h, U, Nu, Nd)
+    G.gbr_ham_set_path(H, G.GBR_HV_FACTORED)
+    x = torch.from_numpy(S.start_vector(D)).cuda()
+    if fp == 32:
+        x = x.float()
+    G.gbr_ham_set_shape(H, fp, 0)
+    assert G.gbr_ham_get_shape(H, fp)["window"] == 0
+    y_plain = _hv(G, H, x)
+    y_ref = oracle.hv(L, h, U, Nu, Nd, x.double().cpu().numpy())
+    assert rel_inf(y_plain.cpu().numpy(), y_ref) <= (TOL64 if fp == 64 else TOL32)
+    for rows in ((32, 32, 32), (64, 64, 64), (64, 32, 64)):
+        G.gbr_ham_set_shape(H, fp, 1, *rows)
+        sh = G.gbr_ham_get_shape(H, fp)
+        if D % 4 == 0 and oracle.sector_dim(L, Nu, 0) % 4 == 0 and oracle.sector_dim(L, 0, Nd) % 4 == 0:
+            assert sh["window"] == 1 and (sh["rows_dn"], sh["rows_up"]) == rows[:2]
+        y_win = _hv(G, H, x)
+        assert torch.equal(y_win, y_plain), (kind, fp, rows)
+    assert G.gbr_device_status() == 0
+
+
+@pytest.mark.parametrize("fp", [32, 64])
+def test_windowed_gathers_stages_and_unaligned_vectors(G, fp):
+    """Stage-by-stage calls equal gbr_hv with the windowed family; vectors
+    off a 16-byte boundary make the combine pass fall back to the plain
+    kernel reading the row-major spin-down product, with identical results."""
+    import torch
+    L, h, U, Nu, Nd = WIN_KINDS["ring12"]()
+    D = oracle.sector_dim(L, Nu, Nd)
+    H = G.gbr_ham_create(L, h, U, Nu, Nd)
+    G.gbr_ham_set_path(H, G.GBR_HV_FACTORED)
+    G.gbr_ham_set_shape(H, fp, 1, 64, 64, 64)
+    dt = torch.float64 if fp == 64 else torch.float32
+    x = torch.from_numpy(S.start_vector(D)).cuda().to(dt)
+    y = _hv(G, H, x)
+    ys = torch.full_like(x, float("nan"))
+    for stage in (1, 2, 3, 4):
+        G.gbr_hv_stage(H, x, ys, stage)
+    assert torch.equal(ys, y)
+    xb = torch.zeros(D + 1, dtype=dt, device="cuda")
+    yb = torch.full((D + 1,), float("nan"), dtype=dt, device="cuda")
+    xb[1:] = x
+    G.gbr_hv(H, xb[1:], yb[1:])
+    assert torch.equal(yb[1:], y)
+
+
+@pytest.mark.parametrize("kind", ["ring10", "sq3x3", "siam", "nonuniformU", "one_site", "empty_spin"])
+def test_chunk_width_and_threads_per_state_keep_parity(G, kind):
+    """Every chunk width of the staggered tables (R = 8, 4) and every number
+    of threads per state of the fused kernel (1, 2, 4) against the oracle;
+    in the factored path R changes nothing (the ranks are the same)."""
+    import torch
+    L, h, U, Nu, Nd = model(kind)
+    x64 = torch.from_numpy(S.start_vector(oracle.sector_dim(L, Nu, Nd))).cuda()
+    y_ref = oracle.hv(L, h, U, Nu, Nd, x64.cpu().numpy())
+    H = G.gbr_ham_create(L, h, U, Nu, Nd)
+    G.gbr_ham_set_path(H, G.GBR_HV_FACTORED)
+    G.gbr_ham_set_shape(H, 64, 0, chunk_bits=8)
+    y8 = _hv(G, H, x64)
+    G.gbr_ham_set_shape(H, 64, 0, chunk_bits=4)
+    assert G.gbr_ham_get_shape(H, 64)["chunk_bits"] == 4
+    assert torch.equal(_hv(G, H, x64), y8)
+    G.gbr_ham_set_path(H, G.GBR_HV_FUSED)
+    for fp, x, tol in ((64, x64, TOL64), (32, x64.float(), TOL32)):
+        yr = y_ref if fp == 64 else oracle.hv(L, h, U, Nu, Nd, x.double().cpu().numpy())
+        for R in (8, 4):
+            for tps in (1, 2, 4):
+                G.gbr_ham_set_shape(H, fp, 0, chunk_bits=R, threads_per_state=tps)
+                sh = G.gbr_ham_get_shape(H, fp)
+                assert (sh["chunk_bits"], sh["threads_per_state"]) == (R, tps)
+                assert rel_inf(_hv(G, H, x).double().cpu().numpy(), yr) <= tol, (kind, fp, R, tps)

@@ -193,3 +193,50 @@ def test_basis_cache_is_reused_and_released(G):
     E.append(G.gbr_lanczos(H, v0(4900), 80, prec=G.GBR_PREC_MIXED, refine=True, store_basis=1)["E0"])
     G.gbr_release_cache()
     assert E[0] == E[1] == E[2]
+
+
+def _golden():
+    import json
+    import os
+    return json.load(open(os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden", "reference_energies.json")))
+
+
+def test_square4x4_U8_reduced_filling_against_oracle_lanczos(G):
+    """The 4x4 t' torus at U = 8 (the workload's geometry and couplings) at
+    N_up = N_dn = 3 (313,600 states), where the oracle's FP64 Lanczos is in
+    reach: FP64 within 1e-10, mixed with refinement within 1e-9."""
+    import torch
+    g = _golden()
+    ref = g["square4x4_tp_U8_N3_3_lanczos_E0"]
+    assert g["square4x4_tp_U8_N3_3_lanczos_change_last_50_steps"] <= 1e-12 * abs(ref)
+    H = G.gbr_ham_create(16, S.square(4, 4, 1.0, -0.3), S.uniform_U(16, 8.0), 3, 3)
+    D, _ = G.gbr_ham_info(H)
+    x = v0(D)
+    r64 = G.gbr_lanczos(H, x, 200, prec=G.GBR_PREC_FP64, refine=True)
+    assert abs(r64["E0"] - ref) <= 1e-10 * abs(ref), (r64["E0"], ref)
+    rm = G.gbr_lanczos(H, x, 200, prec=G.GBR_PREC_MIXED, refine=True)
+    assert abs(rm["E0"] - ref) <= 1e-9 * abs(ref), (rm["E0"], ref)
+    del x
+    torch.cuda.empty_cache()
+
+
+@pytest.mark.parametrize("U", [0.0, 4.0])
+def test_ring18_full_size_against_closed_form_and_bethe_ansatz(G, U):
+    """The 18-site ring at full size (2.36e9 states), 150 mixed-precision
+    steps with the Ritz vector recomputed and the FP64 refinement, as the
+    benchmark runs it: U = 0 against the sum of the lowest one-body levels,
+    U = 4 against the Lieb-Wu Bethe-ansatz energy."""
+    import torch
+    import gbr_synth.gpu as SG
+    g = _golden()
+    ref = g["chain18_U0_N9_9_free_E0"] if U == 0.0 else g["chain18_U4_N9_9_bethe_E0"]
+    H = G.gbr_ham_create(18, S.chain(18), S.uniform_U(18, U), 9, 9)
+    D, _ = G.gbr_ham_info(H)
+    s = SG.uniform(S.SEED_START, D)
+    r = G.gbr_lanczos(H, s, 150, prec=G.GBR_PREC_MIXED, refine=True, store_basis=0, use_graph=True)
+    assert abs(r["E0"] - ref) <= 1e-9 * abs(ref), (r["E0"], ref)
+    assert not r["stored_basis"]
+    H.close()
+    del s
+    G.gbr_release_cache()
+    torch.cuda.empty_cache()
