@@ -859,18 +859,19 @@ def profile_hv(n: int, sector: str = "sq4x4", shape: str = "", fp: int = 32):
     torch.cuda.synchronize()
 
 
-def profile_lanczos(n: int):
-    """A short mixed-precision Lanczos (n steps) on the benchmark sector, with
-    the same handle set-up as the timed steps: the target of the ncu captures
-    of the kernels as the benchmark launches them (fused Lanczos epilogue)."""
+def profile_lanczos(n: int, sector: str = "ring18"):
+    """A short mixed-precision Lanczos (n steps) on one sector, with the same
+    handle set-up as the timed steps (the autotuner's shape): the target of
+    the ncu captures of the kernels as the benchmark launches them (fused
+    Lanczos epilogue)."""
     import torch
     import __graft_entry__
     __graft_entry__.build()
     import gbr_synth as S
     import gbr_synth.gpu as SG
     import paper_2203_04158_gb300 as G
-    h, U = model()
-    H = G.gbr_ham_create(L, h, U, NUP, NDN)
+    Ls, hf, Uv, Nu, Nd = PROFILE_SECTORS[sector]
+    H = G.gbr_ham_create(Ls, hf(S), S.uniform_U(Ls, Uv), Nu, Nd)
     D, _ = G.gbr_ham_info(H)
     G.gbr_ham_tune(H, 32)
     s = SG.uniform(S.SEED_START, D)
@@ -926,7 +927,8 @@ def main():
                          "(half and quarter filling, M = 4..32) as JSON and exit")
     ap.add_argument("--profile-hv", type=int, default=0,
                     help="run this many H·v calls on --profile-sector and exit (for ncu captures)")
-    ap.add_argument("--profile-sector", default="sq4x4", choices=sorted(PROFILE_SECTORS))
+    ap.add_argument("--profile-sector", default="sq4x4", choices=sorted(PROFILE_SECTORS),
+                    help="sector of --profile-hv and --profile-lanczos")
     ap.add_argument("--profile-shape", default="", help="launch shape window,rows_dn,rows_up,rows_lz")
     ap.add_argument("--profile-fp", type=int, default=32, choices=[32, 64])
     args = ap.parse_args()
@@ -937,7 +939,7 @@ def main():
         profile_rank(args.profile_rank)
         return
     if args.profile_lanczos:
-        profile_lanczos(args.profile_lanczos)
+        profile_lanczos(args.profile_lanczos, args.profile_sector)
         return
     if args.eig_timings:
         import torch

@@ -48,7 +48,8 @@ enum {
     GBR_ECUDA = 3,       /* a CUDA runtime call failed */
     GBR_ENOTFOUND = 4,   /* a queried pattern is not a member (check mode) */
     GBR_ETIMEOUT = 5,    /* a bounded device-side wait ran out */
-    GBR_EBREAKDOWN = 6   /* Lanczos stopped early on an invariant subspace */
+    GBR_EBREAKDOWN = 6,  /* Lanczos stopped early on an invariant subspace */
+    GBR_ENONFINITE = 7   /* a non-finite value (NaN or Inf) appeared in a Lanczos scalar */
 };
 
 /* Rank value written for a pattern that is not in the set (check mode) and
@@ -145,6 +146,18 @@ int gbr_trie_info(const gbr_trie *t, int64_t *n_members, int64_t *n_elements, in
 int gbr_trie_build_host(const uint64_t *h_sorted, int64_t n, int M, int R, uint64_t *h_t, int64_t cap,
                         int64_t *size_out);
 
+/* A trie handle from a table kept by the caller (for example one written by
+ * gbr_trie_build_host_ordered in an earlier run and stored): the member list
+ * is validated as by gbr_trie_create_ordered and fixes the layout, and the
+ * table must have exactly that layout's length (cap entries, padding
+ * included; GBR_EINVAL otherwise); its contents are uploaded as given, not
+ * checked.  gbr_trie_rank with check = 1 verifies every result against the
+ * member list, which is what exposes a table that does not belong to it
+ * (queries it misroutes get GBR_NOT_FOUND_*).  The paper has no
+ * counterpart. */
+int gbr_trie_create_from_table(const uint64_t *h_sorted, int64_t n, int M, int R, int msb_first,
+                               const uint64_t *h_t, int64_t len, gbr_trie **out);
+
 /* gbr_trie_build_host with the dispatch order of gbr_trie_create_ordered. */
 int gbr_trie_build_host_ordered(const uint64_t *h_sorted, int64_t n, int M, int R, int msb_first, uint64_t *h_t,
                                 int64_t cap, int64_t *size_out);
@@ -217,9 +230,9 @@ int gbr_ham_get_path(const gbr_ham *H, int *path);
 int gbr_hv(const gbr_ham *H, const void *d_x, void *d_y, int fp, void *stream);
 
 /* gbr_hv for callers that cannot allocate device memory when they multiply
- * (for example code running while a stream is captured into a CUDA graph,
- * or under a fixed memory budget).  The paper has no counterpart: this is
- * an interface of this library.  It computes exactly what gbr_hv's factored
+ * (for example code under a fixed memory budget handed out by a host
+ * framework, or a loop that must never reach the allocator).  The paper has
+ * no counterpart: this is an interface of this library.  It computes exactly what gbr_hv's factored
  * path computes, but its two scratch vectors live in one static device array
  * of 64 MiB that every GPU loading the library reserves until the process
  * exits, so the call itself allocates nothing (no cudaMalloc or cudaFree).
@@ -227,8 +240,11 @@ int gbr_hv(const gbr_ham *H, const void *d_x, void *d_y, int fp, void *stream);
  *   must fit in 64 MiB (dim up to about 8.4 million in FP32, 4.2 million in
  *   FP64); larger sectors return GBR_EINVAL before anything is launched.
  *   Set-up: the first call on a device looks up the array's device address
- *   (cudaGetSymbolAddress) with that device current; make that first call
- *   before any stream capture.
+ *   (cudaGetSymbolAddress) with that device current and keeps it; make that
+ *   first call before any stream capture, and do not use the call after a
+ *   cudaDeviceReset of that device in the same process (the kept address
+ *   would be stale).  With lazy module loading the array is reserved when
+ *   the module first loads on the device, which may be that first call.
  *   Sharing: every call on a device uses the same array, so calls that can
  *   overlap on the GPU (other streams, other threads) race and must be
  *   ordered by the caller.  Nothing needs clearing between calls: every
@@ -246,8 +262,9 @@ int gbr_hv_static(const gbr_ham *H, const void *d_x, void *d_y, int fp, void *st
  *            plain gathers, row-major with the windowed ones;
  *   stage 4: y = H_up X + Dg o X + Z (row gathers, diagonal, combine).
  * Calling 1..4 in order on one stream equals gbr_hv with the factored path.
- * Arguments as for gbr_hv; the handle's scratch (two vectors of dim
- * elements) is allocated on first use, so one H·v at a time per handle. */
+ * Stages 3 and 4 return GBR_EINVAL until stage 1 has run on the handle and
+ * stage 2 (which allocates the handle's scratch, two vectors of dim elements)
+ * in this precision.  Arguments as for gbr_hv; one H·v at a time per handle. */
 int gbr_hv_stage(const gbr_ham *H, const void *d_x, void *d_y, int fp, int stage, void *stream);
 
 /* A call with a stored basis (store_basis) leaves the basis buffer, its one
@@ -281,7 +298,7 @@ int gbr_ham_tune(gbr_ham *H, int fp, void *stream);
 
 /* Launch shape of the H·v for precision fp: the knobs gbr_ham_tune sets,
  * exposed for tests and experiments (the paper has no counterpart).
- * h_shape: 6 ints (host).
+ * h_shape: 9 ints (host).
  *   [0]: 1 = windowed row gathers in the factored path (each CTA copies its
  *     TR own rows of a 512-byte column slice into shared memory with bulk
  *     copies, serves the hops that stay inside them from there, and the
@@ -292,17 +309,21 @@ int gbr_ham_tune(gbr_ham *H, int fp, void *stream);
  *   [4]: chunk width R of the per-spin staggered tables (Fig. fastrank):
  *     8 or 4 (0 = 8); the paper compares both inside the H·v (Sec. V-B);
  *   [5]: threads per state of the fused per-element kernel: 1, 2 or 4
- *     (0 = 1); the threads of a state split its occupied sites.
+ *     (0 = 1); the threads of a state split its occupied sites;
+ *   [6..8]: threads per CTA of the plain spin-down, spin-up and fused-update
+ *     passes: 128, or 64 for column chunks half as wide (0 = 128); the
+ *     windowed kernels always run 256 (reported as such).
  * In the factored path every element sums its hops in the same order under
- * every value of [0..4], so gbr_hv's results do not depend on them; [5]
- * changes the summation order of the fused kernel (a fixed butterfly).
+ * every value of [0..4] and [6..8], so gbr_hv's results do not depend on
+ * them; [5] changes the summation order of the fused kernel (a fixed
+ * butterfly).
  * The windowed family needs per-spin dimensions whose rows are whole 16-byte
  * packs (gbr_ham_get_shape reports 0 otherwise) and 16-byte aligned vectors
  * (a combine pass on other vectors runs the plain kernel).  Errors:
  * GBR_EINVAL for NULL arguments, fp other than 32 or 64, or values outside
  * the lists above. */
 int gbr_ham_set_shape(gbr_ham *H, int fp, const int *h_shape);
-/* The shape gbr_hv uses for precision fp (h_shape: 6 ints, as above). */
+/* The shape gbr_hv uses for precision fp (h_shape: 9 ints, as above). */
 int gbr_ham_get_shape(const gbr_ham *H, int fp, int *h_shape);
 
 /* Device status word of the library's kernels on the current device (the
@@ -462,7 +483,10 @@ typedef struct {
  * iters_done-1 off-diagonal entries; h_ritz (host, may be NULL): the lowest
  * Ritz value after every step.  Stops early (breakdown) when
  * beta_{k+1} <= 1e-13 max_j(|alpha_j|, beta_j).  Synchronises the stream.
- * Errors: GBR_EINVAL, GBR_ENOMEM (vectors do not fit), GBR_ECUDA. */
+ * Errors: GBR_EINVAL, GBR_ENOMEM (vectors do not fit), GBR_ECUDA,
+ * GBR_ENONFINITE (alpha or beta came out NaN or infinite: a NaN or Inf in the
+ * start vector propagates through H·v and the dots and stops the recurrence
+ * at the step where it appears; res->iters_done tells which). */
 int gbr_lanczos(const gbr_ham *H, const gbr_lanczos_opts *opts, const double *d_v0, gbr_lanczos_result *res,
                 double *h_alpha, double *h_beta, double *h_ritz, void *stream);
 

@@ -20,7 +20,8 @@ struct SpinSector {
     DevBuf diag;              // D doubles: sum_p h_pp n_p
     int hmax = 0;             // largest number of valid hops of one state
     int64_t hops = 0;         // total valid hops over all states
-    DevBuf hop_cnt;           // D uint16: valid hops of each state
+    DevBuf hop_cnt;           // D uint16: valid hops of each state (zero until the first ranking pass)
+    int lists_ready = 0;      // 1 once a ranking pass has written the hop lists
     DevBuf hop_tgt;           // hmax x D uint32 (k-major): target rank | sign << 31
     DevBuf hop_bond;          // hmax x D uint16: index into the bond table
 };
@@ -86,6 +87,9 @@ struct gbr_ham {
     // chunk width R of the per-spin staggered tables (8 or 4) and threads per
     // state of the fused per-element kernel (1, 2 or 4)
     int rank_R[2] = {8, 8}, fused_tps[2] = {1, 1};
+    // threads per CTA of the plain gather passes (spin-down, spin-up, fused
+    // update): 128, or 64 for column chunks half as wide
+    int gather_nt[3][2] = {{128, 128}, {128, 128}, {128, 128}};
     // scratch of the factored path (X^T and Z^T), grown on first use; one
     // H·v at a time per handle
     gbr::DevBuf ws_xt, ws_zt;

@@ -337,8 +337,10 @@ struct CombineArgs {
 // free the compiler takes up to 60 registers and the occupancy drops; at 12
 // or 16 CTAs it spills.  Measured on the 4x4 sector: 1.16 ms (10) against
 // 1.21 ms (free) and 1.25 ms (16).
-template <typename T, int VEC, int MODE, int TR>
-__global__ void __launch_bounds__(128, ((MODE >= 1 && sizeof(T) == 4) ? 10 : 1)) k_gather(const int64_t Drows, const int64_t Dcols, const int hmax,
+// NT threads per CTA (128, or 64 for column chunks half as wide: the
+// gathered rows of a chunk then take half the L2).
+template <typename T, int VEC, int MODE, int TR, int NT>
+__global__ void __launch_bounds__(NT, ((MODE >= 1 && sizeof(T) == 4) ? 1280 / NT : 1)) k_gather(const int64_t Drows, const int64_t Dcols, const int hmax,
                                                 const int64_t nrb, const uint16_t *__restrict__ cnt,
                                                 const uint32_t *__restrict__ tgt, const uint16_t *__restrict__ bond,
                                                 const T *__restrict__ bcoef, const int uniform, const T hu,
@@ -347,7 +349,7 @@ __global__ void __launch_bounds__(128, ((MODE >= 1 && sizeof(T) == 4) ? 10 : 1))
     constexpr bool LZ = MODE == 2;
     // row stride of the staged Z tile: 16 bytes of padding put the TR rows of
     // one column in different banks when the tile is written column by column
-    constexpr int ZS = 128 * VEC + 16 / (int)sizeof(T);
+    constexpr int ZS = NT * VEC + 16 / (int)sizeof(T);
     // hop-list row stride, a multiple of 4 so that four targets (and four
     // coefficients) are read with one 16-byte broadcast load
     const int hs = (hmax + 3) & ~3;
@@ -374,16 +376,16 @@ __global__ void __launch_bounds__(128, ((MODE >= 1 && sizeof(T) == 4) ? 10 : 1))
         }
     }
     __syncthreads();
-    const int64_t c0 = cc * (int64_t)(128 * VEC) + (int64_t)threadIdx.x * VEC;
+    const int64_t c0 = cc * (int64_t)(NT * VEC) + (int64_t)threadIdx.x * VEC;
     // combine epilogue: the block Z[r0..r0+TR, chunk] = (Z^T)[chunk, r0..r0+TR]
     // is read from Z^T once, column by column (TR consecutive values each),
     // into shared memory as [row][column]
     T *zs = reinterpret_cast<T *>(smr + (size_t)TR * hs * (4 + sizeof(T)));
     if (COMBINE && !ca.zrow) {
         const T *zt = (const T *)ca.zt;
-        const int64_t cbase = cc * (int64_t)(128 * VEC);
+        const int64_t cbase = cc * (int64_t)(NT * VEC);
         const int nrow = (int)((Drows - r0) < (int64_t)TR ? (Drows - r0) : (int64_t)TR);
-        for (int e = threadIdx.x; e < 128 * VEC * TR; e += blockDim.x) {
+        for (int e = threadIdx.x; e < NT * VEC * TR; e += blockDim.x) {
             const int col = e / TR, i = e % TR;
             const int64_t c = cbase + col;
             zs[i * ZS + col] = (c < Dcols && i < nrow) ? __ldg(zt + c * Drows + r0 + i) : T(0);
@@ -808,6 +810,7 @@ static int launch_hop_lists(const gbr_ham *H, const SpinSector &s, cudaStream_t 
         reinterpret_cast<const uint16_t *>(H->bonds.p) + 2 * H->k.nbond, s.hop_cnt.as<uint16_t>(),
         s.hop_tgt.as<uint32_t>(), s.hop_bond.as<uint16_t>(), s.hmax);
     GBR_LAUNCH_CHECK();
+    const_cast<SpinSector &>(s).lists_ready = 1;
     count_launches(1);
     return GBR_OK;
 }
@@ -863,7 +866,7 @@ static int ensure_ws(const gbr_ham *H, size_t bytes) {
 // the partial-sum sizing of the fused Lanczos epilogue).
 template <typename T>
 static void gather_shape(const gbr_ham *H, int64_t Drows, int64_t Dcols, bool aligned16, bool combine, bool lz,
-                         int *vec_out, int *tr_out) {
+                         int nt, int *vec_out, int *tr_out) {
     const int fpi = sizeof(T) == 8 ? 1 : 0;
     const int vmax = sizeof(T) == 4 ? 4 : 2;
     // widest vector whose column chunk (the rows one wave of CTAs gathers
@@ -873,7 +876,7 @@ static void gather_shape(const gbr_ham *H, int64_t Drows, int64_t Dcols, bool al
     const double cap = sizeof(T) == 4 ? 128e6 : 64e6;
     int vec = 1;
     for (int v = vmax; v >= 2; v /= 2)
-        if (aligned16 && Dcols % v == 0 && (double)Drows * 128 * v * sizeof(T) <= cap) { vec = v; break; }
+        if (aligned16 && Dcols % v == 0 && (double)Drows * nt * v * sizeof(T) <= cap) { vec = v; break; }
     const int tuned = lz ? H->tune_lz_rows[fpi] : (combine ? H->tune_up_rows[fpi] : H->tune_dn_rows[fpi]);
     // untuned default: 4 rows for the FP32 combine pass (its registers limit
     // occupancy; the tuner's pick on the 4x4 sector), 8 otherwise
@@ -952,28 +955,35 @@ static int launch_gather(const gbr_ham *H, const SpinSector &lists, int64_t Drow
     bool aligned16 = (((uintptr_t)w | (uintptr_t)z) & 15u) == 0;
     if (MODE == 2) aligned16 = aligned16 && (((uintptr_t)ca.lz.vprev) & 15u) == 0;
     int vec = 1, TR = 8;
-    gather_shape<T>(H, Drows, Dcols, aligned16, COMBINE, MODE == 2, &vec, &TR);
+    const int fpi = sizeof(T) == 8 ? 1 : 0;
+    const int NT = H->gather_nt[MODE][fpi] == 64 ? 64 : 128;
+    gather_shape<T>(H, Drows, Dcols, aligned16, COMBINE, MODE == 2, NT, &vec, &TR);
     const int64_t nrb = (Drows + TR - 1) / TR;
-    const int64_t ncc = (Dcols + 128 * vec - 1) / (128 * vec);
+    const int64_t ncc = (Dcols + NT * vec - 1) / (NT * vec);
     const int hmax = std::max(1, lists.hmax);
     const int hs = (hmax + 3) & ~3;   // the kernel's padded hop-list stride
-    const size_t smem = (size_t)TR * hs * (4 + sizeof(T)) + (COMBINE ? (size_t)TR * (128 * vec * sizeof(T) + 16) : 0);
+    const size_t smem = (size_t)TR * hs * (4 + sizeof(T)) + (COMBINE ? (size_t)TR * (NT * vec * sizeof(T) + 16) : 0);
     const int64_t blocks = nrb * ncc;
     if (blocks > 0x7FFFFFFF) return set_error(GBR_EINVAL, "sector too large for the gather grid");
-#define GBR_G(V, R)                                                                                          \
+#define GBR_G(V, R, N)                                                                                       \
     {                                                                                                        \
-        auto kern = k_gather<T, V, MODE, R>;                                                                 \
+        auto kern = k_gather<T, V, MODE, R, N>;                                                              \
         if (smem > 48 * 1024) GBR_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)); \
-        kern<<<(int)blocks, 128, smem, st>>>(Drows, Dcols, hmax, nrb, lists.hop_cnt.as<uint16_t>(),          \
-                                             lists.hop_tgt.as<uint32_t>(), lists.hop_bond.as<uint16_t>(),    \
-                                             (const T *)hd.bcoef, H->k.uniform, (T)H->k.hu, w, z, ca);        \
+        kern<<<(int)blocks, N, smem, st>>>(Drows, Dcols, hmax, nrb, lists.hop_cnt.as<uint16_t>(),            \
+                                           lists.hop_tgt.as<uint32_t>(), lists.hop_bond.as<uint16_t>(),      \
+                                           (const T *)hd.bcoef, H->k.uniform, (T)H->k.hu, w, z, ca);          \
+    }
+#define GBR_GN(V, R)                                                                                         \
+    {                                                                                                        \
+        if (NT == 64) GBR_G(V, R, 64) else GBR_G(V, R, 128)                                                  \
     }
 #define GBR_GV(V)                                                                                            \
     {                                                                                                        \
-        if (TR == 4) GBR_G(V, 4) else if (TR == 16) GBR_G(V, 16) else GBR_G(V, 8)                           \
+        if (TR == 4) GBR_GN(V, 4) else if (TR == 16) GBR_GN(V, 16) else GBR_GN(V, 8)                         \
     }
     if (vec == 4) GBR_GV(4) else if (vec == 2) GBR_GV(2) else GBR_GV(1)
 #undef GBR_GV
+#undef GBR_GN
 #undef GBR_G
     GBR_LAUNCH_CHECK();
     count_launches(1);
@@ -1094,9 +1104,10 @@ void *hv_xt_scratch(const gbr_ham *H, int fp) {
 }
 
 int64_t hv_lz_parts(const gbr_ham *H, int fp) {
-    // the smallest launch shape (vector width 1, 4 rows per CTA) bounds every grid
+    // the smallest launch shape (vector width 1, 4 rows and 64 threads per
+    // CTA) bounds every grid
     const int64_t nrb = (H->up.D + 3) / 4;
-    const int64_t ncc = (H->dn.D + 127) / 128;
+    const int64_t ncc = (H->dn.D + 63) / 64;
     (void)fp;
     return nrb * ncc;
 }
@@ -1112,6 +1123,15 @@ int hv_factored_with_scratch(const gbr_ham *H, const void *x, void *y, int fp, c
 
 int hv_stage(const gbr_ham *H, const void *x, void *y, int fp, int stage, cudaStream_t st) {
     const int fpi = fp == 64 ? 1 : 0;
+    // the gather stages read the hop lists (stage 1) and the handle's scratch
+    // (stage 2 allocates it): refuse them before those stages have run
+    if (stage >= 3) {
+        if (!H->up.lists_ready || !dn_lists(H).lists_ready)
+            return set_error(GBR_EINVAL, "stage %d before stage 1 (hop lists) on this handle", stage);
+        const size_t need = (size_t)H->D * (fp == 64 ? 8 : 4);
+        if (H->ws_xt.bytes < need || H->ws_zt.bytes < need)
+            return set_error(GBR_EINVAL, "stage %d before stage 2 (scratch) in this precision", stage);
+    }
     gbr_ham_prec *pb = prec_bufs(H, fpi);
     HamDev hd{pb->dup.p, pb->ddn.p, pb->uval.p, pb->bcoef.p, pb->hcoef.p};
     if (fp == 64) {
@@ -1175,6 +1195,9 @@ static int build_spin(gbr_ham *H, SpinSector &s, int N) {
     if (rc) return rc;
     const int64_t hm = std::max(1, hmax);
     if ((rc = s.hop_cnt.alloc((size_t)s.D * 2))) return rc;
+    // no hops until the first ranking pass writes the lists: a gather pass
+    // that ran before it reads empty lists, never stale targets
+    GBR_CUDA_TRY(cudaMemset(s.hop_cnt.p, 0, (size_t)s.D * 2));
     if ((rc = s.hop_tgt.alloc((size_t)(hm * s.D) * 4))) return rc;
     if ((rc = s.hop_bond.alloc((size_t)(hm * s.D) * 2))) return rc;
     return GBR_OK;
@@ -1385,8 +1408,14 @@ extern "C" int gbr_ham_set_shape(gbr_ham *H, int fp, const int *shape) {
     if (shape[4] != 0 && shape[4] != 4 && shape[4] != 8) return set_error(GBR_EINVAL, "chunk width %d must be 4 or 8", shape[4]);
     if (shape[5] != 0 && shape[5] != 1 && shape[5] != 2 && shape[5] != 4)
         return set_error(GBR_EINVAL, "threads per state %d must be 1, 2 or 4", shape[5]);
+    for (int i = 6; i < 9; ++i)
+        if (shape[i] != 0 && shape[i] != 64 && shape[i] != 128)
+            return set_error(GBR_EINVAL, "threads per CTA %d must be 64 or 128", shape[i]);
     H->rank_R[fpi] = shape[4] ? shape[4] : 8;
     H->fused_tps[fpi] = shape[5] ? shape[5] : 1;
+    H->gather_nt[0][fpi] = shape[6] ? shape[6] : 128;
+    H->gather_nt[1][fpi] = shape[7] ? shape[7] : 128;
+    H->gather_nt[2][fpi] = shape[8] ? shape[8] : 128;
     if (shape[0]) {
         H->win_dn[fpi] = shape[1];
         H->win_up[fpi] = shape[2];
@@ -1419,6 +1448,7 @@ extern "C" int gbr_ham_get_shape(const gbr_ham *H, int fp, int *shape) {
     }
     shape[4] = H->rank_R[fpi];
     shape[5] = H->fused_tps[fpi];
+    for (int i = 0; i < 3; ++i) shape[6 + i] = on ? 256 : H->gather_nt[i][fpi];
     return GBR_OK;
 }
 
@@ -1482,13 +1512,21 @@ extern "C" int gbr_ham_tune(gbr_ham *H, int fp, void *stream) {
     H->win_dn[fpi] = -1;
     for (int pass = 0; pass < 2; ++pass) {
         int *knob = pass == 0 ? &H->tune_up_rows[fpi] : &H->tune_dn_rows[fpi];
-        int best_tr = 8;
-        for (int tr : {4, 8, 16}) {
-            *knob = tr;
-            if ((rc = time_it(&ms))) goto done;
-            if (ms < best_plain || (tr == 8 && ms <= best_plain)) { best_plain = ms; best_tr = tr; }
-        }
+        int *nt_knob = &H->gather_nt[pass == 0 ? 1 : 0][fpi];
+        int best_tr = 8, best_nt = 128;
+        for (int nt : {128, 64})
+            for (int tr : {4, 8, 16}) {
+                *knob = tr;
+                *nt_knob = nt;
+                if ((rc = time_it(&ms))) goto done;
+                if (ms < best_plain || (tr == 8 && nt == 128 && ms <= best_plain)) {
+                    best_plain = ms;
+                    best_tr = tr;
+                    best_nt = nt;
+                }
+            }
         *knob = best_tr;
+        *nt_knob = best_nt;
     }
     {
         H->win_dn[fpi] = 0;
@@ -1536,14 +1574,17 @@ extern "C" int gbr_ham_tune(gbr_ham *H, int fp, void *stream) {
         };
         const bool winmode = H->win_dn[fpi] >= 0;
         float best_lz = 1e30f;
-        int best_tr = 0;
-        for (int tr : {4, 8, 16, 32, 64}) {
-            if (winmode != (tr >= 32)) continue;
-            (winmode ? H->win_lz[fpi] : H->tune_lz_rows[fpi]) = tr;
-            if ((rc = time_lz(&ms))) goto done;
-            if (ms < best_lz) { best_lz = ms; best_tr = tr; }
-        }
+        int best_tr = 0, best_nt = 128;
+        for (int nt : {128, 64})
+            for (int tr : {4, 8, 16, 32, 64}) {
+                if (winmode != (tr >= 32) || (winmode && nt != 128)) continue;
+                (winmode ? H->win_lz[fpi] : H->tune_lz_rows[fpi]) = tr;
+                H->gather_nt[2][fpi] = nt;
+                if ((rc = time_lz(&ms))) goto done;
+                if (ms < best_lz) { best_lz = ms; best_tr = tr; best_nt = nt; }
+            }
         (winmode ? H->win_lz[fpi] : H->tune_lz_rows[fpi]) = best_tr;
+        H->gather_nt[2][fpi] = best_nt;
     }
     // chunk width of the per-spin tables in the factored path (its ranking
     // pass only), then the fused per-element kernel over chunk width and

@@ -3,12 +3,10 @@
 // gbr_hv's factored path keeps two scratch vectors (X^T and its product
 // with the spin-down hop lists) in the Hamiltonian handle and allocates them
 // with cudaMalloc on first use.  Some callers cannot allocate at the moment
-// they multiply: code running while a stream is being captured into a CUDA
-// graph (cudaMalloc is not a capturable operation), code that runs under a
-// fixed memory budget handed out by a host framework, or real-time loops
-// that must not hit the allocator.  gbr_hv_static gives them the same
-// product with the scratch in one file-scope device array of fixed size,
-// so the call itself never allocates.
+// they multiply: code that runs under a fixed memory budget handed out by a
+// host framework, or real-time loops that must never reach the allocator.
+// gbr_hv_static gives them the same product with the scratch in one
+// file-scope device array of fixed size, so the call itself never allocates.
 #include <mutex>
 
 #include "ham.h"
@@ -17,7 +15,9 @@ namespace gbr {
 
 // Scratch for the two vectors of the factored path.  Reserved in device
 // memory of every GPU on which this library's module is loaded, until the
-// process exits.
+// process exits; with CUDA's lazy module loading the module (and so the
+// array) is loaded on the device by its first use, which may be the first
+// gbr_hv_static call.
 constexpr size_t kStaticScratchBytes = (size_t)64 << 20;   // 64 MiB
 __device__ __align__(256) unsigned char g_hv_scratch[kStaticScratchBytes];
 
@@ -27,7 +27,9 @@ static std::mutex g_scratch_mu;
 
 // Device address of g_hv_scratch on the current device.  In host code the
 // symbol is only a host-side stand-in, so the address must come from
-// cudaGetSymbolAddress, once per device, with that device current.
+// cudaGetSymbolAddress, once per device, with that device current.  The
+// address is cached per device: after cudaDeviceReset it is stale, so the
+// entry point must not be used after a reset of the device in this process.
 static int scratch_address(void **out) {
     int dev = 0;
     GBR_CUDA_TRY(cudaGetDevice(&dev));

@@ -39,6 +39,7 @@ struct LzState {
     double scale;     // max_j(|alpha_j|, beta_j)
     double lam_hint;  // convergence test: previous lowest Ritz value and its last decrease
     double gap_hint;
+    int nonfinite;    // 1 once alpha or beta came out NaN or infinite (stops the recurrence)
 };
 
 // 16-byte packs of vector elements for the streaming kernels: every vector
@@ -241,7 +242,16 @@ __global__ void __launch_bounds__(kFinThreads) k_finalize(LzState *st, double *a
         alpha[k] = a;
         scal[kScal * k + 2] = a * scal[kScal * k];
         st->scale = fmax(st->scale, fabs(a));
+        if (!isfinite(a)) {
+            st->stop = 1;
+            st->nonfinite = 1;
+        }
     } else {
+        if (!isfinite(s)) {
+            st->stop = 1;
+            st->nonfinite = 1;
+            return;
+        }
         const double b = sqrt(fmax(s, 0.0));
         beta[k + 1] = b;
         scal[kScal * (k + 1)] = 1.0 / b;
@@ -706,6 +716,9 @@ static int lz_run(Lz &z, const double *d_v0, gbr_lanczos_result *res, const gbr_
     // steps done: k (advanced once per completed non-final step) + 1 for the step that set stop
     const int kdone = std::min(z.iters, hs.k + 1);
     res->iters_done = kdone;
+    if (hs.nonfinite)
+        return set_error(GBR_ENONFINITE, "Lanczos step %d produced a non-finite alpha or beta (NaN or Inf in the "
+                         "start vector or the operator)", hs.k);
     res->breakdown = hs.breakdown;
     res->converged = hs.converged;
     res->stored_basis = z.store;

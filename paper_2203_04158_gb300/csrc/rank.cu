@@ -1,6 +1,7 @@
 // Ranking and unranking kernels for fixed-popcount sectors (staggered
 // lookup, Sec. III-B of Wallerberger & Held) and for packed tries (Sec. IV).
 #include <algorithm>
+#include <mutex>
 #include <cstring>
 
 #include "gbr_common.h"
@@ -346,8 +347,39 @@ static int launch_comb_rank(const gbr_comb *c, const uint64_t *pat, RT *out, int
     return GBR_OK;
 }
 
+// The walk reads the leading ("hot") levels with the L2 evict_last policy.
+// The L2 keeps such lines only inside its persisting set-aside, which is
+// empty unless the context asks for one, so the hot levels were evicted by
+// the random reads of the large levels.  This sizes the set-aside to the hot
+// levels (at most the device's maximum), once per process and device; the
+// set-aside belongs to this process's CUDA context and ends with it.
+static size_t g_persist_done[64] = {0};
+static std::mutex g_persist_mu;
+
+size_t ensure_persisting_l2(size_t bytes) {
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return 0;
+    std::lock_guard<std::mutex> lock(g_persist_mu);
+    if (g_persist_done[dev] >= bytes) return g_persist_done[dev];
+    int maxp = 0;
+    if (cudaDeviceGetAttribute(&maxp, cudaDevAttrMaxPersistingL2CacheSize, dev) != cudaSuccess || maxp <= 0) {
+        cudaGetLastError();
+        return 0;
+    }
+    size_t cur = 0;
+    cudaDeviceGetLimit(&cur, cudaLimitPersistingL2CacheSize);
+    const size_t want = std::min(bytes, (size_t)maxp);
+    if (cur < want && cudaDeviceSetLimit(cudaLimitPersistingL2CacheSize, want) != cudaSuccess) {
+        cudaGetLastError();   // no set-aside on this device (e.g. a MIG slice): the walk still runs
+        return 0;
+    }
+    g_persist_done[dev] = std::max(cur, want);
+    return g_persist_done[dev];
+}
+
 template <typename E, typename RT>
 static int launch_trie_rank(const gbr_trie *T, const uint64_t *pat, RT *out, int64_t n, int check, cudaStream_t st) {
+    ensure_persisting_l2((size_t)T->hot_entries * sizeof(E));
     TrieK d;
     memset(&d, 0, sizeof(d));
     d.H = T->H;
@@ -472,16 +504,11 @@ extern "C" int gbr_comb_unrank(const gbr_comb *c, const void *d_rank, int rank_b
     return GBR_OK;
 }
 
-extern "C" int gbr_trie_create_ordered(const uint64_t *h_sorted, int64_t n, int M, int R, int msb_first,
-                                       gbr_trie **out) {
-    clear_error();
-    if (!out) return set_error(GBR_EINVAL, "out is NULL");
-    *out = nullptr;
-    if (msb_first != 0 && msb_first != 1) return set_error(GBR_EINVAL, "msb_first=%d must be 0 or 1", msb_first);
-    TriePlan plan;
-    std::vector<uint64_t> t;
-    int rc = trie_build(h_sorted, n, M, R, &plan, &t, msb_first);
-    if (rc) return rc;
+namespace gbr {
+// Handle from a trie plan and its table (entries as uint64, padding included).
+static int trie_upload(const uint64_t *h_sorted, int64_t n, int M, int R, int msb_first, const TriePlan &plan,
+                       std::vector<uint64_t> &t, gbr_trie **out) {
+    int rc = GBR_OK;
     gbr_trie *T = new (std::nothrow) gbr_trie();
     if (!T) return set_error(GBR_ENOMEM, "host allocation failed");
     T->M = M; T->R = R; T->H = plan.H;
@@ -518,6 +545,38 @@ extern "C" int gbr_trie_create_ordered(const uint64_t *h_sorted, int64_t n, int 
     if (rc) { delete T; return rc; }
     *out = T;
     return GBR_OK;
+}
+}  // namespace gbr
+
+extern "C" int gbr_trie_create_ordered(const uint64_t *h_sorted, int64_t n, int M, int R, int msb_first,
+                                       gbr_trie **out) {
+    clear_error();
+    if (!out) return set_error(GBR_EINVAL, "out is NULL");
+    *out = nullptr;
+    if (msb_first != 0 && msb_first != 1) return set_error(GBR_EINVAL, "msb_first=%d must be 0 or 1", msb_first);
+    TriePlan plan;
+    std::vector<uint64_t> t;
+    int rc = trie_build(h_sorted, n, M, R, &plan, &t, msb_first);
+    if (rc) return rc;
+    return trie_upload(h_sorted, n, M, R, msb_first, plan, t, out);
+}
+
+extern "C" int gbr_trie_create_from_table(const uint64_t *h_sorted, int64_t n, int M, int R, int msb_first,
+                                          const uint64_t *h_t, int64_t len, gbr_trie **out) {
+    clear_error();
+    if (!out) return set_error(GBR_EINVAL, "out is NULL");
+    *out = nullptr;
+    if (msb_first != 0 && msb_first != 1) return set_error(GBR_EINVAL, "msb_first=%d must be 0 or 1", msb_first);
+    if (!h_t) return set_error(GBR_EINVAL, "NULL table");
+    TriePlan plan;
+    std::vector<uint64_t> t;
+    int rc = trie_build(h_sorted, n, M, R, &plan, &t, msb_first);   // the member list's layout
+    if (rc) return rc;
+    if (len != (int64_t)t.size())
+        return set_error(GBR_EINVAL, "table of %lld entries, the member list's trie has %lld", (long long)len,
+                         (long long)t.size());
+    t.assign(h_t, h_t + len);
+    return trie_upload(h_sorted, n, M, R, msb_first, plan, t, out);
 }
 
 extern "C" int gbr_trie_create(const uint64_t *h_sorted, int64_t n, int M, int R, gbr_trie **out) {

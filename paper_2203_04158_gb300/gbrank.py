@@ -20,7 +20,7 @@ LIB_PATH = os.path.join(_HERE, "_build", "libgbrank.so")
 _lock = threading.Lock()
 _lib = None
 
-GBR_OK, GBR_EINVAL, GBR_ENOMEM, GBR_ECUDA, GBR_ENOTFOUND, GBR_ETIMEOUT, GBR_EBREAKDOWN = range(7)
+GBR_OK, GBR_EINVAL, GBR_ENOMEM, GBR_ECUDA, GBR_ENOTFOUND, GBR_ETIMEOUT, GBR_EBREAKDOWN, GBR_ENONFINITE = range(8)
 GBR_RANK_STAGGERED, GBR_RANK_CNS = 0, 1
 GBR_HV_AUTO, GBR_HV_FUSED, GBR_HV_FACTORED = 0, 1, 2
 GBR_PREC_FP64, GBR_PREC_MIXED = 0, 1
@@ -78,6 +78,7 @@ def lib():
                 "gbr_trie_create_ordered": (i32, [vp, i64, i32, i32, i32, vp]),
                 "gbr_trie_build_host_ordered": (i32, [vp, i64, i32, i32, i32, vp, i64, vp]),
                 "gbr_trie_destroy": (None, [vp]),
+                "gbr_trie_create_from_table": (i32, [vp, i64, i32, i32, i32, vp, i64, vp]),
                 "gbr_trie_info": (i32, [vp, vp, vp, vp, vp]),
                 "gbr_trie_build_host": (i32, [vp, i64, i32, i32, vp, i64, vp]),
                 "gbr_trie_rank": (i32, [vp, vp, vp, i32, i64, i32, vp]),
@@ -254,6 +255,16 @@ def gbr_trie_create(sorted_members: np.ndarray, M: int, R: int = 8, msb_first: b
     return Trie(p)
 
 
+def gbr_trie_create_from_table(sorted_members: np.ndarray, M: int, R: int, table: np.ndarray,
+                               msb_first: bool = False) -> Trie:
+    a = np.ascontiguousarray(sorted_members, dtype=np.uint64)
+    t = np.ascontiguousarray(table, dtype=np.uint64)
+    p = C.c_void_p()
+    _check(lib().gbr_trie_create_from_table(_hptr(a), a.size, M, R, int(bool(msb_first)), _hptr(t), t.size,
+                                            C.byref(p)))
+    return Trie(p)
+
+
 def gbr_trie_info(t: Trie):
     nm, ne, eb, lv = C.c_int64(), C.c_int64(), C.c_int(), C.c_int()
     _check(lib().gbr_trie_info(t, C.byref(nm), C.byref(ne), C.byref(eb), C.byref(lv)))
@@ -335,16 +346,19 @@ def gbr_ham_tune(H: Ham, fp: int = 32, stream=None):
 
 
 def gbr_ham_set_shape(H: Ham, fp: int, window: int, rows_dn: int = 0, rows_up: int = 0, rows_lz: int = 0,
-                      chunk_bits: int = 0, threads_per_state: int = 0):
-    sh = np.array([window, rows_dn, rows_up, rows_lz, chunk_bits, threads_per_state], dtype=np.int32)
+                      chunk_bits: int = 0, threads_per_state: int = 0, threads_dn: int = 0, threads_up: int = 0,
+                      threads_lz: int = 0):
+    sh = np.array([window, rows_dn, rows_up, rows_lz, chunk_bits, threads_per_state, threads_dn, threads_up,
+                   threads_lz], dtype=np.int32)
     _check(lib().gbr_ham_set_shape(H, fp, _hptr(sh)))
 
 
 def gbr_ham_get_shape(H: Ham, fp: int) -> dict:
-    sh = np.zeros(6, dtype=np.int32)
+    sh = np.zeros(9, dtype=np.int32)
     _check(lib().gbr_ham_get_shape(H, fp, _hptr(sh)))
     return dict(window=int(sh[0]), rows_dn=int(sh[1]), rows_up=int(sh[2]), rows_lz=int(sh[3]),
-                chunk_bits=int(sh[4]), threads_per_state=int(sh[5]))
+                chunk_bits=int(sh[4]), threads_per_state=int(sh[5]), threads_dn=int(sh[6]),
+                threads_up=int(sh[7]), threads_lz=int(sh[8]))
 
 
 def gbr_device_status(clear: bool = True) -> int:

@@ -55,7 +55,7 @@ def test_shape_status_and_operator_lanczos_validate_on_the_host(G):
     """The launch-shape, device-status and set/term Lanczos entry points
     reject NULL arguments before touching a device."""
     lib = C.CDLL(G.gbrank.LIB_PATH)
-    shape = (C.c_int * 6)(1, 64, 64, 64, 8, 1)
+    shape = (C.c_int * 9)(1, 64, 64, 64, 8, 1, 0, 0, 0)
     assert lib.gbr_ham_set_shape(None, 32, shape) == G.GBR_EINVAL
     assert lib.gbr_ham_get_shape(None, 32, shape) == G.GBR_EINVAL
     assert lib.gbr_device_status(0, None) == G.GBR_EINVAL

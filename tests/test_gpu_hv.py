@@ -188,8 +188,8 @@ def _hv(G, H, x):
 @pytest.mark.parametrize("fp", [32, 64])
 def test_windowed_gathers_equal_plain_gathers_and_oracle(G, kind, fp):
     """Every element sums its hops in the same order in both gather families
-    and under every tile, so the windowed H·v equals the plain one bit for
-    bit; both match the oracle."""
+    and under every tile and CTA width, so every shape gives the plain H·v
+    bit for bit; it matches the oracle."""
     import torch
     L, h, U, Nu, Nd = WIN_KINDS[kind]()
     D = oracle.sector_dim(L, Nu, Nd)
@@ -203,6 +203,11 @@ def test_windowed_gathers_equal_plain_gathers_and_oracle(G, kind, fp):
     y_plain = _hv(G, H, x)
     y_ref = oracle.hv(L, h, U, Nu, Nd, x.double().cpu().numpy())
     assert rel_inf(y_plain.cpu().numpy(), y_ref) <= (TOL64 if fp == 64 else TOL32)
+    for nt in (64, 128):
+        for rows in ((4, 16, 8), (16, 4, 4)):
+            G.gbr_ham_set_shape(H, fp, 0, *rows, threads_dn=nt, threads_up=nt, threads_lz=nt)
+            assert G.gbr_ham_get_shape(H, fp)["threads_up"] == nt
+            assert torch.equal(_hv(G, H, x), y_plain), (kind, fp, nt, rows)
     for rows in ((32, 32, 32), (64, 64, 64), (64, 32, 64)):
         G.gbr_ham_set_shape(H, fp, 1, *rows)
         sh = G.gbr_ham_get_shape(H, fp)
@@ -263,3 +268,31 @@ def test_chunk_width_and_threads_per_state_keep_parity(G, kind):
                 sh = G.gbr_ham_get_shape(H, fp)
                 assert (sh["chunk_bits"], sh["threads_per_state"]) == (R, tps)
                 assert rel_inf(_hv(G, H, x).double().cpu().numpy(), yr) <= tol, (kind, fp, R, tps)
+
+
+@pytest.mark.parametrize("fp", [32, 64])
+def test_quarter_filled_open_chain_sampled_rows(G, fp):
+    """The quarter-filled open chain of Eq. Hring (L = 16, N_up = N_dn = 4,
+    3.3 million states; the low-filling regime of Sec. V-B): sampled rows of
+    both paths and both chunk widths against the oracle, which reads x_j from
+    the seeded generator on demand."""
+    import torch
+    import gbr_synth.gpu as SG
+    L, N = 16, 4
+    h, U = S.chain(L, pbc=False), S.uniform_U(L, 4.0)
+    H = G.gbr_ham_create(L, h, U, N, N)
+    D, _ = G.gbr_ham_info(H)
+    x = SG.uniform(S.SEED_START, D)
+    if fp == 32:
+        x = x.float()
+    rows = np.unique(np.concatenate([[0, 1, D - 1], S.bounded(23, np.arange(400, dtype=np.uint64), D)])).astype(np.int64)
+    y_ref = oracle.hv_rows_seeded(L, h, U, N, N, S.SEED_START, rows)
+    idx = torch.from_numpy(rows).cuda()
+    tol = TOL64 if fp == 64 else TOL32
+    for path in (G.GBR_HV_FUSED, G.GBR_HV_FACTORED):
+        G.gbr_ham_set_path(H, path)
+        for R in (8, 4):
+            G.gbr_ham_set_shape(H, fp, 0, chunk_bits=R)
+            y = torch.empty_like(x)
+            G.gbr_hv(H, x, y)
+            assert rel_inf(y[idx].double().cpu().numpy(), y_ref) <= tol, (path, R)

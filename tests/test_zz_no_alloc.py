@@ -1,6 +1,7 @@
 """gbr_hv_static, the H·v entry point for callers that cannot allocate
-device memory when they multiply (for example while a stream is being
-captured into a CUDA graph, or under a fixed memory budget).
+device memory when they multiply (for example code that runs under a fixed
+memory budget handed out by a host framework, or a loop that must never
+reach the allocator).
 
 It must give the same product as gbr_hv, call after call, with its scratch
 in the library's static device array instead of freshly allocated memory.
@@ -33,22 +34,60 @@ def sectors():
 
 @pytest.mark.parametrize("fp", [32, 64])
 def test_static_scratch_hv_matches_gbr_hv_on_consecutive_calls(G, fp):
+    """Same kernels and launch shapes as gbr_hv's factored path, so the two
+    products agree bit for bit (the tolerance of the other parity tests is
+    checked as well); the first call on a fresh handle comes before any
+    gbr_hv and must not allocate the handle's own scratch."""
     import torch
     import gbr_synth.gpu as SG
+    # one call on another handle first: with lazy module loading it is the
+    # call that loads the module holding the static array (64 MiB), which is
+    # not an allocation by the call being measured below
+    Hw = G.gbr_ham_create(8, S.chain(8), S.uniform_U(8, 4.0), 4, 4)
+    xw = torch.zeros(4900, dtype=torch.float32 if fp == 32 else torch.float64, device="cuda")
+    G.gbr_hv_static(Hw, xw, torch.empty_like(xw))
     for L, h, U, Nu, Nd in sectors():
         H = G.gbr_ham_create(L, h, U, Nu, Nd)
+        G.gbr_ham_set_path(H, G.GBR_HV_FACTORED)
         D, _ = G.gbr_ham_info(H)
         for call, seed in enumerate((41, 42)):
             x = SG.uniform(seed, D)
             if fp == 32:
                 x = x.float()
+            y = torch.full_like(x, float("nan"))
+            torch.cuda.synchronize()
+            free0 = torch.cuda.mem_get_info()[0]
+            G.gbr_hv_static(H, x, y)
+            torch.cuda.synchronize()
+            if call == 0:
+                # one scratch vector is D * fp / 8 bytes: the call took none
+                assert free0 - torch.cuda.mem_get_info()[0] < D * fp // 8
             y_ref = torch.empty_like(x)
             G.gbr_hv(H, x, y_ref)
-            y = torch.full_like(x, float("nan"))
-            G.gbr_hv_static(H, x, y)
             torch.cuda.synchronize()
             err = rel_inf(y.double().cpu().numpy(), y_ref.double().cpu().numpy())
             assert err <= TOL[fp], (L, Nu, Nd, fp, call, err)
+            assert torch.equal(y, y_ref), (L, Nu, Nd, fp, call)
+
+
+def test_static_scratch_limit_is_per_precision(G):
+    """A 14-site ring with N_up = 5, N_dn = 7 (6,870,864 states): its two
+    FP32 scratch vectors (55 MB) fit the 64 MiB array, its FP64 ones do not."""
+    import torch
+    import gbr_synth.gpu as SG
+    H = G.gbr_ham_create(14, S.chain(14), S.uniform_U(14, 4.0), 5, 7)
+    G.gbr_ham_set_path(H, G.GBR_HV_FACTORED)
+    D, _ = G.gbr_ham_info(H)
+    assert D == 6870864
+    x = SG.uniform(43, D).float()
+    y, y_ref = torch.empty_like(x), torch.empty_like(x)
+    G.gbr_hv_static(H, x, y)
+    G.gbr_hv(H, x, y_ref)
+    assert torch.equal(y, y_ref)
+    x64 = x.double()
+    with pytest.raises(G.GbrError) as e:
+        G.gbr_hv_static(H, x64, torch.empty_like(x64))
+    assert e.value.code == G.GBR_EINVAL and "scratch" in str(e.value)
 
 
 def test_static_scratch_rejects_sectors_beyond_its_size(G):
