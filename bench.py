@@ -299,7 +299,9 @@ def ranking_extras(G, torch):
     torch.cuda.synchronize()
     t = e0.elapsed_time(e1) / 1e3 / reps
     out["staggered_M32_N16"] = {"queries": n, "ranks_per_s": n / t, "ms": t * 1e3,
-                                "GBs": 12 * n / t / 1e9, "frac_of_hbm": 12 * n / t / 1e9 / hbm}
+                                "GBs": 12 * n / t / 1e9, "frac_of_hbm": 12 * n / t / 1e9 / hbm,
+                                "roofline": {"bound": "hbm", "bytes_per_query": 12, "achieved_GBs": 12 * n / t / 1e9,
+                                             "peak": hbm, "frac": 12 * n / t / 1e9 / hbm}}
     ps, _ = torch.sort(pats)
     G.gbr_comb_rank(c, ps, r)
     e0.record()
@@ -326,8 +328,13 @@ def ranking_extras(G, torch):
     e1.record()
     torch.cuda.synchronize()
     t = e0.elapsed_time(e1) / 1e3 / reps
+    hbm, _ = peaks()
     out["trie_40bit_2p24"] = {"queries": n, "ranks_per_s": n / t, "ms": t * 1e3,
-                              "overhead_f": info["n_elements"] / info["n_members"], "levels": info["levels"]}
+                              "overhead_f": info["n_elements"] / info["n_members"], "levels": info["levels"],
+                              "roofline": {"bound": "hbm", "bytes_per_query": 76,
+                                           "note": "8 B query + 4 B rank + one 32-byte sector of each of the two "
+                                                   "levels beyond L2 (1.7 GiB and 75 MiB)",
+                                           "achieved_GBs": 76 * n / t / 1e9, "frac": 76 * n / t / 1e9 / hbm}}
     qs, _ = torch.sort(q)
     G.gbr_trie_rank(tr, qs, r)
     e0.record()
@@ -337,6 +344,7 @@ def ranking_extras(G, torch):
     torch.cuda.synchronize()
     t = e0.elapsed_time(e1) / 1e3 / reps
     out["trie_40bit_2p24_sorted"] = {"ranks_per_s": n / t, "ms": t * 1e3}
+
     # the same set in a trie dispatched from the most significant chunk
     trm = G.gbr_trie_create(members, 40, 8, msb_first=True)
     infm = G.gbr_trie_info(trm)
@@ -859,9 +867,10 @@ def profile_hv(n: int, sector: str = "sq4x4", shape: str = "", fp: int = 32):
     torch.cuda.synchronize()
 
 
-def profile_lanczos(n: int, sector: str = "ring18"):
+def profile_lanczos(n: int, sector: str = "ring18", shape: str = ""):
     """A short mixed-precision Lanczos (n steps) on one sector, with the same
-    handle set-up as the timed steps (the autotuner's shape): the target of
+    handle set-up as the timed steps (the autotuner's shape, or the given
+    shape "window,rows_dn,rows_up,rows_lz,..." without tuning): the target of
     the ncu captures of the kernels as the benchmark launches them (fused
     Lanczos epilogue)."""
     import torch
@@ -873,7 +882,11 @@ def profile_lanczos(n: int, sector: str = "ring18"):
     Ls, hf, Uv, Nu, Nd = PROFILE_SECTORS[sector]
     H = G.gbr_ham_create(Ls, hf(S), S.uniform_U(Ls, Uv), Nu, Nd)
     D, _ = G.gbr_ham_info(H)
-    G.gbr_ham_tune(H, 32)
+    if shape:
+        G.gbr_ham_set_path(H, G.GBR_HV_FACTORED)
+        G.gbr_ham_set_shape(H, 32, *[int(v) for v in shape.split(",")])
+    else:
+        G.gbr_ham_tune(H, 32)
     s = SG.uniform(S.SEED_START, D)
     G.gbr_lanczos(H, s, n, prec=G.GBR_PREC_MIXED, refine=False, store_basis=0, profile=True)
     torch.cuda.synchronize()
@@ -939,7 +952,7 @@ def main():
         profile_rank(args.profile_rank)
         return
     if args.profile_lanczos:
-        profile_lanczos(args.profile_lanczos, args.profile_sector)
+        profile_lanczos(args.profile_lanczos, args.profile_sector, args.profile_shape)
         return
     if args.eig_timings:
         import torch
