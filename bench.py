@@ -122,14 +122,16 @@ def src_hash():
     return h.hexdigest()[:16]
 
 
-def ncu_traffic(kernel: str):
-    """DRAM bytes per launch of the kernel from the committed ncu summary, or
-    None if there is none or the kernel source changed since it was taken."""
+def ncu_traffic(kernel: str, workload: str = WORKLOAD):
+    """DRAM bytes per launch of the kernel (here: per FP32 H·v as the Lanczos
+    launches it, summed over its kernels) from the committed ncu summary of a
+    full-size capture, or None if there is none or the kernel source changed
+    since it was taken."""
     p = os.path.join(ROOT, "profiles", "ncu_counters.json")
     if not os.path.exists(p):
         return None
     d = json.load(open(p))
-    e = d.get(WORKLOAD, {}).get(kernel)
+    e = d.get(workload, {}).get(kernel)
     if not e or e.get("src_hash") != src_hash():
         return None
     return e.get("dram_bytes_per_launch_full_size")
@@ -521,7 +523,7 @@ def square_extras(G, torch):
                        "mixed_rel_err": abs(rmt["E0"] - ref) / abs(ref), "fp64_s": rdt["seconds"],
                        "fp64_iters": rdt["iters"], "fp64_rel_err": abs(rdt["E0"] - ref) / abs(ref),
                        "speedup": rdt["seconds"] / rmt["seconds"]},
-           "roofline": stage_roofline(rp, D, elems, G),
+           "roofline": stage_roofline(rp, D, elems, G, name),
            "hv_paths": hv_path_extras(G, torch, H, s)}
     H.close()
     del s
@@ -652,7 +654,7 @@ def hv_count(r) -> int:
     return n + 1
 
 
-def stage_roofline(r, D: int, elems: int, G):
+def stage_roofline(r, D: int, elems: int, G, workload: str = WORKLOAD):
     """Roofline of the FP32 H·v as the Lanczos launches it, from a profiled
     solve (CUDA events at the stage boundaries of every H·v on the launching
     stream): hop lists, spin-down gather, spin-up gather with diagonal,
@@ -670,7 +672,8 @@ def stage_roofline(r, D: int, elems: int, G):
     k = int(np.argmax(st))
     onchip = (elems - D) * 4                      # one 4-byte gather per off-diagonal matrix element
     return {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s", "frac": achieved / hbm,
-            "traffic": None, "kernel": "fp32_hv (hop lists + spin-down gather + spin-up gather with combine)",
+            "traffic": ncu_traffic("fp32_hv_lanczos", workload),
+            "kernel": "fp32_hv (hop lists + spin-down gather + spin-up gather with combine)",
             "peak_source": src, "avg_launch_ms": t_hv * 1e3, "algorithmic_bytes_per_launch": alg,
             "timing": "profiled solve outside the timed steps, CUDA events per stage on the launching stream",
             "dominant_kernel": {"name": names[k], "avg_launch_ms": float(per[k] * 1e3),

@@ -447,6 +447,72 @@ __global__ void __launch_bounds__(kRedThreads) k_ritz_accum3(const T *__restrict
     }
 }
 
+// The same sum for FP32 vectors in FP32 arithmetic: x holds an unevaluated
+// pair (hi, lo) of floats in each 8-byte slot, every term is added as the
+// exact FP32 product of the coefficient's leading part plus the product with
+// its trailing part (c = c_hi + c_lo), in two-float sums -- about 2^-48 of
+// each term, with FP32 instructions only (the FP64 pipe of this GPU runs the
+// FP64 version of this sum at a third of the memory rate).  k_ritz_finish_ff
+// turns the pairs into doubles once the sum is complete.
+__global__ void __launch_bounds__(kRedThreads) k_ritz_accum3_ff(const float *__restrict__ u0, const float *__restrict__ u1,
+                                                                const float *__restrict__ u2, int cnt, const double *s,
+                                                                const double *scal, int j0, int64_t n,
+                                                                float2 *__restrict__ x2) {
+    float ch[3], cl[3];
+#pragma unroll
+    for (int t = 0; t < 3; ++t) {
+        const double c = t < cnt ? s[j0 + t] * scal[kScal * (j0 + t)] : 0.0;
+        ch[t] = (float)c;
+        cl[t] = (float)(c - (double)ch[t]);
+    }
+    const int64_t np = n / 4;
+    const int64_t tid = blockIdx.x * (int64_t)blockDim.x + threadIdx.x, stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t p = tid; p < np; p += stride) {
+        float4 a[3];
+        a[0] = __ldcs(reinterpret_cast<const float4 *>(u0) + p);
+        a[1] = cnt > 1 ? __ldcs(reinterpret_cast<const float4 *>(u1) + p) : make_float4(0.f, 0.f, 0.f, 0.f);
+        a[2] = cnt > 2 ? __ldcs(reinterpret_cast<const float4 *>(u2) + p) : make_float4(0.f, 0.f, 0.f, 0.f);
+        float4 xa = make_float4(0.f, 0.f, 0.f, 0.f), xb = xa;
+        if (j0) {
+            xa = reinterpret_cast<const float4 *>(x2)[2 * p];
+            xb = reinterpret_cast<const float4 *>(x2)[2 * p + 1];
+        }
+        FF acc[4] = {{xa.x, xa.y}, {xa.z, xa.w}, {xb.x, xb.y}, {xb.z, xb.w}};
+#pragma unroll
+        for (int t = 0; t < 3; ++t) {
+            if (t >= cnt) break;
+            const float v[4] = {a[t].x, a[t].y, a[t].z, a[t].w};
+#pragma unroll
+            for (int e = 0; e < 4; ++e) {
+                ff_add_prod(acc[e], ch[t], v[e]);
+                acc[e].lo = fmaf(cl[t], v[e], acc[e].lo);
+            }
+        }
+        reinterpret_cast<float4 *>(x2)[2 * p] = make_float4(acc[0].hi, acc[0].lo, acc[1].hi, acc[1].lo);
+        reinterpret_cast<float4 *>(x2)[2 * p + 1] = make_float4(acc[2].hi, acc[2].lo, acc[3].hi, acc[3].lo);
+    }
+    for (int64_t i = np * 4 + tid; i < n; i += stride) {
+        FF acc = j0 ? FF{x2[i].x, x2[i].y} : FF{0.f, 0.f};
+        const float v[3] = {u0[i], cnt > 1 ? u1[i] : 0.f, cnt > 2 ? u2[i] : 0.f};
+#pragma unroll
+        for (int t = 0; t < 3; ++t) {
+            if (t >= cnt) break;
+            ff_add_prod(acc, ch[t], v[t]);
+            acc.lo = fmaf(cl[t], v[t], acc.lo);
+        }
+        x2[i] = make_float2(acc.hi, acc.lo);
+    }
+}
+
+// x[i] = hi + lo in FP64, in place (each thread reads and writes its own slots)
+__global__ void __launch_bounds__(kRedThreads) k_ritz_finish_ff(double *__restrict__ x, int64_t n) {
+    const float2 *x2 = reinterpret_cast<const float2 *>(x);
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        const float2 v = x2[i];
+        x[i] = (double)v.x + (double)v.y;
+    }
+}
+
 // FP64 dots <a,b> partials (refinement)
 __global__ void __launch_bounds__(kRedThreads) k_dot64(const double *__restrict__ a, const double *__restrict__ b,
                                                        int64_t n, double *part) {
@@ -778,8 +844,13 @@ static int lz_run(Lz &z, const double *d_v0, gbr_lanczos_result *res, const gbr_
                     const T *u0 = z.buf[j0 % 3].as<T>();
                     const T *u1 = cnt > 1 ? z.buf[(j0 + 1) % 3].as<T>() : u0;
                     const T *u2 = cnt > 2 ? z.buf[(j0 + 2) % 3].as<T>() : u0;
-                    k_ritz_accum3<T><<<z.grid, kRedThreads, 0, s>>>(u0, u1, u2, cnt, sv, z.scal.as<double>(), j0, n,
-                                                                  x.as<double>());
+                    if (sizeof(T) == 4)
+                        k_ritz_accum3_ff<<<z.grid, kRedThreads, 0, s>>>((const float *)u0, (const float *)u1,
+                                                                        (const float *)u2, cnt, sv, z.scal.as<double>(),
+                                                                        j0, n, x.as<float2>());
+                    else
+                        k_ritz_accum3<T><<<z.grid, kRedThreads, 0, s>>>(u0, u1, u2, cnt, sv, z.scal.as<double>(), j0,
+                                                                      n, x.as<double>());
                     count_launches(1);
                     j0 = j + 1;
                 }
@@ -788,6 +859,10 @@ static int lz_run(Lz &z, const double *d_v0, gbr_lanczos_result *res, const gbr_
                     if (rc) return rc;
                 }
                 ph = (ph + 1) % 3;
+            }
+            if (sizeof(T) == 4) {
+                k_ritz_finish_ff<<<z.grid, kRedThreads, 0, s>>>(x.as<double>(), n);
+                count_launches(1);
             }
         }
         GBR_LAUNCH_CHECK();
