@@ -45,13 +45,29 @@ struct HamK {
 // pass: w = H u_k / g_k - (beta_k / g_{k-1}) u_{k-1} (k read from device
 // memory) and per-CTA partial sums of <w, u_k> (part may be NULL).  The two
 // factors are precomputed: scal[4k] = 1/g_k, scal[4k+1] = beta_k / g_{k-1}
-// (0 at k = 0).
+// (0 at k = 0).  With xt_next set (a second run of the recurrence, alpha_k
+// already stored in scal[4k+2] = alpha_k / g_k) the epilogue also finishes
+// the step: w - (alpha_k / g_k) u_k = u_{k+1} goes to y row-major and, through
+// the CTA's Z tile, transposed to xt_next (X^T of the next H·v); no partials.
 struct LzHook {
     const void *vprev;
     const double *scal;
     const int *kstate;
     double *part;
+    void *xt_next = nullptr;
 };
+
+// The recurrence's two updates with their roundings spelled out, so that every
+// kernel computing a step (the fused epilogue, the separate update kernels,
+// the first and the second run) rounds it the same way: s * w - b * p with
+// s * w rounded first, and w - a * x with one rounding.  Left to itself the
+// compiler may contract s * w - b * p either way round.
+__device__ __forceinline__ float lz_rec(float s, float w, float b, float p) { return __fmaf_rn(-b, p, __fmul_rn(s, w)); }
+__device__ __forceinline__ double lz_rec(double s, double w, double b, double p) {
+    return __fma_rn(-b, p, __dmul_rn(s, w));
+}
+__device__ __forceinline__ float lz_fnma(float a, float x, float w) { return __fmaf_rn(-a, x, w); }
+__device__ __forceinline__ double lz_fnma(double a, double x, double w) { return __fma_rn(-a, x, w); }
 
 // Device work buffers of a Lanczos solve, kept between calls and grown when
 // needed (one set per operator handle).
@@ -115,9 +131,12 @@ bool hv_is_factored(const gbr_ham *H);
 // factored H·v with the fused Lanczos epilogue; *nparts receives the number
 // of partial sums written (the grid of the spin-up pass)
 // xt_ready: X^T is already in the handle's scratch (written by the previous
-// step's update), so the transpose is skipped
+// step's update), so the transpose is skipped.  With hook.xt_next set,
+// *updated tells whether the spin-up pass finished the step (u_{k+1} in y,
+// its transpose in xt_next); when it could not (windowed passes, or a launch
+// shape without full 16-byte vectors) y holds w and the caller updates.
 int hv_launch_lz(const gbr_ham *H, const void *x, void *y, int fp, cudaStream_t st, cudaEvent_t *ev, const LzHook &hook,
-                 int *nparts, bool xt_ready = false);
+                 int *nparts, bool xt_ready = false, bool *updated = nullptr);
 // the handle's X^T scratch for precision fp (allocated if needed; NULL on failure)
 void *hv_xt_scratch(const gbr_ham *H, int fp);
 // upper bound of the partial sums hv_launch_lz writes for precision fp

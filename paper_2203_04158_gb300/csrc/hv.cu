@@ -332,7 +332,10 @@ struct CombineArgs {
 // as 1, then the first update of a Lanczos step on unnormalised vectors
 // u_j = g_j v_j (g_0 = 1, g_j = beta_j) in the same epilogue,
 // w = y / g_k - (beta_k / g_{k-1}) u_{k-1} (k > 0; x = u_k) and the block's
-// partial <w, x>.
+// partial <w, x>.  MODE 3: as 2 on a second run of the recurrence (alpha_k
+// known, no partials), then u_{k+1} = w - (alpha_k / g_k) x to y and, through
+// the Z tile (each thread overwrites the values it read), transposed to
+// ca.lz.xt_next once the CTA's rows are done.
 // The FP32 combine passes are held to 10 CTAs per SM (48 registers): left
 // free the compiler takes up to 60 registers and the occupancy drops; at 12
 // or 16 CTAs it spills.  Measured on the 4x4 sector: 1.16 ms (10) against
@@ -346,14 +349,15 @@ __global__ void __launch_bounds__(NT, ((MODE >= 1 && sizeof(T) == 4) ? 1280 / NT
                                                 const T *__restrict__ bcoef, const int uniform, const T hu,
                                                 const T *__restrict__ x, T *__restrict__ y, const CombineArgs ca) {
     constexpr bool COMBINE = MODE >= 1;
-    constexpr bool LZ = MODE == 2;
+    constexpr bool LZ = MODE >= 2;
+    constexpr bool UPD = MODE == 3;
     // row stride of the staged Z tile: 16 bytes of padding put the TR rows of
     // one column in different banks when the tile is written column by column
     constexpr int ZS = NT * VEC + 16 / (int)sizeof(T);
     // hop-list row stride, a multiple of 4 so that four targets (and four
     // coefficients) are read with one 16-byte broadcast load
     const int hs = (hmax + 3) & ~3;
-    extern __shared__ __align__(16) unsigned char smr[];
+    extern __shared__ __align__(128) unsigned char smr[];
     uint32_t *st = reinterpret_cast<uint32_t *>(smr);
     T *sc = reinterpret_cast<T *>(smr + (size_t)TR * hs * 4);
     __shared__ int scnt[64];
@@ -395,11 +399,12 @@ __global__ void __launch_bounds__(NT, ((MODE >= 1 && sizeof(T) == 4) ? 1280 / NT
     const bool active = c0 < Dcols;
     DotAcc<T> dacc;
     int klz = 0;
-    T slz = T(1), blz = T(0);
+    T slz = T(1), blz = T(0), alz = T(0);
     if (LZ) {
         klz = *ca.lz.kstate;
         slz = (T)ca.lz.scal[4 * klz];
         blz = (T)ca.lz.scal[4 * klz + 1];
+        if (UPD) alz = (T)ca.lz.scal[4 * klz + 2];
     }
     // combine epilogue: column states and diagonals of this thread's columns
     uint32_t ad[VEC];
@@ -513,10 +518,22 @@ __global__ void __launch_bounds__(NT, ((MODE >= 1 && sizeof(T) == 4) ? 1280 / NT
                         vp[0] = __ldcs(vpv);
                     }
 #pragma unroll
-                    for (int v = 0; v < VEC; ++v) acc[v] = slz * acc[v] - blz * vp[v];
+                    for (int v = 0; v < VEC; ++v) acc[v] = lz_rec(slz, acc[v], blz, vp[v]);
                 }
+                if (UPD) {
 #pragma unroll
-                for (int v = 0; v < VEC; ++v) dacc.add(acc[v], xo[v]);
+                    for (int v = 0; v < VEC; ++v) acc[v] = lz_fnma(alz, xo[v], acc[v]);
+                    if (VEC == 4 && sizeof(T) == 4) {
+                        *reinterpret_cast<float4 *>(zs + i * ZS + threadIdx.x * VEC) =
+                            make_float4((float)acc[0], (float)acc[1 % VEC], (float)acc[2 % VEC], (float)acc[3 % VEC]);
+                    } else {
+#pragma unroll
+                        for (int v = 0; v < VEC; ++v) zs[i * ZS + threadIdx.x * VEC + v] = acc[v];
+                    }
+                } else {
+#pragma unroll
+                    for (int v = 0; v < VEC; ++v) dacc.add(acc[v], xo[v]);
+                }
             }
         }
         if (VEC == 4 && sizeof(T) == 4) {
@@ -529,7 +546,19 @@ __global__ void __launch_bounds__(NT, ((MODE >= 1 && sizeof(T) == 4) ? 1280 / NT
             y[r * Dcols + c0] = acc[0];
         }
     }
-    if (LZ && ca.lz.part) {
+    if (UPD) {
+        // u_{k+1} of the CTA's rows and columns, TR consecutive values per
+        // column of the transpose (as the Z tile was read)
+        __syncthreads();
+        T *xt = (T *)ca.lz.xt_next;
+        const int64_t cbase = cc * (int64_t)(NT * VEC);
+        const int nrow = (int)((Drows - r0) < (int64_t)TR ? (Drows - r0) : (int64_t)TR);
+        for (int e = threadIdx.x; e < NT * VEC * TR; e += blockDim.x) {
+            const int col = e / TR, i = e % TR;
+            const int64_t c = cbase + col;
+            if (c < Dcols && i < nrow) __stcs(xt + c * Drows + r0 + i, zs[i * ZS + col]);
+        }
+    } else if (LZ && ca.lz.part) {
         const double r = block_sum(dacc.value());
         if (threadIdx.x == 0) ca.lz.part[blockIdx.x] = r;
     }
@@ -747,7 +776,7 @@ __global__ void __launch_bounds__(256, 2) k_gwin(const int64_t Drows, const int6
                         T vp[VEC];
                         WinVec<T>::get(vp, __ldcs(reinterpret_cast<const V *>((const T *)ca.lz.vprev + r * Dcols + c0 + cl)));
 #pragma unroll
-                        for (int v = 0; v < VEC; ++v) acc[v] = slz * acc[v] - blz * vp[v];
+                        for (int v = 0; v < VEC; ++v) acc[v] = lz_rec(slz, acc[v], blz, vp[v]);
                     }
 #pragma unroll
                     for (int v = 0; v < VEC; ++v) dacc.add(acc[v], xo[v]);
@@ -937,11 +966,22 @@ static int launch_gwin(const gbr_ham *H, const SpinSector &lists, int64_t Drows,
 }
 
 // One row-gather pass Z = H_lists W (+ the combine epilogue, + the Lanczos update).
+// MODE 3 runs only with full 16-byte vectors and the Z tile (the caller has
+// checked that the windowed passes are off); on any other launch shape it
+// launches nothing and sets *declined.
 template <typename T, int MODE>
 static int launch_gather(const gbr_ham *H, const SpinSector &lists, int64_t Drows, int64_t Dcols, const T *w, T *z,
-                         const CombineArgs &ca, cudaStream_t st, const HamDev &hd, int *grid_out = nullptr) {
+                         const CombineArgs &ca, cudaStream_t st, const HamDev &hd, int *grid_out = nullptr,
+                         bool *declined = nullptr) {
     constexpr bool COMBINE = MODE >= 1;
-    if (gwin_on<T>(H)) {
+    constexpr int VM = 16 / (int)sizeof(T);
+    if (declined) *declined = false;
+    if constexpr (MODE == 3) {
+        if (ca.zrow || !ca.lz.xt_next) {
+            if (declined) *declined = true;
+            return GBR_OK;
+        }
+    } else if (gwin_on<T>(H)) {
         // the windowed kernels need every vector on a 16-byte boundary
         uintptr_t al = (uintptr_t)w | (uintptr_t)z;
         if (COMBINE) al |= (uintptr_t)ca.zt;
@@ -953,11 +993,15 @@ static int launch_gather(const gbr_ham *H, const SpinSector &lists, int64_t Drow
         // unaligned vectors falls through to the plain kernel reading Z row-major
     }
     bool aligned16 = (((uintptr_t)w | (uintptr_t)z) & 15u) == 0;
-    if (MODE == 2) aligned16 = aligned16 && (((uintptr_t)ca.lz.vprev) & 15u) == 0;
+    if (MODE >= 2) aligned16 = aligned16 && (((uintptr_t)ca.lz.vprev) & 15u) == 0;
     int vec = 1, TR = 8;
     const int fpi = sizeof(T) == 8 ? 1 : 0;
-    const int NT = H->gather_nt[MODE][fpi] == 64 ? 64 : 128;
-    gather_shape<T>(H, Drows, Dcols, aligned16, COMBINE, MODE == 2, NT, &vec, &TR);
+    const int NT = H->gather_nt[MODE >= 2 ? 2 : MODE][fpi] == 64 ? 64 : 128;
+    gather_shape<T>(H, Drows, Dcols, aligned16, COMBINE, MODE >= 2, NT, &vec, &TR);
+    if (MODE == 3 && vec != VM) {
+        if (declined) *declined = true;
+        return GBR_OK;
+    }
     const int64_t nrb = (Drows + TR - 1) / TR;
     const int64_t ncc = (Dcols + NT * vec - 1) / (NT * vec);
     const int hmax = std::max(1, lists.hmax);
@@ -981,7 +1025,11 @@ static int launch_gather(const gbr_ham *H, const SpinSector &lists, int64_t Drow
     {                                                                                                        \
         if (TR == 4) GBR_GN(V, 4) else if (TR == 16) GBR_GN(V, 16) else GBR_GN(V, 8)                         \
     }
-    if (vec == 4) GBR_GV(4) else if (vec == 2) GBR_GV(2) else GBR_GV(1)
+    if constexpr (MODE == 3) {
+        GBR_GV(VM)
+    } else {
+        if (vec == 4) GBR_GV(4) else if (vec == 2) GBR_GV(2) else GBR_GV(1)
+    }
 #undef GBR_GV
 #undef GBR_GN
 #undef GBR_G
@@ -1022,7 +1070,8 @@ static int stage_dn(const gbr_ham *H, cudaStream_t st, const HamDev &hd, const S
 // Y = H_up X + Dg o X + (Z^T)^T
 template <typename T>
 static int stage_up(const gbr_ham *H, const T *x, T *y, cudaStream_t st, const HamDev &hd,
-                    const Scratch *ws = nullptr, const LzHook *hook = nullptr, int *nparts = nullptr) {
+                    const Scratch *ws = nullptr, const LzHook *hook = nullptr, int *nparts = nullptr,
+                    bool *updated = nullptr) {
     CombineArgs ca;
     ca.lz = hook ? *hook : LzHook{nullptr, nullptr, nullptr, nullptr};
     ca.st_up = H->up.states.as<uint32_t>();
@@ -1033,6 +1082,16 @@ static int stage_up(const gbr_ham *H, const T *x, T *y, cudaStream_t st, const H
     ca.zt = ws ? ws->zt : H->ws_zt.p;
     ca.hk = H->k;
     ca.zrow = gwin_on<T>(H) ? 1 : 0;
+    if (updated) *updated = false;
+    if (hook && hook->xt_next) {
+        bool declined = true;
+        int rc = launch_gather<T, 3>(H, H->up, H->up.D, H->dn.D, x, y, ca, st, hd, nparts, &declined);
+        if (rc || !declined) {
+            if (!rc && updated) *updated = true;
+            return rc;
+        }
+        ca.lz.xt_next = nullptr;
+    }
     if (hook) return launch_gather<T, 2>(H, H->up, H->up.D, H->dn.D, x, y, ca, st, hd, nparts);
     return launch_gather<T, 1>(H, H->up, H->up.D, H->dn.D, x, y, ca, st, hd, nparts);
 }
@@ -1040,7 +1099,7 @@ static int stage_up(const gbr_ham *H, const T *x, T *y, cudaStream_t st, const H
 template <typename T>
 static int launch_factored(const gbr_ham *H, const T *x, T *y, cudaStream_t st, const HamDev &hd,
                            cudaEvent_t *ev = nullptr, const Scratch *ws = nullptr, const LzHook *hook = nullptr,
-                           int *nparts = nullptr, bool xt_ready = false) {
+                           int *nparts = nullptr, bool xt_ready = false, bool *updated = nullptr) {
     if (ev) cudaEventRecord(ev[0], st);
     int rc = stage_hop_lists<T>(H, st);
     if (rc) return rc;
@@ -1049,7 +1108,7 @@ static int launch_factored(const gbr_ham *H, const T *x, T *y, cudaStream_t st, 
     if (ev) cudaEventRecord(ev[2], st);
     if ((rc = stage_dn<T>(H, st, hd, ws))) return rc;
     if (ev) cudaEventRecord(ev[3], st);
-    if ((rc = stage_up<T>(H, x, y, st, hd, ws, hook, nparts))) return rc;
+    if ((rc = stage_up<T>(H, x, y, st, hd, ws, hook, nparts, updated))) return rc;
     if (ev) cudaEventRecord(ev[4], st);
     return GBR_OK;
 }
@@ -1089,13 +1148,15 @@ bool hv_is_factored(const gbr_ham *H) {
 }
 
 int hv_launch_lz(const gbr_ham *H, const void *x, void *y, int fp, cudaStream_t st, cudaEvent_t *ev, const LzHook &hook,
-                 int *nparts, bool xt_ready) {
+                 int *nparts, bool xt_ready, bool *updated) {
     const int fpi = fp == 64 ? 1 : 0;
     gbr_ham_prec *pb = prec_bufs(H, fpi);
     HamDev hd{pb->dup.p, pb->ddn.p, pb->uval.p, pb->bcoef.p, pb->hcoef.p};
     if (fp == 64)
-        return launch_factored<double>(H, (const double *)x, (double *)y, st, hd, ev, nullptr, &hook, nparts, xt_ready);
-    return launch_factored<float>(H, (const float *)x, (float *)y, st, hd, ev, nullptr, &hook, nparts, xt_ready);
+        return launch_factored<double>(H, (const double *)x, (double *)y, st, hd, ev, nullptr, &hook, nparts, xt_ready,
+                                       updated);
+    return launch_factored<float>(H, (const float *)x, (float *)y, st, hd, ev, nullptr, &hook, nparts, xt_ready,
+                                  updated);
 }
 
 void *hv_xt_scratch(const gbr_ham *H, int fp) {

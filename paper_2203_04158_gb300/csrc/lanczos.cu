@@ -80,7 +80,7 @@ __global__ void __launch_bounds__(kRedThreads) k_step1(const LzState *st, const 
         if (k > 0) {
             const Pack<T> pp = VP[p];
 #pragma unroll
-            for (int j = 0; j < V; ++j) wp.e[j] = s1 * wp.e[j] - b * pp.e[j];
+            for (int j = 0; j < V; ++j) wp.e[j] = lz_rec(s1, wp.e[j], b, pp.e[j]);
             W[p] = wp;
         }
         if (want_dot)
@@ -89,7 +89,7 @@ __global__ void __launch_bounds__(kRedThreads) k_step1(const LzState *st, const 
     }
     for (int64_t i = np * V + tid; i < n; i += stride) {
         T wi = w[i];
-        if (k > 0) wi = s1 * wi - b * vprev[i];
+        if (k > 0) wi = lz_rec(s1, wi, b, vprev[i]);
         w[i] = wi;
         if (want_dot) acc.add(wi, v[i]);
     }
@@ -121,7 +121,7 @@ __global__ void __launch_bounds__(kRedThreads) k_step2(const LzState *st, const 
         Pack<T> wp = W[p];
         const Pack<T> vv = VV[p];
 #pragma unroll
-        for (int j = 0; j < V; ++j) wp.e[j] -= a * vv.e[j];
+        for (int j = 0; j < V; ++j) wp.e[j] = lz_fnma(a, vv.e[j], wp.e[j]);
         W[p] = wp;
         if (vb) VB[p] = wp;
         if (want_dot)
@@ -129,7 +129,7 @@ __global__ void __launch_bounds__(kRedThreads) k_step2(const LzState *st, const 
             for (int j = 0; j < V; ++j) acc.add(wp.e[j], wp.e[j]);
     }
     for (int64_t i = np * V + tid; i < n; i += stride) {
-        const T wi = w[i] - a * v[i];
+        const T wi = lz_fnma(a, v[i], w[i]);
         w[i] = wi;
         if (vb) vb[i] = wi;
         if (want_dot) acc.add(wi, wi);
@@ -163,7 +163,7 @@ __global__ void __launch_bounds__(256) k_step2_t(const LzState *st, const double
             Pack<T> wp = *reinterpret_cast<const Pack<T> *>(w + r * cols + c);
             const Pack<T> vv = *reinterpret_cast<const Pack<T> *>(v + r * cols + c);
 #pragma unroll
-            for (int e = 0; e < V; ++e) wp.e[e] -= a * vv.e[e];
+            for (int e = 0; e < V; ++e) wp.e[e] = lz_fnma(a, vv.e[e], wp.e[e]);
             *reinterpret_cast<Pack<T> *>(w + r * cols + c) = wp;
 #pragma unroll
             for (int e = 0; e < V; ++e) {
@@ -175,7 +175,7 @@ __global__ void __launch_bounds__(256) k_step2_t(const LzState *st, const double
             for (int e = 0; e < V; ++e) {
                 T wi = T(0);
                 if (r < rows && c + e < cols) {
-                    wi = w[r * cols + c + e] - a * v[r * cols + c + e];
+                    wi = lz_fnma(a, v[r * cols + c + e], w[r * cols + c + e]);
                     w[r * cols + c + e] = wi;
                     if (want_dot) acc.add(wi, wi);
                 }
@@ -616,11 +616,15 @@ static int lz_step(Lz &z, int phase, bool pass2, cudaEvent_t *ev4, bool want_rit
     double *part = z.part.as<double>();
     int64_t nk = 0;
     int nparts = z.grid;
+    bool updated = false;
     if (z.factored()) {
-        // w = H v - beta_k v_{k-1} and the partials of <w, v> in the H·v epilogue
-        const LzHook hook{vprev, z.scal.as<double>(), &st->k, pass2 ? nullptr : part};
+        // w = H v - beta_k v_{k-1} and the partials of <w, v> in the H·v
+        // epilogue; in the second run (alpha_k stored) the epilogue also
+        // finishes the step and writes X^T of u_{k+1} when it can
+        LzHook hook{vprev, z.scal.as<double>(), &st->k, pass2 ? nullptr : part};
+        if (pass2 && z.fuse_t) hook.xt_next = z.xt;
         // X^T comes from the previous step's update except in each pass's first step
-        int rc = hv_launch_lz(z.op.ham, v, w, z.fp, z.st, ev4, hook, &nparts, z.fuse_t && !first);
+        int rc = hv_launch_lz(z.op.ham, v, w, z.fp, z.st, ev4, hook, &nparts, z.fuse_t && !first, &updated);
         if (rc) return rc;
     } else {
         int rc = z.apply(v, w, z.fp, z.st, ev4);
@@ -636,16 +640,19 @@ static int lz_step(Lz &z, int phase, bool pass2, cudaEvent_t *ev4, bool want_rit
     // with re-orthogonalisation the basis slot is written after it
     T *slot_basis = (z.store && !pass2 && !z.reorth && !basis_slots) ? z.basis.as<T>() : nullptr;
     int nparts2 = z.grid;
-    if (z.fuse_t) {
+    if (updated) {
+        // u_{k+1} and its transpose came out of the H·v (second run only)
+    } else if (z.fuse_t) {
         const int64_t rows = z.op.ham->up.D, cols = z.op.ham->dn.D;
         const dim3 g((unsigned)((cols + 63) / 64), (unsigned)((rows + 63) / 64));
         k_step2_t<T><<<g, 256, 0, z.st>>>(st, z.scal.as<double>(), v, w, (T *)z.xt, rows, cols, part, pass2 ? 0 : 1);
         nparts2 = (int)(g.x * g.y);
+        ++nk;
     } else {
         k_step2<T><<<z.grid, kRedThreads, 0, z.st>>>(st, z.scal.as<double>(), v, w, slot_basis, n, part,
                                                     (pass2 || z.reorth) ? 0 : 1);
+        ++nk;
     }
-    ++nk;
     if (z.reorth && !pass2) {
         T *basis = z.basis.as<T>();
         const int gj = std::max(1, std::min<int>(z.grid, (int)((n + kRedThreads - 1) / kRedThreads)));

@@ -64,6 +64,48 @@ def test_graph_replay_and_second_pass_are_bit_identical(G):
         assert abs(a["E0"] - b["E0"]) <= 1e-13 * abs(a["E0"])
 
 
+def test_second_run_finishes_each_step_in_the_spin_up_pass(G):
+    """Without a stored basis the Ritz vector comes from a second run of the
+    recurrence with the stored scalars.  When the per-spin dimensions are
+    whole 16-byte packs, the spin-up pass of that run finishes each step
+    itself (u_{k+1} row-major and transposed for the next H·v): one launch
+    fewer per step than the separate update, which the windowed passes keep.
+    Both rebuild the first run's vectors, so E0 and the residual agree with
+    the stored-basis solve, and eager and graph launches agree bit for bit."""
+    # 4x3 torus with diagonal hopping, N_up = 5, N_dn = 6: 792 x 924 states,
+    # both multiples of 4; the 924 columns end in a ragged column chunk, and
+    # 16 rows per CTA in a ragged row block (792 = 49.5 x 16)
+    L, h, U, Nu, Nd = 12, S.square(4, 3, 1.0, -0.3), S.uniform_U(12, 8.0), 5, 6
+    D = oracle.sector_dim(L, Nu, Nd)
+    assert D == 792 * 924
+    H = G.gbr_ham_create(L, h, U, Nu, Nd)
+    G.gbr_ham_set_path(H, G.GBR_HV_FACTORED)
+    for prec, fp in ((G.GBR_PREC_FP64, 64), (G.GBR_PREC_MIXED, 32)):
+        for rows_lz in (4, 16):
+            G.gbr_ham_set_shape(H, fp, 0, 8, 8, rows_lz)
+            a = G.gbr_lanczos(H, v0(D), 60, prec=prec, refine=True, store_basis=1)
+            n0 = G.gbr_launch_count()
+            b = G.gbr_lanczos(H, v0(D), 60, prec=prec, refine=True, store_basis=0, use_graph=False)
+            nb = G.gbr_launch_count() - n0
+            c = G.gbr_lanczos(H, v0(D), 60, prec=prec, refine=True, store_basis=0, use_graph=True)
+            assert a["stored_basis"] and not b["stored_basis"] and b["ritz_terms"] == 60
+            assert np.array_equal(a["alpha"], b["alpha"]) and np.array_equal(a["beta"], b["beta"])
+            assert np.array_equal(b["alpha"], c["alpha"]) and np.array_equal(b["beta"], c["beta"])
+            assert b["E0"] == c["E0"] and b["residual"] == c["residual"], (prec, rows_lz)
+            assert abs(a["E0"] - b["E0"]) <= 1e-13 * abs(a["E0"]), (prec, rows_lz)
+            # the two Ritz vectors differ only by the rounding of their sums
+            assert abs(a["residual"] - b["residual"]) <= 1e-6 * a["residual"], (prec, rows_lz)
+        G.gbr_ham_set_shape(H, fp, 1, 32, 32, 32)
+        assert G.gbr_ham_get_shape(H, fp)["window"] == 1
+        n0 = G.gbr_launch_count()
+        w = G.gbr_lanczos(H, v0(D), 60, prec=prec, refine=True, store_basis=0, use_graph=False)
+        nw = G.gbr_launch_count() - n0
+        assert nw - nb == w["ritz_terms"] - 1, (prec, nw, nb)
+        assert abs(w["E0"] - a["E0"]) <= 1e-12 * abs(a["E0"])
+        G.gbr_ham_set_shape(H, fp, 0)
+    assert G.gbr_device_status() == 0
+
+
 def test_free_fermion_closed_form_ring8(G):
     L, h, U, Nu, Nd = ring8(U=0.0)
     H = G.gbr_ham_create(L, h, U, Nu, Nd)

@@ -43,7 +43,10 @@ def test_set_lanczos_every_Sz_at_fixed_N(G, prec):
     Sh = G.gbr_setham_create(L, h, Uv, st, 8)
     r = _solve(G, G.gbr_setham_lanczos, Sh, st.size, 160, prec)
     _check(r["E0"], ref, prec)
-    assert r["residual"] <= 1e-6
+    # the residual of a Ritz vector built from FP32 Lanczos vectors cannot go
+    # below about |H| u_32 (|H| = 20.6 here, u_32 = 2^-24: 1.2e-6); FP64 vectors
+    # reach the converged Ritz pair's own residual
+    assert r["residual"] <= (1e-6 if prec == 0 else 1e-5)
 
 
 def test_set_lanczos_open_subset_is_the_projected_operator(G):
