@@ -319,6 +319,43 @@ __global__ void __launch_bounds__(256) k_transpose16(const T *__restrict__ in, T
     }
 }
 
+// Asynchronous copies of B = 4, 8, 16 (or twice 16) bytes from global to shared memory
+// (cp.async: no registers are held while they are in flight).  The issuing
+// thread waits for its own copies with cp_async_wait_all; other threads see
+// them after a barrier that follows that wait.
+template <int B>
+__device__ __forceinline__ void cp_async(void *dst, const void *src) {
+    const uint32_t d = (uint32_t)__cvta_generic_to_shared(dst);
+    if constexpr (B == 32) {
+        cp_async<16>(dst, src);
+        cp_async<16>((char *)dst + 16, (const char *)src + 16);
+    } else if constexpr (B == 16)
+        asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(d), "l"(src) : "memory");
+    else
+        asm volatile("cp.async.ca.shared.global [%0], [%1], %2;" ::"r"(d), "l"(src), "n"(B) : "memory");
+}
+// the same with an L2 cache policy (data read once: evict_first)
+template <int B>
+__device__ __forceinline__ void cp_async_hint(void *dst, const void *src, uint64_t pol) {
+    const uint32_t d = (uint32_t)__cvta_generic_to_shared(dst);
+    if constexpr (B == 32) {
+        cp_async_hint<16>(dst, src, pol);
+        cp_async_hint<16>((char *)dst + 16, (const char *)src + 16, pol);
+    } else if constexpr (B == 16)
+        asm volatile("cp.async.cg.shared.global.L2::cache_hint [%0], [%1], 16, 16, %2;" ::"r"(d), "l"(src), "l"(pol)
+                     : "memory");
+    else
+        asm volatile("cp.async.ca.shared.global.L2::cache_hint [%0], [%1], %2, %2, %3;" ::"r"(d), "l"(src), "n"(B),
+                     "l"(pol)
+                     : "memory");
+}
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;" ::: "memory"); }
+__device__ __forceinline__ uint64_t l2_evict_first() {
+    uint64_t p;
+    asm volatile("createpolicy.fractional.L2::evict_first.b64 %0, 1.0;" : "=l"(p));
+    return p;
+}
+
 struct CombineArgs {
     const uint32_t *st_up, *st_dn;   // per-spin patterns (row and column states)
     const void *dup, *ddn, *uval;     // per-spin diagonals, U class values (precision T)
@@ -351,6 +388,7 @@ __global__ void __launch_bounds__(NT, ((MODE >= 1 && sizeof(T) == 4) ? 1280 / NT
     constexpr bool COMBINE = MODE >= 1;
     constexpr bool LZ = MODE >= 2;
     constexpr bool UPD = MODE == 3;
+    constexpr int VB = VEC * (int)sizeof(T);   // bytes of one thread's slice of a row
     // row stride of the staged Z tile: 16 bytes of padding put the TR rows of
     // one column in different banks when the tile is written column by column
     constexpr int ZS = NT * VEC + 16 / (int)sizeof(T);
@@ -360,42 +398,37 @@ __global__ void __launch_bounds__(NT, ((MODE >= 1 && sizeof(T) == 4) ? 1280 / NT
     extern __shared__ __align__(128) unsigned char smr[];
     uint32_t *st = reinterpret_cast<uint32_t *>(smr);
     T *sc = reinterpret_cast<T *>(smr + (size_t)TR * hs * 4);
-    __shared__ int scnt[64];
-    // U class values (combine), in shared memory to keep registers for occupancy
+    // combine epilogue: the block Z[r0..r0+TR, chunk] = (Z^T)[chunk, r0..r0+TR]
+    // (TR rows of ZS), then one slot each for the current row's own x slice
+    // (diagonal term) and its u_{k-1} slice (Lanczos update)
+    T *zs = reinterpret_cast<T *>(smr + (size_t)TR * hs * (4 + sizeof(T)));
+    T *xs = zs + (size_t)TR * ZS;
+    T *vs = xs + NT * VEC;
+    __shared__ int scnt[TR];
+    // per-row spin-up pattern and diagonal, U class values (combine), in
+    // shared memory to keep registers for occupancy
+    __shared__ uint32_t sau[TR];
+    __shared__ T sdu[TR];
     __shared__ T suv[kMaxUClasses];
     const int64_t rb = blockIdx.x % nrb, cc = blockIdx.x / nrb;
     const int64_t r0 = rb * TR;
-    for (int i = threadIdx.x; i < TR; i += blockDim.x) scnt[i] = (r0 + i < Drows) ? (int)cnt[r0 + i] : 0;
-    if (COMBINE && threadIdx.x < kMaxUClasses)
-        suv[threadIdx.x] = threadIdx.x < ca.hk.nucls ? ((const T *)ca.uval)[threadIdx.x] : T(0);
-    __syncthreads();
-    for (int e = threadIdx.x; e < TR * hmax; e += blockDim.x) {
-        const int i = e % TR, k = e / TR;
-        if (k < scnt[i]) {
-            const int64_t g = (int64_t)k * Drows + r0 + i;
-            const uint32_t w = tgt[g];
-            const T c = uniform ? hu : bcoef[bond[g]];
-            st[i * hs + k] = w & 0x7FFFFFFFu;
-            sc[i * hs + k] = (w >> 31) ? -c : c;
-        }
-    }
-    __syncthreads();
-    const int64_t c0 = cc * (int64_t)(NT * VEC) + (int64_t)threadIdx.x * VEC;
-    // combine epilogue: the block Z[r0..r0+TR, chunk] = (Z^T)[chunk, r0..r0+TR]
-    // is read from Z^T once, column by column (TR consecutive values each),
-    // into shared memory as [row][column]
-    T *zs = reinterpret_cast<T *>(smr + (size_t)TR * hs * (4 + sizeof(T)));
+    const int nrow = (int)((Drows - r0) < (int64_t)TR ? (Drows - r0) : (int64_t)TR);
+    const int64_t cbase = cc * (int64_t)(NT * VEC);
+    // The prologue issues every load that does not wait on another before the
+    // first barrier: the Z tile goes to shared memory by asynchronous copies
+    // (4 or 8 bytes each, waited for before the second barrier), so it is in
+    // flight while the hop lists are staged.
     if (COMBINE && !ca.zrow) {
         const T *zt = (const T *)ca.zt;
-        const int64_t cbase = cc * (int64_t)(NT * VEC);
-        const int nrow = (int)((Drows - r0) < (int64_t)TR ? (Drows - r0) : (int64_t)TR);
+        const uint64_t pol = l2_evict_first();
         for (int e = threadIdx.x; e < NT * VEC * TR; e += blockDim.x) {
             const int col = e / TR, i = e % TR;
             const int64_t c = cbase + col;
-            zs[i * ZS + col] = (c < Dcols && i < nrow) ? __ldg(zt + c * Drows + r0 + i) : T(0);
+            if (c < Dcols && i < nrow) cp_async_hint<(int)sizeof(T)>(zs + i * ZS + col, zt + c * Drows + r0 + i, pol);
+            else zs[i * ZS + col] = T(0);
         }
-        __syncthreads();
     }
+    const int64_t c0 = cbase + (int64_t)threadIdx.x * VEC;
     const bool active = c0 < Dcols;
     DotAcc<T> dacc;
     int klz = 0;
@@ -417,9 +450,39 @@ __global__ void __launch_bounds__(NT, ((MODE >= 1 && sizeof(T) == 4) ? 1280 / NT
             dd[v] = ddn[c0 + v];
         }
     }
+    for (int i = threadIdx.x; i < TR; i += blockDim.x) {
+        scnt[i] = i < nrow ? (int)cnt[r0 + i] : 0;
+        if (COMBINE && i < nrow) {
+            sau[i] = ca.st_up[r0 + i];
+            sdu[i] = ((const T *)ca.dup)[r0 + i];
+        }
+    }
+    if (COMBINE && threadIdx.x < kMaxUClasses)
+        suv[threadIdx.x] = threadIdx.x < ca.hk.nucls ? ((const T *)ca.uval)[threadIdx.x] : T(0);
+    __syncthreads();
+    for (int e = threadIdx.x; e < TR * hmax; e += blockDim.x) {
+        const int i = e % TR, k = e / TR;
+        if (k < scnt[i]) {
+            const int64_t g = (int64_t)k * Drows + r0 + i;
+            const uint32_t w = tgt[g];
+            const T c = uniform ? hu : bcoef[bond[g]];
+            st[i * hs + k] = w & 0x7FFFFFFFu;
+            sc[i * hs + k] = (w >> 31) ? -c : c;
+        }
+    }
+    if (COMBINE && !ca.zrow) cp_async_wait_all();
+    __syncthreads();
+    const uint64_t pol_first = LZ ? l2_evict_first() : 0;
     for (int i = 0; i < TR && active; ++i) {
         const int64_t r = r0 + i;
         if (r >= Drows) break;
+        // combine: the row's own x slice and u_{k-1} slice travel to this
+        // thread's slots while the row gathers (each thread reads back only
+        // what it copied, after waiting for its own copies)
+        if (COMBINE) {
+            cp_async<VB>(xs + threadIdx.x * VEC, x + r * Dcols + c0);
+            if (LZ && klz > 0) cp_async_hint<VB>(vs + threadIdx.x * VEC, (const T *)ca.lz.vprev + r * Dcols + c0, pol_first);
+        }
         const int n = scnt[i];
         const uint32_t *ti = st + i * hs;
         const T *ci = sc + i * hs;
@@ -446,10 +509,23 @@ __global__ void __launch_bounds__(NT, ((MODE >= 1 && sizeof(T) == 4) ? 1280 / NT
                 a4.x += c4.z * v2.x; a4.y += c4.z * v2.y; a4.z += c4.z * v2.z; a4.w += c4.z * v2.w;
                 a4.x += c4.w * v3.x; a4.y += c4.w * v3.y; a4.z += c4.w * v3.z; a4.w += c4.w * v3.w;
             }
-            for (; k < n; ++k) {
-                const float4 v = __ldcg(reinterpret_cast<const float4 *>(x + (int64_t)ti[k] * Dcols + c0));
-                const float c = cf[k];
-                a4.x += c * v.x; a4.y += c * v.y; a4.z += c * v.z; a4.w += c * v.w;
+            if (k < n) {
+                // the last one to three hops as one batch of independent loads
+                const bool h1 = k + 1 < n, h2 = k + 2 < n;
+                const float4 zero = make_float4(0.f, 0.f, 0.f, 0.f);
+                const float4 v0 = __ldcg(reinterpret_cast<const float4 *>(x + (int64_t)ti[k] * Dcols + c0));
+                const float4 v1 = h1 ? __ldcg(reinterpret_cast<const float4 *>(x + (int64_t)ti[k + 1] * Dcols + c0)) : zero;
+                const float4 v2 = h2 ? __ldcg(reinterpret_cast<const float4 *>(x + (int64_t)ti[k + 2] * Dcols + c0)) : zero;
+                float c = cf[k];
+                a4.x += c * v0.x; a4.y += c * v0.y; a4.z += c * v0.z; a4.w += c * v0.w;
+                if (h1) {
+                    c = cf[k + 1];
+                    a4.x += c * v1.x; a4.y += c * v1.y; a4.z += c * v1.z; a4.w += c * v1.w;
+                }
+                if (h2) {
+                    c = cf[k + 2];
+                    a4.x += c * v2.x; a4.y += c * v2.y; a4.z += c * v2.z; a4.w += c * v2.w;
+                }
             }
             acc[0] = a4.x; acc[1] = a4.y; acc[2] = a4.z; acc[3 % VEC] = a4.w;
         } else if (VEC == 2) {
@@ -467,17 +543,16 @@ __global__ void __launch_bounds__(NT, ((MODE >= 1 && sizeof(T) == 4) ? 1280 / NT
             acc[0] = a0;
         }
         if (COMBINE) {
-            const uint32_t au = ca.st_up[r];
-            const T du = ((const T *)ca.dup)[r];
+            const uint32_t au = sau[i];
+            const T du = sdu[i];
+            cp_async_wait_all();
             T xo[VEC];
             if (VEC == 4 && sizeof(T) == 4) {
-                const float4 o = __ldg(reinterpret_cast<const float4 *>(x + r * Dcols + c0));
+                const float4 o = *reinterpret_cast<const float4 *>(xs + threadIdx.x * VEC);
                 xo[0] = o.x; xo[1 % VEC] = o.y; xo[2 % VEC] = o.z; xo[3 % VEC] = o.w;
-            } else if (VEC == 2) {
-                const typename Vec<T>::v2 o = __ldg(reinterpret_cast<const typename Vec<T>::v2 *>(x + r * Dcols + c0));
-                xo[0] = o.x; xo[1 % VEC] = o.y;
             } else {
-                xo[0] = __ldg(x + r * Dcols + c0);
+#pragma unroll
+                for (int v = 0; v < VEC; ++v) xo[v] = xs[threadIdx.x * VEC + v];
             }
             T zv[VEC];
             if (ca.zrow) {
@@ -505,17 +580,14 @@ __global__ void __launch_bounds__(NT, ((MODE >= 1 && sizeof(T) == 4) ? 1280 / NT
                 acc[v] += dg * xo[v] + zv[v];
             }
             if (LZ) {
-                const T *vpv = (const T *)ca.lz.vprev + r * Dcols + c0;
                 if (klz > 0) {
                     T vp[VEC];
                     if (VEC == 4 && sizeof(T) == 4) {
-                        const float4 o = __ldcs(reinterpret_cast<const float4 *>(vpv));
+                        const float4 o = *reinterpret_cast<const float4 *>(vs + threadIdx.x * VEC);
                         vp[0] = o.x; vp[1 % VEC] = o.y; vp[2 % VEC] = o.z; vp[3 % VEC] = o.w;
-                    } else if (VEC == 2) {
-                        const typename Vec<T>::v2 o = __ldcs(reinterpret_cast<const typename Vec<T>::v2 *>(vpv));
-                        vp[0] = o.x; vp[1 % VEC] = o.y;
                     } else {
-                        vp[0] = __ldcs(vpv);
+#pragma unroll
+                        for (int v = 0; v < VEC; ++v) vp[v] = vs[threadIdx.x * VEC + v];
                     }
 #pragma unroll
                     for (int v = 0; v < VEC; ++v) acc[v] = lz_rec(slz, acc[v], blz, vp[v]);
@@ -551,8 +623,6 @@ __global__ void __launch_bounds__(NT, ((MODE >= 1 && sizeof(T) == 4) ? 1280 / NT
         // column of the transpose (as the Z tile was read)
         __syncthreads();
         T *xt = (T *)ca.lz.xt_next;
-        const int64_t cbase = cc * (int64_t)(NT * VEC);
-        const int nrow = (int)((Drows - r0) < (int64_t)TR ? (Drows - r0) : (int64_t)TR);
         for (int e = threadIdx.x; e < NT * VEC * TR; e += blockDim.x) {
             const int col = e / TR, i = e % TR;
             const int64_t c = cbase + col;
@@ -1006,7 +1076,10 @@ static int launch_gather(const gbr_ham *H, const SpinSector &lists, int64_t Drow
     const int64_t ncc = (Dcols + NT * vec - 1) / (NT * vec);
     const int hmax = std::max(1, lists.hmax);
     const int hs = (hmax + 3) & ~3;   // the kernel's padded hop-list stride
-    const size_t smem = (size_t)TR * hs * (4 + sizeof(T)) + (COMBINE ? (size_t)TR * (NT * vec * sizeof(T) + 16) : 0);
+    // hop lists, then (combine) the Z tile and the row slots for x and (Lanczos) u_{k-1}
+    const size_t smem = (size_t)TR * hs * (4 + sizeof(T)) +
+                        (COMBINE ? (size_t)TR * (NT * vec * sizeof(T) + 16) + (MODE >= 2 ? 2 : 1) * (size_t)NT * vec * sizeof(T)
+                                 : 0);
     const int64_t blocks = nrb * ncc;
     if (blocks > 0x7FFFFFFF) return set_error(GBR_EINVAL, "sector too large for the gather grid");
 #define GBR_G(V, R, N)                                                                                       \
