@@ -356,6 +356,15 @@ __device__ __forceinline__ uint64_t l2_evict_first() {
     return p;
 }
 
+// Row stride padding (elements) of the staged Z tile.  The tile is written
+// column by column, TR rows of one column from consecutive threads, so a warp
+// covers 32 / TR columns; a padding of 32 / TR FP32 elements puts all 32 in
+// different banks for TR = 4 and 8.  The rows stay 16-byte aligned for the
+// vector reads, so TR = 16 keeps 4 (two-way conflicts); FP64 keeps 16 bytes.
+__host__ __device__ constexpr int ztile_pad(int elem_bytes, int TR) {
+    return (elem_bytes == 4 && TR == 4) ? 8 : 16 / elem_bytes;
+}
+
 struct CombineArgs {
     const uint32_t *st_up, *st_dn;   // per-spin patterns (row and column states)
     const void *dup, *ddn, *uval;     // per-spin diagonals, U class values (precision T)
@@ -373,14 +382,14 @@ struct CombineArgs {
 // known, no partials), then u_{k+1} = w - (alpha_k / g_k) x to y and, through
 // the Z tile (each thread overwrites the values it read), transposed to
 // ca.lz.xt_next once the CTA's rows are done.
-// The FP32 combine passes are held to 10 CTAs per SM (48 registers): left
-// free the compiler takes up to 60 registers and the occupancy drops; at 12
-// or 16 CTAs it spills.  Measured on the 4x4 sector: 1.16 ms (10) against
-// 1.21 ms (free) and 1.25 ms (16).
+// The FP32 passes are held to 1280 threads per SM (48 registers): left free
+// the compiler takes up to 56-60 registers and the occupancy drops; at 12 or
+// 16 CTAs of 128 threads the combine pass spills.  Measured on the 4x4
+// sector: combine 1.16 ms (10 CTAs) against 1.21 ms (free) and 1.25 ms (16).
 // NT threads per CTA (128, or 64 for column chunks half as wide: the
 // gathered rows of a chunk then take half the L2).
 template <typename T, int VEC, int MODE, int TR, int NT>
-__global__ void __launch_bounds__(NT, ((MODE >= 1 && sizeof(T) == 4) ? 1280 / NT : 1)) k_gather(const int64_t Drows, const int64_t Dcols, const int hmax,
+__global__ void __launch_bounds__(NT, (sizeof(T) == 4 ? 1280 / NT : 1)) k_gather(const int64_t Drows, const int64_t Dcols, const int hmax,
                                                 const int64_t nrb, const uint16_t *__restrict__ cnt,
                                                 const uint32_t *__restrict__ tgt, const uint16_t *__restrict__ bond,
                                                 const T *__restrict__ bcoef, const int uniform, const T hu,
@@ -389,9 +398,7 @@ __global__ void __launch_bounds__(NT, ((MODE >= 1 && sizeof(T) == 4) ? 1280 / NT
     constexpr bool LZ = MODE >= 2;
     constexpr bool UPD = MODE == 3;
     constexpr int VB = VEC * (int)sizeof(T);   // bytes of one thread's slice of a row
-    // row stride of the staged Z tile: 16 bytes of padding put the TR rows of
-    // one column in different banks when the tile is written column by column
-    constexpr int ZS = NT * VEC + 16 / (int)sizeof(T);
+    constexpr int ZS = NT * VEC + ztile_pad((int)sizeof(T), TR);
     // hop-list row stride, a multiple of 4 so that four targets (and four
     // coefficients) are read with one 16-byte broadcast load
     const int hs = (hmax + 3) & ~3;
@@ -1078,7 +1085,7 @@ static int launch_gather(const gbr_ham *H, const SpinSector &lists, int64_t Drow
     const int hs = (hmax + 3) & ~3;   // the kernel's padded hop-list stride
     // hop lists, then (combine) the Z tile and the row slots for x and (Lanczos) u_{k-1}
     const size_t smem = (size_t)TR * hs * (4 + sizeof(T)) +
-                        (COMBINE ? (size_t)TR * (NT * vec * sizeof(T) + 16) + (MODE >= 2 ? 2 : 1) * (size_t)NT * vec * sizeof(T)
+                        (COMBINE ? (size_t)TR * (NT * vec + ztile_pad((int)sizeof(T), TR)) * sizeof(T) + (MODE >= 2 ? 2 : 1) * (size_t)NT * vec * sizeof(T)
                                  : 0);
     const int64_t blocks = nrb * ncc;
     if (blocks > 0x7FFFFFFF) return set_error(GBR_EINVAL, "sector too large for the gather grid");
