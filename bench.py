@@ -870,12 +870,14 @@ def profile_hv(n: int, sector: str = "sq4x4", shape: str = "", fp: int = 32):
     torch.cuda.synchronize()
 
 
-def profile_lanczos(n: int, sector: str = "ring18", shape: str = ""):
+def profile_lanczos(n: int, sector: str = "ring18", shape: str = "", second_run: bool = False):
     """A short mixed-precision Lanczos (n steps) on one sector, with the same
     handle set-up as the timed steps (the autotuner's shape, or the given
     shape "window,rows_dn,rows_up,rows_lz,..." without tuning): the target of
     the ncu captures of the kernels as the benchmark launches them (fused
-    Lanczos epilogue)."""
+    Lanczos epilogue).  second_run: the Ritz vector too, from the second run
+    of the recurrence (no stored basis), whose spin-up pass finishes each
+    step."""
     import torch
     import __graft_entry__
     __graft_entry__.build()
@@ -891,7 +893,7 @@ def profile_lanczos(n: int, sector: str = "ring18", shape: str = ""):
     else:
         G.gbr_ham_tune(H, 32)
     s = SG.uniform(S.SEED_START, D)
-    G.gbr_lanczos(H, s, n, prec=G.GBR_PREC_MIXED, refine=False, store_basis=0, profile=True)
+    G.gbr_lanczos(H, s, n, prec=G.GBR_PREC_MIXED, refine=second_run, store_basis=0, profile=True)
     torch.cuda.synchronize()
 
 
@@ -947,6 +949,9 @@ def main():
                     help="sector of --profile-hv and --profile-lanczos")
     ap.add_argument("--profile-shape", default="", help="launch shape window,rows_dn,rows_up,rows_lz")
     ap.add_argument("--profile-fp", type=int, default=32, choices=[32, 64])
+    ap.add_argument("--profile-second-run", action="store_true",
+                    help="with --profile-lanczos: also form the Ritz vector by the second run of the recurrence "
+                         "(the spin-up pass that finishes each step and writes the next X^T)")
     args = ap.parse_args()
     if args.profile_hv:
         profile_hv(args.profile_hv, args.profile_sector, args.profile_shape, args.profile_fp)
@@ -955,7 +960,7 @@ def main():
         profile_rank(args.profile_rank)
         return
     if args.profile_lanczos:
-        profile_lanczos(args.profile_lanczos, args.profile_sector, args.profile_shape)
+        profile_lanczos(args.profile_lanczos, args.profile_sector, args.profile_shape, args.profile_second_run)
         return
     if args.eig_timings:
         import torch
