@@ -442,7 +442,14 @@ typedef struct {
     int prec;         /* GBR_PREC_FP64: FP64 vectors and H·v;
                          GBR_PREC_MIXED: FP32 vectors and H·v, FP64 scalars */
     int refine;       /* 1 = form the Ritz vector and return the FP64 Rayleigh
-                         quotient <x,Hx>/<x,x> and residual |Hx - E x| / |x| */
+                         quotient <x,Hx>/<x,x> and residual |Hx - E x| / |x|.
+                         The vector is that of the shortest prefix T_k (k a
+                         multiple of 8) whose lowest pair has residual estimate
+                         beta_{k+1} |s_k| <= u max_j(|alpha_j|, beta_j), u the unit
+                         roundoff of the vectors (2^-24 mixed, 2^-53 FP64), else of
+                         the whole T: a run that goes on past that point without
+                         re-orthogonalisation grows copies of the converged state,
+                         which spoil the Ritz vector of the longer T */
     int store_basis;  /* 1 = keep all vectors (needed by reorth; makes the Ritz
                          vector one pass), 0 = recompute the basis in a second
                          run of the recurrence, -1 = decide from free memory */
@@ -474,7 +481,8 @@ typedef struct {
                                 is counted in the last slot) */
     int stage_launches[4];   /* profile: launches of each stage */
     int converged;           /* 1 if the tol test stopped the recurrence */
-    int ritz_terms;          /* Lanczos vectors summed into the Ritz vector (refine) */
+    int ritz_terms;          /* Lanczos vectors summed into the Ritz vector (refine):
+                                the prefix length, less any ritz_tail terms */
 } gbr_lanczos_result;
 
 /* Runs Lanczos from the start vector d_v0 (dim doubles on the device, not

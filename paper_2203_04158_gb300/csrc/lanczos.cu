@@ -345,6 +345,34 @@ __global__ void __launch_bounds__(32) k_conv_check(LzState *st, const double *al
     }
 }
 
+// The prefix of the recurrence whose Ritz vector the refinement forms: the
+// shortest T_k (k = 8, 16, ... below kdone) whose lowest Ritz pair has the
+// residual estimate beta_{k+1} |s_k| <= u * max_j(|alpha_j|, beta_j), u the
+// unit roundoff of the vectors' precision; kdone if there is none.  A run
+// without re-orthogonalisation that goes on past that point grows copies of
+// the converged state in T, and the Ritz vector of the longer T loses
+// accuracy, while the stored vectors cannot make it more accurate than at
+// that prefix.  One warp; *kout receives the prefix length.
+__global__ void __launch_bounds__(32) k_ritz_prefix(const LzState *st, const double *alpha, const double *beta,
+                                                    int kdone, double u, double *work, int *kout) {
+    __shared__ double lam_prev, gap;
+    __shared__ int found;
+    if (threadIdx.x == 0) {
+        lam_prev = 0.0;
+        gap = 0.0;
+        found = kdone;
+    }
+    __syncthreads();
+    const double thr = u * st->scale;
+    for (int k = 8; k < kdone; k += 8) {
+        const double lam = tridiag_lowest_warm(alpha, beta, k, &lam_prev, &gap);
+        if (threadIdx.x == 0 && beta[k] * tridiag_last_component(alpha, beta, k, lam, work) <= thr) found = k;
+        __syncthreads();
+        if (found != kdone) break;
+    }
+    if (threadIdx.x == 0) *kout = found;
+}
+
 // per-step Ritz value into ritz[k]
 __global__ void k_copy_ritz(const LzState *st, const double *val, double *ritz) {
     if (threadIdx.x == 0) ritz[st->k] = val[0];
@@ -795,10 +823,10 @@ static int lz_run(Lz &z, const double *d_v0, gbr_lanczos_result *res, const gbr_
     res->breakdown = hs.breakdown;
     res->converged = hs.converged;
     res->stored_basis = z.store;
-    // lowest Ritz value and (if refining) its eigenvector
+    // lowest Ritz value of T_kdone
     double *tri = z.tri.as<double>();
     k_tridiag<<<1, kRedThreads, 0, s>>>(z.state.as<LzState>(), z.alpha.as<double>(), z.beta.as<double>(), kdone, tri,
-                                       o->refine ? z.svec.as<double>() : nullptr, z.work.as<double>());
+                                       nullptr, z.work.as<double>());
     GBR_LAUNCH_CHECK();
     count_launches(1);
     double Er = 0.0;
@@ -812,12 +840,25 @@ static int lz_run(Lz &z, const double *d_v0, gbr_lanczos_result *res, const gbr_
         if ((rc = grow(x, (size_t)n * 8))) return rc;
         if ((rc = grow(hx, (size_t)n * 8))) return rc;
         double *sv = z.svec.as<double>();
+        // the Ritz vector of the converged prefix T_kr, then its eigenvector s
+        int *kbuf = reinterpret_cast<int *>(tri + 8);
+        const double unit = sizeof(T) == 4 ? 5.9604644775390625e-8 : 1.1102230246251565e-16;
+        k_ritz_prefix<<<1, 32, 0, s>>>(z.state.as<LzState>(), z.alpha.as<double>(), z.beta.as<double>(), kdone, unit,
+                                       z.work.as<double>(), kbuf);
+        int kr = kdone;
+        GBR_CUDA_TRY(cudaMemcpyAsync(&kr, kbuf, sizeof(int), cudaMemcpyDeviceToHost, s));
+        GBR_CUDA_TRY(cudaStreamSynchronize(s));
+        if (kr < 1 || kr > kdone) kr = kdone;
+        k_tridiag<<<1, kRedThreads, 0, s>>>(z.state.as<LzState>(), z.alpha.as<double>(), z.beta.as<double>(), kr,
+                                           tri + 4, sv, z.work.as<double>());
+        count_launches(2);
+        GBR_LAUNCH_CHECK();
         // terms of the Ritz sum: drop the trailing coefficients whose norm is
         // at most ritz_tail (s is normalised by the tridiagonal solver)
-        int nterm = kdone;
-        if (o->ritz_tail > 0.0 && kdone > 1) {
-            std::vector<double> hs((size_t)kdone);
-            GBR_CUDA_TRY(cudaMemcpyAsync(hs.data(), sv, sizeof(double) * (size_t)kdone, cudaMemcpyDeviceToHost, s));
+        int nterm = kr;
+        if (o->ritz_tail > 0.0 && kr > 1) {
+            std::vector<double> hs((size_t)kr);
+            GBR_CUDA_TRY(cudaMemcpyAsync(hs.data(), sv, sizeof(double) * (size_t)kr, cudaMemcpyDeviceToHost, s));
             GBR_CUDA_TRY(cudaStreamSynchronize(s));
             double s2 = 0.0;
             for (double v : hs) s2 += v * v;

@@ -88,7 +88,7 @@ def test_second_run_finishes_each_step_in_the_spin_up_pass(G):
             b = G.gbr_lanczos(H, v0(D), 60, prec=prec, refine=True, store_basis=0, use_graph=False)
             nb = G.gbr_launch_count() - n0
             c = G.gbr_lanczos(H, v0(D), 60, prec=prec, refine=True, store_basis=0, use_graph=True)
-            assert a["stored_basis"] and not b["stored_basis"] and b["ritz_terms"] == 60
+            assert a["stored_basis"] and not b["stored_basis"] and b["ritz_terms"] <= 60
             assert np.array_equal(a["alpha"], b["alpha"]) and np.array_equal(a["beta"], b["beta"])
             assert np.array_equal(b["alpha"], c["alpha"]) and np.array_equal(b["beta"], c["beta"])
             assert b["E0"] == c["E0"] and b["residual"] == c["residual"], (prec, rows_lz)
@@ -100,6 +100,7 @@ def test_second_run_finishes_each_step_in_the_spin_up_pass(G):
         n0 = G.gbr_launch_count()
         w = G.gbr_lanczos(H, v0(D), 60, prec=prec, refine=True, store_basis=0, use_graph=False)
         nw = G.gbr_launch_count() - n0
+        assert w["ritz_terms"] == b["ritz_terms"]
         assert nw - nb == w["ritz_terms"] - 1, (prec, nw, nb)
         assert abs(w["E0"] - a["E0"]) <= 1e-12 * abs(a["E0"])
         G.gbr_ham_set_shape(H, fp, 0)
@@ -190,6 +191,30 @@ def test_factored_path_fused_update_matches_oracle_and_is_reproducible(G):
         assert abs(a["E0"] - b["E0"]) <= 1e-13 * abs(a["E0"])
 
 
+def test_ritz_vector_of_the_converged_prefix(G):
+    """A run far past convergence (300 steps on 4,900 states, no
+    re-orthogonalisation) forms its Ritz vector from the shortest prefix whose
+    lowest pair has converged to the vectors' roundoff, before the recurrence
+    grows copies of that state: the same energy and residual, bit for bit, as
+    a run stopped at that prefix, and the refined energy close to dense
+    diagonalisation."""
+    L, h, U, Nu, Nd = ring8()
+    H = G.gbr_ham_create(L, h, U, Nu, Nd)
+    E_dense = oracle.dense_E0(L, h, U, Nu, Nd)
+    for prec, bar in ((G.GBR_PREC_MIXED, 1e-11), (G.GBR_PREC_FP64, 1e-13)):
+        run = G.gbr_lanczos(H, v0(4900), 300, prec=prec, refine=True, store_basis=1)
+        assert run["iters"] == 300
+        assert abs(run["E0"] - E_dense) <= bar * abs(E_dense), (prec, run["E0"], E_dense)
+        k = run["ritz_terms"]
+        assert 8 <= k <= 300
+        if prec == G.GBR_PREC_MIXED:
+            assert k % 8 == 0 and k < 300
+        if k < 300:
+            short = G.gbr_lanczos(H, v0(4900), k, prec=prec, refine=True, store_basis=1)
+            assert short["ritz_terms"] == k
+            assert short["E0"] == run["E0"] and short["residual"] == run["residual"], prec
+
+
 def test_ritz_tail_cut_keeps_the_bar_and_matches_between_basis_modes(G):
     """Dropping the trailing Ritz coefficients (norm <= ritz_tail) moves the
     refined energy by about ritz_tail^2 times the spectral spread: at 1e-6
@@ -203,8 +228,8 @@ def test_ritz_tail_cut_keeps_the_bar_and_matches_between_basis_modes(G):
     a = G.gbr_lanczos(H, v0(4900), 120, prec=G.GBR_PREC_MIXED, refine=True, store_basis=1, ritz_tail=1e-6)
     b = G.gbr_lanczos(H, v0(4900), 120, prec=G.GBR_PREC_MIXED, refine=True, store_basis=0, ritz_tail=1e-6)
     full = G.gbr_lanczos(H, v0(4900), 120, prec=G.GBR_PREC_MIXED, refine=True, store_basis=1)
-    assert full["ritz_terms"] == full["iters"]
-    assert a["ritz_terms"] == b["ritz_terms"] < a["iters"]
+    assert full["ritz_terms"] <= full["iters"]
+    assert a["ritz_terms"] == b["ritz_terms"] <= full["ritz_terms"]
     for r in (a, b):
         assert abs(r["E0"] - E_dense) <= 1e-9 * abs(E_dense)
         assert r["E0"] >= E_dense - 1e-12 * abs(E_dense)
