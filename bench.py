@@ -744,6 +744,7 @@ def run_ours(args, rank: int, world: int):
                        "elements_per_hv": elems, "lanczos_iters": ITERS, "hv_per_step": nhv,
                        "precision": "FP32 vectors and H·v, FP64-grade dots, FP64 tridiagonal and Rayleigh quotient",
                        "basis": "stored" if results[-1]["stored_basis"] else "recomputed (second run of the recurrence)",
+                       "ritz_terms": results[-1]["ritz_terms"],
                        "cuda_graphs": True, "gather_shape": shape,
                        "l2": "inputs larger than L2 (9.5 GB FP32 vectors)", "parallelism": f"replicas{world}"},
             "clocks": clk.summary(), "gpu_launches": int(launches), "roofline": roofline,

@@ -192,6 +192,17 @@ def test_trie_full_size_40bit(G, msb_first):
     sel = np.unique(S.bounded(14, np.arange(2000, dtype=np.uint64), n)).astype(np.int64)
     ps = as_u64(pats[torch.from_numpy(sel).cuda()])
     assert np.array_equal(oracle.rank_bisect_many(members, ps), as_u32(r[torch.from_numpy(sel).cuda()]).astype(np.int64))
+    # random 40-bit patterns (about 1.5 % members): the non-members walk to
+    # arbitrary entries, also through the compressed copies of the large
+    # levels, and the check flags every one of them
+    q = SG.bounded(15, 1 << 16, 1 << 40)
+    q[::7] = mdev[SG.bounded(16, q[::7].numel(), nset)]
+    rq = torch.empty(q.numel(), dtype=torch.int32, device="cuda")
+    G.gbr_trie_rank(t, q, rq, check=1)
+    exp = oracle.rank_bisect_many(members, as_u64(q))
+    got = as_u32(rq).astype(np.int64)
+    got[got == 0xFFFFFFFF] = -1
+    assert np.array_equal(got, exp) and (exp >= 0).sum() >= q.numel() // 7
 
 
 def test_comb_unaligned_views_use_the_scalar_kernel(G):
