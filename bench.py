@@ -647,10 +647,11 @@ def eig_timings(G, torch, cases=(("half", range(4, 33, 4)), ("quarter", (8, 16, 
 
 def hv_count(r) -> int:
     """H·v calls one solve ran: the recurrence, the second run of it for the
-    Ritz vector when the basis was not stored, and the FP64 refinement."""
+    Ritz vector when the basis was not stored (starting after the kept head
+    of the basis, if any), and the FP64 refinement."""
     n = r["iters"]
     if not r["stored_basis"]:
-        n += max(r["ritz_terms"] - 1, 0)
+        n += max(r["ritz_terms"] - max(r.get("basis_head", 0), 1), 0)
     return n + 1
 
 
@@ -744,7 +745,7 @@ def run_ours(args, rank: int, world: int):
                        "elements_per_hv": elems, "lanczos_iters": ITERS, "hv_per_step": nhv,
                        "precision": "FP32 vectors and H·v, FP64-grade dots, FP64 tridiagonal and Rayleigh quotient",
                        "basis": "stored" if results[-1]["stored_basis"] else "recomputed (second run of the recurrence)",
-                       "ritz_terms": results[-1]["ritz_terms"],
+                       "ritz_terms": results[-1]["ritz_terms"], "basis_head": results[-1]["basis_head"],
                        "cuda_graphs": True, "gather_shape": shape,
                        "l2": "inputs larger than L2 (9.5 GB FP32 vectors)", "parallelism": f"replicas{world}"},
             "clocks": clk.summary(), "gpu_launches": int(launches), "roofline": roofline,

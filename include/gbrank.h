@@ -452,7 +452,10 @@ typedef struct {
                          which spoil the Ritz vector of the longer T */
     int store_basis;  /* 1 = keep all vectors (needed by reorth; makes the Ritz
                          vector one pass), 0 = recompute the basis in a second
-                         run of the recurrence, -1 = decide from free memory */
+                         run of the recurrence, -1 = decide from free memory:
+                         all vectors if they fit, else the leading ones that fit
+                         (at least 8; the second run starts after them),
+                         -m (m >= 2) = keep the leading m vectors */
     int use_graph;    /* 1 = replay each iteration as a captured CUDA graph */
     int profile;      /* 1 = time every H·v stage with CUDA events (no graphs) */
     double tol;       /* > 0: every 8 steps, stop once the lowest Ritz pair of T
@@ -483,6 +486,11 @@ typedef struct {
     int converged;           /* 1 if the tol test stopped the recurrence */
     int ritz_terms;          /* Lanczos vectors summed into the Ritz vector (refine):
                                 the prefix length, less any ritz_tail terms */
+    int basis_head;          /* without a stored basis (refine): leading vectors of
+                                the Ritz sum taken from the head of the basis that
+                                the first run kept (store_basis -1 keeps as many as
+                                fit when the whole basis does not); the second run
+                                of the recurrence starts after them.  0 = none */
 } gbr_lanczos_result;
 
 /* Runs Lanczos from the start vector d_v0 (dim doubles on the device, not

@@ -99,15 +99,16 @@ __global__ void __launch_bounds__(kRedThreads) k_step1(const LzState *st, const 
 }
 
 // w -= (alpha_k / g_k) u_k, which makes w the next unnormalised vector
-// u_{k+1}; partial <w, w>; with a basis, u_{k+1} also into its slot k + 1
+// u_{k+1}; partial <w, w>; with a basis of `slots` vectors, u_{k+1} also into
+// its slot k + 1 while k + 1 < slots
 template <typename T>
 __global__ void __launch_bounds__(kRedThreads) k_step2(const LzState *st, const double *scal, const T *__restrict__ v,
-                                                       T *__restrict__ w, T *__restrict__ basis, int64_t n, double *part,
-                                                       int want_dot) {
+                                                       T *__restrict__ w, T *__restrict__ basis, int slots, int64_t n,
+                                                       double *part, int want_dot) {
     if (st->stop) return;
     const int k = st->k;
     const T a = (T)scal[kScal * k + 2];
-    T *vb = basis ? basis + (int64_t)(k + 1) * n : nullptr;
+    T *vb = (basis && k + 1 < slots) ? basis + (int64_t)(k + 1) * n : nullptr;
     DotAcc<T> acc;
     constexpr int V = Pack<T>::N;
     // the basis slot is aligned to 16 bytes only when n * sizeof(T) is
@@ -145,14 +146,18 @@ __global__ void __launch_bounds__(kRedThreads) k_step2(const LzState *st, const 
 // next H·v reads X^T, and this saves it the transpose's read of the vector.
 // 16-byte packs; needs rows and cols that are multiples of the pack and
 // 16-byte aligned vectors (edge tiles go element by element).
+// With a basis of `slots` vectors, u_{k+1} also goes into its slot k + 1
+// while k + 1 < slots (rows * cols is a whole number of packs, so every slot
+// is 16-byte aligned).
 template <typename T>
 __global__ void __launch_bounds__(256) k_step2_t(const LzState *st, const double *scal, const T *__restrict__ v,
-                                                 T *__restrict__ w, T *__restrict__ xt, int64_t rows, int64_t cols,
-                                                 double *part, int want_dot) {
+                                                 T *__restrict__ w, T *__restrict__ xt, T *__restrict__ basis,
+                                                 int slots, int64_t rows, int64_t cols, double *part, int want_dot) {
     if (st->stop) return;
     constexpr int TILE = 64, V = Pack<T>::N, RP = TILE / V;
     __shared__ T tile[TILE][TILE + 1];
     const T a = (T)scal[kScal * st->k + 2];
+    T *vb = (basis && st->k + 1 < slots) ? basis + (int64_t)(st->k + 1) * rows * cols : nullptr;
     const int64_t c0 = (int64_t)blockIdx.x * TILE, r0 = (int64_t)blockIdx.y * TILE;
     const bool full = r0 + TILE <= rows && c0 + TILE <= cols;
     DotAcc<T> acc;
@@ -165,6 +170,7 @@ __global__ void __launch_bounds__(256) k_step2_t(const LzState *st, const double
 #pragma unroll
             for (int e = 0; e < V; ++e) wp.e[e] = lz_fnma(a, vv.e[e], wp.e[e]);
             *reinterpret_cast<Pack<T> *>(w + r * cols + c) = wp;
+            if (vb) *reinterpret_cast<Pack<T> *>(vb + r * cols + c) = wp;
 #pragma unroll
             for (int e = 0; e < V; ++e) {
                 tile[i][j * V + e] = wp.e[e];
@@ -177,6 +183,7 @@ __global__ void __launch_bounds__(256) k_step2_t(const LzState *st, const double
                 if (r < rows && c + e < cols) {
                     wi = lz_fnma(a, v[r * cols + c + e], w[r * cols + c + e]);
                     w[r * cols + c + e] = wi;
+                    if (vb) vb[r * cols + c + e] = wi;
                     if (want_dot) acc.add(wi, wi);
                 }
                 tile[i][j * V + e] = wi;
@@ -595,6 +602,7 @@ struct Lz {
     int iters, reorth, store;
     int in_basis = 0;  // the stored basis slots are the working vectors (eager launches only)
     int fuse_t = 0;    // the update writes X^T for the next H·v (k_step2_t)
+    int head = 0;      // without a stored basis: leading vectors u_0 .. u_{head-1} kept by the first run
     void *xt = nullptr;
     int grid;
     double tol = 0.0;
@@ -665,19 +673,30 @@ static int lz_step(Lz &z, int phase, bool pass2, cudaEvent_t *ev4, bool want_rit
                                                 nparts, 0, z.iters);
         ++nk;
     }
-    // with re-orthogonalisation the basis slot is written after it
-    T *slot_basis = (z.store && !pass2 && !z.reorth && !basis_slots) ? z.basis.as<T>() : nullptr;
+    // the update also writes u_{k+1} into its basis slot: every slot with a
+    // stored basis (with re-orthogonalisation the slot is written after it),
+    // the first z.head slots with a kept head of the basis
+    T *slot_basis = nullptr;
+    int slots = 0;
+    if (!pass2 && z.store && !z.reorth && !basis_slots) {
+        slot_basis = z.basis.as<T>();
+        slots = z.iters + 1;
+    } else if (!pass2 && !z.store && z.head > 0) {
+        slot_basis = z.basis.as<T>();
+        slots = z.head;
+    }
     int nparts2 = z.grid;
     if (updated) {
         // u_{k+1} and its transpose came out of the H·v (second run only)
     } else if (z.fuse_t) {
         const int64_t rows = z.op.ham->up.D, cols = z.op.ham->dn.D;
         const dim3 g((unsigned)((cols + 63) / 64), (unsigned)((rows + 63) / 64));
-        k_step2_t<T><<<g, 256, 0, z.st>>>(st, z.scal.as<double>(), v, w, (T *)z.xt, rows, cols, part, pass2 ? 0 : 1);
+        k_step2_t<T><<<g, 256, 0, z.st>>>(st, z.scal.as<double>(), v, w, (T *)z.xt, slot_basis, slots, rows, cols, part,
+                                          pass2 ? 0 : 1);
         nparts2 = (int)(g.x * g.y);
         ++nk;
     } else {
-        k_step2<T><<<z.grid, kRedThreads, 0, z.st>>>(st, z.scal.as<double>(), v, w, slot_basis, n, part,
+        k_step2<T><<<z.grid, kRedThreads, 0, z.st>>>(st, z.scal.as<double>(), v, w, slot_basis, slots, n, part,
                                                     (pass2 || z.reorth) ? 0 : 1);
         ++nk;
     }
@@ -733,7 +752,7 @@ static int lz_run(Lz &z, const double *d_v0, gbr_lanczos_result *res, const gbr_
     k_norm2<T><<<z.grid, kRedThreads, 0, s>>>(z.state.as<LzState>(), B0, n, z.part.as<double>());
     k_sum<<<1, kRedThreads, 0, s>>>(z.part.as<double>(), z.grid, z.tri.as<double>() + 1);
     k_scale_start<T><<<z.grid, kRedThreads, 0, s>>>(B0, z.tri.as<double>() + 1, n);
-    if (z.store) GBR_CUDA_TRY(cudaMemcpyAsync(z.basis.p, B0, (size_t)n * sizeof(T), cudaMemcpyDeviceToDevice, s));
+    if (z.store || z.head > 0) GBR_CUDA_TRY(cudaMemcpyAsync(z.basis.p, B0, (size_t)n * sizeof(T), cudaMemcpyDeviceToDevice, s));
     GBR_LAUNCH_CHECK();
     count_launches(4);
 
@@ -870,43 +889,70 @@ static int lz_run(Lz &z, const double *d_v0, gbr_lanczos_result *res, const gbr_
             }
         }
         res->ritz_terms = nterm;
+        res->basis_head = (!z.store && z.head >= 2) ? std::min(z.head, nterm) : 0;
         if (z.store) {
             k_ritz_from_basis<T><<<z.grid, kRedThreads, 0, s>>>(z.basis.as<T>(), sv, z.scal.as<double>(), nterm, n,
                                                                 x.as<double>());
             count_launches(1);
         } else {
-            // second pass of the same recurrence with the stored scalars
-            LzState zero2{};
-            GBR_CUDA_TRY(cudaMemcpyAsync(z.state.p, &zero2, sizeof(zero2), cudaMemcpyHostToDevice, s));
-            k_cast_start<T><<<z.grid, kRedThreads, 0, s>>>(d_v0, B0, n);
-            k_norm2<T><<<z.grid, kRedThreads, 0, s>>>(z.state.as<LzState>(), B0, n, z.part.as<double>());
-            k_sum<<<1, kRedThreads, 0, s>>>(z.part.as<double>(), z.grid, z.tri.as<double>() + 1);
-            k_scale_start<T><<<z.grid, kRedThreads, 0, s>>>(B0, z.tri.as<double>() + 1, n);
-            count_launches(4);
-            // u_j sits in buffer j mod 3 until step j + 2 overwrites it, so the
-            // sum takes the vectors three at a time (one pass over x per three)
-            int ph = 0, j0 = 0;
-            for (int j = 0; j < nterm; ++j) {
-                if (j % 3 == 2 || j + 1 == nterm) {
-                    const int cnt = j - j0 + 1;
-                    const T *u0 = z.buf[j0 % 3].as<T>();
-                    const T *u1 = cnt > 1 ? z.buf[(j0 + 1) % 3].as<T>() : u0;
-                    const T *u2 = cnt > 2 ? z.buf[(j0 + 2) % 3].as<T>() : u0;
-                    if (sizeof(T) == 4)
-                        k_ritz_accum3_ff<<<z.grid, kRedThreads, 0, s>>>((const float *)u0, (const float *)u1,
-                                                                        (const float *)u2, cnt, sv, z.scal.as<double>(),
-                                                                        j0, n, x.as<float2>());
-                    else
-                        k_ritz_accum3<T><<<z.grid, kRedThreads, 0, s>>>(u0, u1, u2, cnt, sv, z.scal.as<double>(), j0,
-                                                                      n, x.as<double>());
-                    count_launches(1);
-                    j0 = j + 1;
+            // the Ritz sum takes the vectors three at a time (one pass over x
+            // per three): first the head of the basis the first run kept
+            // (u_0 .. u_{m-1}), then the rest from a second run of the same
+            // recurrence with the stored scalars, restarted from the head's
+            // last two vectors (from the start vector without a head)
+            const int m = (z.head >= 2) ? std::min(z.head, nterm) : 0;
+            auto accum = [&](const T *u0, const T *u1, const T *u2, int cnt, int j0) {
+                if (sizeof(T) == 4)
+                    k_ritz_accum3_ff<<<z.grid, kRedThreads, 0, s>>>((const float *)u0, (const float *)u1,
+                                                                    (const float *)u2, cnt, sv, z.scal.as<double>(), j0,
+                                                                    n, x.as<float2>());
+                else
+                    k_ritz_accum3<T><<<z.grid, kRedThreads, 0, s>>>(u0, u1, u2, cnt, sv, z.scal.as<double>(), j0, n,
+                                                                  x.as<double>());
+                count_launches(1);
+            };
+            const T *hb = z.basis.as<T>();
+            for (int j0 = 0; j0 < m; j0 += 3) {
+                const int cnt = std::min(3, m - j0);
+                const T *u0 = hb + (int64_t)j0 * n;
+                accum(u0, cnt > 1 ? u0 + n : u0, cnt > 2 ? u0 + 2 * n : u0, cnt, j0);
+            }
+            if (nterm > m) {
+                int jstart = 0;
+                if (m >= 2) {
+                    LzState rs{};
+                    rs.k = m - 1;
+                    GBR_CUDA_TRY(cudaMemcpyAsync(z.state.p, &rs, sizeof(rs), cudaMemcpyHostToDevice, s));
+                    GBR_CUDA_TRY(cudaMemcpyAsync(z.buf[(m - 2) % 3].p, hb + (int64_t)(m - 2) * n, (size_t)n * sizeof(T),
+                                                 cudaMemcpyDeviceToDevice, s));
+                    GBR_CUDA_TRY(cudaMemcpyAsync(z.buf[(m - 1) % 3].p, hb + (int64_t)(m - 1) * n, (size_t)n * sizeof(T),
+                                                 cudaMemcpyDeviceToDevice, s));
+                    jstart = m - 1;
+                } else {
+                    LzState zero2{};
+                    GBR_CUDA_TRY(cudaMemcpyAsync(z.state.p, &zero2, sizeof(zero2), cudaMemcpyHostToDevice, s));
+                    k_cast_start<T><<<z.grid, kRedThreads, 0, s>>>(d_v0, B0, n);
+                    k_norm2<T><<<z.grid, kRedThreads, 0, s>>>(z.state.as<LzState>(), B0, n, z.part.as<double>());
+                    k_sum<<<1, kRedThreads, 0, s>>>(z.part.as<double>(), z.grid, z.tri.as<double>() + 1);
+                    k_scale_start<T><<<z.grid, kRedThreads, 0, s>>>(B0, z.tri.as<double>() + 1, n);
+                    count_launches(4);
                 }
-                if (j + 1 < nterm) {
-                    rc = lz_step<T>(z, ph, true, nullptr, false, -1, j == 0);
-                    if (rc) return rc;
+                // u_j sits in buffer j mod 3 until step j + 2 overwrites it
+                int ph = jstart % 3, j0 = m;
+                for (int j = jstart; j < nterm; ++j) {
+                    if (j >= m && ((j - m) % 3 == 2 || j + 1 == nterm)) {
+                        const int cnt = j - j0 + 1;
+                        const T *u0 = z.buf[j0 % 3].as<T>();
+                        accum(u0, cnt > 1 ? z.buf[(j0 + 1) % 3].as<T>() : u0, cnt > 2 ? z.buf[(j0 + 2) % 3].as<T>() : u0,
+                              cnt, j0);
+                        j0 = j + 1;
+                    }
+                    if (j + 1 < nterm) {
+                        rc = lz_step<T>(z, ph, true, nullptr, false, -1, j == jstart);
+                        if (rc) return rc;
+                    }
+                    ph = (ph + 1) % 3;
                 }
-                ph = (ph + 1) % 3;
             }
             if (sizeof(T) == 4) {
                 k_ritz_finish_ff<<<z.grid, kRedThreads, 0, s>>>(x.as<double>(), n);
@@ -1108,26 +1154,53 @@ int lanczos_solve(const LzOp &op, const gbr_lanczos_opts *o, const double *d_v0,
     z.st = (cudaStream_t)stream;
     const size_t es = z.fp == 64 ? 8 : 4;
     const size_t basis_bytes = (size_t)(z.iters + 1) * (size_t)z.n * es;
+    // the working vectors, the FP64 Ritz vector and its product, and the
+    // factored H·v's scratch first, so that what remains free is what a
+    // basis can have
+    int rc;
+    for (int i = 0; i < 3; ++i)
+        if ((rc = grow(z.buf[i], (size_t)z.n * es))) return rc;
+    if (o->refine) {
+        if ((rc = grow(z.x, (size_t)z.n * 8))) return rc;
+        if ((rc = grow(z.hx, (size_t)z.n * 8))) return rc;
+    }
+    // (in FP64 size with refinement: its FP64 H·v takes the same scratch)
+    if (z.factored() && !hv_xt_scratch(op.ham, o->refine ? 64 : z.fp))
+        return set_error(GBR_ENOMEM, "scratch of the factored H·v");
     // the basis is needed by re-orthogonalisation; with refinement it makes
     // the Ritz vector one pass instead of a second run of the recurrence
-    int store = 0;
+    int store = 0, head = 0;
     if (z.reorth) {
         store = 1;
     } else if (o->refine) {
         store = o->store_basis;
-        if (store < 0) {
+        if (store <= -2) {
+            // the caller's head: the leading -store_basis vectors
+            head = (int)std::min<int64_t>(-(int64_t)store, (int64_t)z.iters + 1);
+            store = 0;
+        } else if (store < 0) {
             size_t fr = 0, tot = 0;
             GBR_CUDA_TRY(cudaMemGetInfo(&fr, &tot));
             // the handle's and the process cache's bases are reused or released before a larger one is taken
             fr += z.basis.bytes + cache_bytes_here();
-            const size_t need = basis_bytes + (size_t)z.n * (3 * es + 16) + ((size_t)2 << 30);
-            store = need < fr ? 1 : 0;
+            // 2 GB to spare for the smaller buffers
+            const size_t fixed = (size_t)2 << 30;
+            store = basis_bytes + fixed < fr ? 1 : 0;
+            if (!store && fr > fixed) {
+                // not the whole basis: keep its leading vectors, as many as fit
+                // in nine tenths of what is left (at least 8), so that the
+                // second run of the recurrence starts after them
+                const size_t per = (size_t)z.n * es;
+                const size_t fit = (fr - fixed) / 10 * 9 / per;
+                head = (int)std::min<size_t>(fit, (size_t)z.iters + 1);
+                if (head < 8) head = 0;
+            }
         }
     }
     z.store = store;
+    z.head = store ? 0 : head;
     const int64_t blocks = (z.n + kRedThreads - 1) / kRedThreads;
     z.grid = (int)std::max<int64_t>(1, std::min<int64_t>(blocks, (int64_t)sm_count() * 4));
-    int rc;
     if ((rc = grow(z.state, sizeof(LzState)))) return rc;
     if ((rc = grow(z.alpha, sizeof(double) * (size_t)(z.iters + 2)))) return rc;
     if ((rc = grow(z.beta, sizeof(double) * (size_t)(z.iters + 2)))) return rc;
@@ -1140,15 +1213,17 @@ int lanczos_solve(const LzOp &op, const gbr_lanczos_opts *o, const double *d_v0,
     if ((rc = grow(z.svec, sizeof(double) * (size_t)(z.iters + 2)))) return rc;
     if ((rc = grow(z.work, sizeof(double) * 3 * (size_t)(z.iters + 2)))) return rc;
     if ((rc = grow(z.ritz_tmp, sizeof(double) * (size_t)(z.iters + 2)))) return rc;
-    for (int i = 0; i < 3; ++i)
-        if ((rc = grow(z.buf[i], (size_t)z.n * es))) return rc;
     if (z.store) {
         cache_take(z.basis, basis_bytes);
         if ((rc = grow(z.basis, basis_bytes))) return rc;
+    } else if (z.head > 0) {
+        const size_t head_bytes = (size_t)z.head * (size_t)z.n * es;
+        cache_take(z.basis, head_bytes);
+        if ((rc = grow(z.basis, head_bytes))) return rc;
     }
     rc = z.fp == 64 ? lz_run<double>(z, d_v0, res, o, h_alpha, h_beta, h_ritz)
                     : lz_run<float>(z, d_v0, res, o, h_alpha, h_beta, h_ritz);
-    if (z.store) cache_put(z.basis);
+    if (z.store || z.head > 0) cache_put(z.basis);
     return rc;
 }
 }  // namespace gbr

@@ -44,7 +44,7 @@ class LanczosResult(C.Structure):
     _fields_ = [("E0", C.c_double), ("E_ritz", C.c_double), ("residual", C.c_double), ("iters_done", C.c_int),
                 ("breakdown", C.c_int), ("stored_basis", C.c_int), ("seconds", C.c_double),
                 ("hv_seconds", C.c_double), ("stage_seconds", C.c_double * 4), ("stage_launches", C.c_int * 4),
-                ("converged", C.c_int), ("ritz_terms", C.c_int)]
+                ("converged", C.c_int), ("ritz_terms", C.c_int), ("basis_head", C.c_int)]
 
 
 class Term(C.Structure):
@@ -420,7 +420,7 @@ def _lanczos(fn, handle, v0, iters, reorth, prec, refine, store_basis, use_graph
     return dict(E0=r.E0, E_ritz=r.E_ritz, residual=r.residual, iters=k, breakdown=bool(r.breakdown),
                 stored_basis=bool(r.stored_basis), seconds=r.seconds, hv_seconds=r.hv_seconds,
                 stage_seconds=list(r.stage_seconds), stage_launches=list(r.stage_launches),
-                converged=bool(r.converged), ritz_terms=r.ritz_terms,
+                converged=bool(r.converged), ritz_terms=r.ritz_terms, basis_head=r.basis_head,
                 alpha=a[:k].copy(), beta=b[:max(k - 1, 0)].copy(), ritz=None if rz is None else rz[:k].copy())
 
 

@@ -191,6 +191,36 @@ def test_factored_path_fused_update_matches_oracle_and_is_reproducible(G):
         assert abs(a["E0"] - b["E0"]) <= 1e-13 * abs(a["E0"])
 
 
+def test_kept_head_of_the_basis(G):
+    """When the whole basis does not fit, the first run keeps its leading
+    vectors (store_basis = -m asks for m of them; -1 keeps as many as fit):
+    the Ritz sum takes those from memory and the second run of the
+    recurrence starts after them, with fewer launches.  Energy and residual
+    match the stored-basis solve, and the recurrence is the same."""
+    L, h, U, Nu, Nd = 12, S.square(4, 3, 1.0, -0.3), S.uniform_U(12, 8.0), 5, 6
+    D = oracle.sector_dim(L, Nu, Nd)
+    H = G.gbr_ham_create(L, h, U, Nu, Nd)
+    G.gbr_ham_set_path(H, G.GBR_HV_FACTORED)
+    for prec in (G.GBR_PREC_FP64, G.GBR_PREC_MIXED):
+        full = G.gbr_lanczos(H, v0(D), 60, prec=prec, refine=True, store_basis=1)
+        n0 = G.gbr_launch_count()
+        sec = G.gbr_lanczos(H, v0(D), 60, prec=prec, refine=True, store_basis=0, use_graph=True)
+        n_sec = G.gbr_launch_count() - n0
+        assert sec["basis_head"] == 0
+        # head sizes that leave each remainder of the groups of three
+        for m in (2, 10, 11, 12, 1000):
+            n0 = G.gbr_launch_count()
+            hd = G.gbr_lanczos(H, v0(D), 60, prec=prec, refine=True, store_basis=-m, use_graph=True)
+            n_hd = G.gbr_launch_count() - n0
+            assert not hd["stored_basis"] and hd["ritz_terms"] == sec["ritz_terms"]
+            assert hd["basis_head"] == min(m, hd["ritz_terms"]), (prec, m)
+            assert np.array_equal(hd["alpha"], sec["alpha"]) and np.array_equal(hd["beta"], sec["beta"])
+            assert abs(hd["E0"] - full["E0"]) <= 1e-13 * abs(full["E0"]), (prec, m)
+            assert abs(hd["residual"] - full["residual"]) <= 1e-6 * full["residual"], (prec, m)
+            if m >= 10:
+                assert n_hd < n_sec, (prec, m, n_hd, n_sec)
+
+
 def test_ritz_vector_of_the_converged_prefix(G):
     """A run far past convergence (300 steps on 4,900 states, no
     re-orthogonalisation) forms its Ritz vector from the shortest prefix whose
