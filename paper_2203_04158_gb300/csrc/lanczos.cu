@@ -1043,11 +1043,12 @@ __global__ void __launch_bounds__(kRedThreads) k_check_rcp64(int64_t n, double *
 
 using namespace gbr;
 
-// The stored basis is a solve's one large allocation (105 GB for 200 FP32
-// steps on the 4x4 sector).  A finished call leaves it in a process-wide
-// cache instead of in the handle; the next call on the same device takes it
-// when it is large enough, so repeated solves, also on new handles, neither
-// allocate nor free it.  gbr_release_cache frees it.
+// The stored basis (or its kept head) is a solve's one large allocation (105
+// GB for 200 FP32 steps on the 4x4 sector).  A finished call leaves it in a
+// process-wide cache instead of in the handle; the next call on the same
+// device takes it when it is large enough, so repeated solves, also on new
+// handles, neither allocate nor free it.  gbr_release_cache frees it, and a
+// solve whose working vectors do not fit beside it frees it first.
 namespace gbr {
 static std::mutex g_cache_mu;
 static void *g_cache_p = nullptr;
@@ -1106,6 +1107,16 @@ static void cache_put(DevBuf &b) {
     b.p = nullptr;
     b.bytes = 0;
 }
+
+// frees the cached basis when it is on the current device
+static void cache_drop_here() {
+    std::lock_guard<std::mutex> g(g_cache_mu);
+    if (!g_cache_p || g_cache_dev != current_device()) return;
+    free_on(g_cache_p, g_cache_dev);
+    g_cache_p = nullptr;
+    g_cache_bytes = 0;
+    g_cache_dev = -1;
+}
 }  // namespace gbr
 
 extern "C" int gbr_release_cache(void) {
@@ -1157,16 +1168,23 @@ int lanczos_solve(const LzOp &op, const gbr_lanczos_opts *o, const double *d_v0,
     // the working vectors, the FP64 Ritz vector and its product, and the
     // factored H·v's scratch first, so that what remains free is what a
     // basis can have
-    int rc;
-    for (int i = 0; i < 3; ++i)
-        if ((rc = grow(z.buf[i], (size_t)z.n * es))) return rc;
-    if (o->refine) {
-        if ((rc = grow(z.x, (size_t)z.n * 8))) return rc;
-        if ((rc = grow(z.hx, (size_t)z.n * 8))) return rc;
+    // (the scratch in FP64 size with refinement: its FP64 H·v takes the same
+    // buffers).  If they do not fit beside a basis kept from an earlier solve
+    // (in the process cache or in this handle), that basis is freed first.
+    int rc = GBR_OK;
+    for (int attempt = 0; attempt < 2; ++attempt) {
+        rc = GBR_OK;
+        for (int i = 0; i < 3 && !rc; ++i) rc = grow(z.buf[i], (size_t)z.n * es);
+        if (!rc && o->refine) rc = grow(z.x, (size_t)z.n * 8);
+        if (!rc && o->refine) rc = grow(z.hx, (size_t)z.n * 8);
+        if (!rc && z.factored() && !hv_xt_scratch(op.ham, o->refine ? 64 : z.fp))
+            rc = set_error(GBR_ENOMEM, "scratch of the factored H·v");
+        if (rc != GBR_ENOMEM || attempt == 1) break;
+        cache_drop_here();
+        z.basis.release();
+        clear_error();
     }
-    // (in FP64 size with refinement: its FP64 H·v takes the same scratch)
-    if (z.factored() && !hv_xt_scratch(op.ham, o->refine ? 64 : z.fp))
-        return set_error(GBR_ENOMEM, "scratch of the factored H·v");
+    if (rc) return rc;
     // the basis is needed by re-orthogonalisation; with refinement it makes
     // the Ritz vector one pass instead of a second run of the recurrence
     int store = 0, head = 0;
