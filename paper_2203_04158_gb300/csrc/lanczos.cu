@@ -765,13 +765,13 @@ static int lz_run(Lz &z, const double *d_v0, gbr_lanczos_result *res, const gbr_
     // every basis slot starts on a 16-byte boundary (the step kernels load
     // 16-byte packs) only when a vector is a whole number of packs
     z.in_basis = (z.store && !z.reorth && !graphs && ((size_t)z.n * sizeof(T)) % 16 == 0) ? 1 : 0;
-    // the tiled update that also writes X^T: factored H·v, no re-orthogonalisation
-    // (which changes w after the update), no separate basis-slot copy, and
+    // the tiled update that also writes X^T (and the basis slot): factored
+    // H·v, no re-orthogonalisation (which changes w after the update), and
     // dimensions that are whole 16-byte packs
     {
         const int64_t V = 16 / (int64_t)sizeof(T);
-        z.fuse_t = (z.factored() && !z.reorth && (!z.store || z.in_basis) && z.op.ham->up.D % V == 0 &&
-                    z.op.ham->dn.D % V == 0 && (z.op.ham->up.D + 63) / 64 <= 65535) ? 1 : 0;
+        z.fuse_t = (z.factored() && !z.reorth && z.op.ham->up.D % V == 0 && z.op.ham->dn.D % V == 0 &&
+                    (z.op.ham->up.D + 63) / 64 <= 65535) ? 1 : 0;
         z.xt = z.fuse_t ? hv_xt_scratch(z.op.ham, z.fp) : nullptr;
         if (z.fuse_t && !z.xt) return set_error(GBR_ENOMEM, "scratch for X^T");
     }
