@@ -455,7 +455,9 @@ typedef struct {
                          run of the recurrence, -1 = decide from free memory:
                          all vectors if they fit, else the leading ones that fit
                          (at least 8; the second run starts after them),
-                         -m (m >= 2) = keep the leading m vectors */
+                         -m (m >= 2) = keep the leading m vectors.  A head is
+                         kept only when a vector is a whole number of 16-byte
+                         packs (dim * element size divisible by 16) */
     int use_graph;    /* 1 = replay each iteration as a captured CUDA graph */
     int profile;      /* 1 = time every H·v stage with CUDA events (no graphs) */
     double tol;       /* > 0: every 8 steps, stop once the lowest Ritz pair of T

@@ -1216,6 +1216,10 @@ int lanczos_solve(const LzOp &op, const gbr_lanczos_opts *o, const double *d_v0,
         }
     }
     z.store = store;
+    // the head's slots follow one another at the vector's length, and the
+    // Ritz sum reads them in 16-byte packs: a head only when a vector is a
+    // whole number of packs
+    if (((size_t)z.n * es) % 16 != 0) head = 0;
     z.head = store ? 0 : head;
     const int64_t blocks = (z.n + kRedThreads - 1) / kRedThreads;
     z.grid = (int)std::max<int64_t>(1, std::min<int64_t>(blocks, (int64_t)sm_count() * 4));

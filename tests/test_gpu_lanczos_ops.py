@@ -105,3 +105,36 @@ def test_term_lanczos_two_orbital_kanamori_impurity(G, nu, nd):
     T = G.gbr_termham_create(2 * L, [G.gbr_term_product(o, c) for c, o in terms], st, 8)
     for prec in (0, 1):
         _check(_solve(G, G.gbr_termham_lanczos, T, st.size, 200, prec)["E0"], ref, prec)
+
+
+def test_set_lanczos_kept_head_and_ritz_tail(G):
+    """The operator-generic recurrence (set H·v, no spin factorisation) with a
+    kept head of the basis: every head size, with and without a cut Ritz
+    tail, gives the energy of the stored-basis solve (the same vectors,
+    summed from memory or rebuilt by the second run).  12,870 states: an
+    FP32 vector is not a whole number of 16-byte packs, so FP32 keeps no
+    head (its slots would not be aligned for the packed Ritz sum) and runs
+    the plain second run; FP64 keeps one."""
+    import torch
+    L, N = 8, 8
+    h, Uv = S.chain(L), S.uniform_U(L, 4.0)
+    st = S.fixed_N_states(L, N)
+    Sh = G.gbr_setham_create(L, h, Uv, st, 8)
+    v0 = torch.from_numpy(S.start_vector(st.size)).cuda()
+    for prec in (0, 1):
+        for tail in (0.0, 1e-6):
+            full = G.gbr_setham_lanczos(Sh, v0, 90, prec=prec, refine=True, store_basis=1, ritz_tail=tail)
+            sec = G.gbr_setham_lanczos(Sh, v0, 90, prec=prec, refine=True, store_basis=0, ritz_tail=tail)
+            for m in (2, 7, 40, 500):
+                hd = G.gbr_setham_lanczos(Sh, v0, 90, prec=prec, refine=True, store_basis=-m, ritz_tail=tail)
+                es = 8 if prec == 0 else 4
+                kept = min(m, hd["ritz_terms"]) if (st.size * es) % 16 == 0 else 0
+                assert hd["basis_head"] == kept, (prec, m, hd["basis_head"])
+                # the same recurrence as the second-run solve (the head only adds
+                # the slot writes); a stored basis whose slots are not 16-byte
+                # aligned sums its dots element by element, so its alpha and
+                # beta may differ from these in the last bits
+                assert np.array_equal(hd["alpha"], sec["alpha"]) and np.array_equal(hd["beta"], sec["beta"]), (prec, m)
+                assert hd["ritz_terms"] == sec["ritz_terms"]
+                assert abs(hd["E0"] - sec["E0"]) <= 1e-13 * abs(sec["E0"]), (prec, tail, m)
+                assert abs(hd["E0"] - full["E0"]) <= 1e-12 * abs(full["E0"]), (prec, tail, m)
