@@ -77,3 +77,16 @@ def test_a_rank_that_leaves_is_reported_not_waited_for():
     out = _run("fail")
     assert out[1][1] == "raised"
     assert out[0][1] == "error"
+
+
+def test_hv_count_of_a_solve():
+    """H·v calls a solve runs, as the benchmark counts them: the recurrence,
+    the second run of it after the kept head of the basis (none with a stored
+    basis), and the FP64 refinement."""
+    import bench
+    base = {"iters": 150, "ritz_terms": 120}
+    assert bench.hv_count(dict(base, stored_basis=True, basis_head=0)) == 151
+    assert bench.hv_count(dict(base, stored_basis=False, basis_head=0)) == 150 + 119 + 1
+    assert bench.hv_count(dict(base, stored_basis=False, basis_head=16)) == 150 + 104 + 1
+    assert bench.hv_count(dict(base, stored_basis=False, basis_head=120)) == 151
+    assert bench.hv_count(dict(base, stored_basis=False)) == 150 + 119 + 1
