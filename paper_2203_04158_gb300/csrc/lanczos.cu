@@ -273,6 +273,22 @@ __global__ void __launch_bounds__(kFinThreads) k_finalize(LzState *st, double *a
     }
 }
 
+// First stage for a long list of partial sums (the spin-up pass of the ring
+// writes one per CTA, 2.3 million): block b sums the contiguous segment
+// [b * seg, (b + 1) * seg) in a fixed order, so that the single-block
+// finalisation reads one value per block instead of the whole list.
+constexpr int kReduceAbove = 1 << 16, kReduceBlocks = 512;
+__global__ void __launch_bounds__(kRedThreads) k_reduce_parts(const LzState *st, const double *__restrict__ part,
+                                                              int nparts, double *__restrict__ out) {
+    if (st->stop) return;
+    const int seg = (nparts + (int)gridDim.x - 1) / (int)gridDim.x;
+    const int lo = (int)blockIdx.x * seg, hi = min(nparts, lo + seg);
+    double v = 0.0;
+    for (int i = lo + (int)threadIdx.x; i < hi; i += (int)blockDim.x) v += part[i];
+    const double r = block_sum(v);
+    if (threadIdx.x == 0) out[blockIdx.x] = r;
+}
+
 __global__ void k_advance(LzState *st) {
     if (threadIdx.x == 0 && blockIdx.x == 0 && !st->stop) st->k += 1;
 }
@@ -603,6 +619,7 @@ struct Lz {
     int in_basis = 0;  // the stored basis slots are the working vectors (eager launches only)
     int fuse_t = 0;    // the update writes X^T for the next H·v (k_step2_t)
     int head = 0;      // without a stored basis: leading vectors u_0 .. u_{head-1} kept by the first run
+    int64_t part_cap = 0;  // partial sums the part buffer holds before its second-stage block (kReduceBlocks)
     void *xt = nullptr;
     int grid;
     double tol = 0.0;
@@ -668,11 +685,22 @@ static int lz_step(Lz &z, int phase, bool pass2, cudaEvent_t *ev4, bool want_rit
         k_step1<T><<<z.grid, kRedThreads, 0, z.st>>>(st, z.scal.as<double>(), vprev, v, w, n, part, pass2 ? 0 : 1);
         ++nk;
     }
-    if (!pass2) {
-        k_finalize<<<1, kFinThreads, 0, z.st>>>(st, z.alpha.as<double>(), z.beta.as<double>(), z.scal.as<double>(), part,
-                                                nparts, 0, z.iters);
+    // alpha (which 0) or beta (which 1) from np partial sums, through the
+    // first-stage reduction when there are many
+    auto finalize = [&](int np, int which) {
+        const double *src = part;
+        if (np > kReduceAbove) {
+            double *p2 = part + z.part_cap;
+            k_reduce_parts<<<kReduceBlocks, kRedThreads, 0, z.st>>>(st, part, np, p2);
+            ++nk;
+            src = p2;
+            np = kReduceBlocks;
+        }
+        k_finalize<<<1, kFinThreads, 0, z.st>>>(st, z.alpha.as<double>(), z.beta.as<double>(), z.scal.as<double>(), src,
+                                                np, which, z.iters);
         ++nk;
-    }
+    };
+    if (!pass2) finalize(nparts, 0);
     // the update also writes u_{k+1} into its basis slot: every slot with a
     // stored basis (with re-orthogonalisation the slot is written after it),
     // the first z.head slots with a kept head of the basis
@@ -713,11 +741,7 @@ static int lz_step(Lz &z, int phase, bool pass2, cudaEvent_t *ev4, bool want_rit
         k_norm2<T><<<z.grid, kRedThreads, 0, z.st>>>(st, w, n, part);
         ++nk;
     }
-    if (!pass2) {
-        k_finalize<<<1, kFinThreads, 0, z.st>>>(st, z.alpha.as<double>(), z.beta.as<double>(), z.scal.as<double>(), part,
-                                                nparts2, 1, z.iters);
-        ++nk;
-    }
+    if (!pass2) finalize(nparts2, 1);
     if (z.tol > 0.0 && !pass2) {
         k_conv_check<<<1, 32, 0, z.st>>>(st, z.alpha.as<double>(), z.beta.as<double>(), z.tol, z.work.as<double>());
         ++nk;
@@ -1229,7 +1253,8 @@ int lanczos_solve(const LzOp &op, const gbr_lanczos_opts *o, const double *d_v0,
     if ((rc = grow(z.scal, sizeof(double) * kScal * (size_t)(z.iters + 2)))) return rc;
     size_t nparts = (size_t)z.grid * (size_t)(z.reorth ? z.iters + 1 : 1);
     if (op.ham) nparts = std::max(nparts, (size_t)hv_lz_parts(op.ham, z.fp));
-    if ((rc = grow(z.part, sizeof(double) * nparts))) return rc;
+    z.part_cap = (int64_t)nparts;
+    if ((rc = grow(z.part, sizeof(double) * (nparts + kReduceBlocks)))) return rc;
     if ((rc = grow(z.coef, sizeof(double) * (size_t)(z.iters + 2)))) return rc;
     if ((rc = grow(z.tri, sizeof(double) * 16))) return rc;
     if ((rc = grow(z.svec, sizeof(double) * (size_t)(z.iters + 2)))) return rc;
