@@ -42,6 +42,32 @@ def test_library_exports_every_declared_symbol(G):
     assert G.gbr_version() == 1
 
 
+def test_binding_structs_match_the_header(tmp_path):
+    """The ctypes mirrors of the header's structs (options, results, term
+    tuples, model descriptions) have the C layout: sizes and every field's
+    offset, from a C program compiled against the header."""
+    import subprocess
+    from paper_2203_04158_gb300 import gbrank as B
+    pairs = [("gbr_lanczos_opts", B.LanczosOpts), ("gbr_lanczos_result", B.LanczosResult),
+             ("gbr_term", B.Term), ("gbr_model_desc", B.ModelDesc)]
+    lines = ["#include <stdio.h>", "#include <stddef.h>", '#include "gbrank.h"', "int main(void) {"]
+    for cname, py in pairs:
+        lines.append(f'    printf("%zu\\n", sizeof({cname}));')
+        for f in py._fields_:
+            lines.append(f'    printf("%zu\\n", offsetof({cname}, {f[0]}));')
+    lines += ["    return 0;", "}"]
+    src = tmp_path / "layout.c"
+    src.write_text("\n".join(lines) + "\n")
+    exe = tmp_path / "layout"
+    subprocess.check_call(["gcc", "-std=c99", "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe)])
+    got = [int(v) for v in subprocess.check_output([str(exe)]).split()]
+    want = []
+    for _, py in pairs:
+        want.append(C.sizeof(py))
+        want += [getattr(py, f[0]).offset for f in py._fields_]
+    assert got == want
+
+
 def test_null_handles_are_rejected_on_the_host(G):
     lib = C.CDLL(G.gbrank.LIB_PATH)
     assert lib.gbr_release_cache() == G.GBR_OK          # nothing cached: no device call
